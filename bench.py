@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the H_h matrix-vector product on GB300.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+Workload (default): N = 65,536 points uniform in [0,1]^3, kernel 1/r with
+K(x,x) = 0, leaf 128, eta 1, switch level 4, tol 1e-6, adaptive storage from
+{fp64, fp32, fp16, bf16}, one fp64 right-hand side U(-1,1); timed next to the
+uniform-fp64 H_h matvec of the same compression.  A step is one complete
+product y = A_h x (permute in, phase 1, phase 2 with the dense diagonal,
+permute out).  The factors (about 1.9 GB adaptive, 3.7 GB fp64) exceed the
+L2 cache, so every step streams them from HBM.
+
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling);
+the max time over ranks is reported.  --impl reference times the CPU oracle
+(oracle/, float64 NumPy) on a bounded sample of the same product.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import hh_workloads as W  # noqa: E402
+
+CACHE = os.environ.get("HH_CACHE_DIR", "/tmp/hh_cache")
+WORKLOADS = {
+    "adaptive_65k": "N=65,536 points U[0,1]^3, kernel 1/r (K(x,x)=0), leaf 128, eta 1, switch level 4, "
+                    "tol 1e-6, adaptive {fp64,fp32,fp16,bf16} vs uniform fp64, 1 RHS U(-1,1)",
+}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_matrices(P, torch, rank, ws, dev):
+    c = W.CONFIGS["adaptive_65k"]
+    pts = W.config_points("adaptive_65k")
+    args = (c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"], c["tol"], W.F64)
+    if ws > 1 and rank != 0:
+        torch.distributed.barrier()       # rank 0 builds the cache file first
+    t0 = time.time()
+    H64 = P.HMatrix.build_cached(pts, CACHE, *args, device=dev)
+    if ws > 1 and rank == 0:
+        torch.distributed.barrier()
+    Ham = H64.reencode(c["fmts"], dev)
+    return c, pts, H64, Ham, time.time() - t0
+
+
+def timed_loop(torch, H, x, y, steps, ws):
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(steps):
+        H.matvec(x, out=y)
+    e1.record(st)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    return e0.elapsed_time(e1)
+
+
+def max_over_ranks(torch, v, ws):
+    if ws == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def traffic_for(kernel: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
+    the current sources (profiles/traffic.json carries the source digest)."""
+    try:
+        from paper_2604_09147_gb300 import build as b
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        if t.get("source_digest") == b._digest() and kernel in t.get("kernels", {}):
+            return float(t["kernels"][kernel]["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def oracle_sample(path: str, x: np.ndarray, budget_s: float, fraction: float | None = None):
+    """Time the oracle's Algorithm 4 (float64 NumPy) on a bounded sample:
+    whole products while they fit the budget, else a slice of the blocks;
+    returns (products per second, description, blocks, seconds)."""
+    from oracle import hhfile
+    from oracle import matvec as M
+    G = hhfile.read(path)
+    blocks = G.lowrank
+    if fraction is None:
+        t = time.perf_counter()
+        M.matvec(G, x)
+        one = time.perf_counter() - t
+        fraction = 1.0 if one <= budget_s / 3 else max(0.01, (budget_s / 3) / one)
+    nb = max(1, int(round(len(blocks) * fraction)))
+    part = G.__class__(**{**G.__dict__, "lowrank": blocks[:nb],
+                          "dense": G.dense[:max(1, int(round(len(G.dense) * fraction)))]})
+    frac_bytes = (sum(b.k * (b.m + b.n) for b in part.lowrank) + sum(d.m * d.n for d in part.dense)) / \
+        max(1.0, sum(b.k * (b.m + b.n) for b in blocks) + sum(d.m * d.n for d in G.dense))
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        M.matvec(part, x)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 50:
+            break
+    rate = reps * frac_bytes / el
+    desc = (f"oracle Algorithm 4 in float64 NumPy over {nb} of {len(blocks)} low-rank blocks "
+            f"({100 * frac_bytes:.1f}% of the factor+dense words), {reps} passes, {el:.1f} s")
+    return rate, desc, el
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import paper_2604_09147_gb300 as P
+    c = W.CONFIGS["adaptive_65k"]
+    pts = W.config_points("adaptive_65k")
+    H64 = P.HMatrix.build_cached(pts, CACHE, c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"],
+                                 c["tol"], W.F64, device=-1)
+    Ham = H64.reencode(c["fmts"], -1)
+    path = os.path.join(CACHE, "bench_adaptive_ref.hhm")
+    Ham.save(path)
+    x = W.config_rhs("adaptive_65k")[:, 0]
+    per_step = max(0.5, 120.0 / max(1, args.steps + args.warmup))
+    rate, desc, el = oracle_sample(path, x, per_step * args.steps)
+    out = {"impl": "reference", "metric": "H_h matvecs/s (adaptive precision)", "value": rate,
+           "unit": "matvec/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000.0 / rate, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOADS["adaptive_65k"]},
+           "cpu_baseline": {"value": rate, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": rate, "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", init_method="env://")
+    dev = torch.cuda.current_device()
+    import paper_2604_09147_gb300 as P
+    from paper_2604_09147_gb300 import build as B
+    B.build()
+    c, pts, H64, Ham, build_s = build_matrices(P, torch, rank, ws, dev)
+    n = len(pts)
+    x = torch.from_numpy(W.config_rhs("adaptive_65k")[:, 0].copy()).cuda()
+    y = torch.empty_like(x)
+    inf, inf64 = Ham.info(), H64.info()
+    for _ in range(args.warmup):
+        Ham.matvec(x, out=y)
+        H64.matvec(x, out=y)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t_amp = timed_loop(torch, Ham, x, y, args.steps, ws)
+    t_64 = timed_loop(torch, H64, x, y, args.steps, ws)
+    clk = clocks.stop()
+    t_amp = max_over_ranks(torch, t_amp, ws)
+    t_64 = max_over_ranks(torch, t_64, ws)
+    Ham.sync_status()
+    ms_amp, ms_64 = t_amp / args.steps, t_64 / args.steps
+    value = ws * args.steps / (t_amp / 1000.0)
+    hbm, peak_kind = peaks()
+
+    # per-launch device times (CUDA events between the four launches)
+    phases = np.zeros(4)
+    nph = min(args.steps, 200)
+    for _ in range(nph):
+        phases += np.array(Ham.matvec_timed(x, y))
+    phases /= nph
+    bytes_p1 = inf["v_bytes"]
+    bytes_p2 = inf["u_bytes"] + inf["dense_bytes"]
+    dom = 1 if phases[1] >= phases[2] else 2
+    dom_bytes = bytes_p1 if dom == 1 else bytes_p2
+    dom_name = "pass_kernel<1,...> (phase 1: t_b = V_b^T x_J)" if dom == 1 else \
+        "pass_kernel<2,...> (phase 2: y_I += U_b t_b, dense diagonal)"
+    achieved = dom_bytes / (phases[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic_for(f"phase{dom}"), "kernel": dom_name, "peak_kind": f"of {peak_kind}",
+                "bytes_per_launch": dom_bytes, "ms_per_launch": float(phases[dom]),
+                "phase_ms": {"prep": phases[0], "phase1": phases[1], "phase2": phases[2], "finish": phases[3]}}
+
+    # end to end through the C-ABI from pinned host buffers
+    xh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    xh.copy_(x.cpu())
+    xnp = xh.numpy()
+    e2e_steps = max(3, min(args.steps, 200))
+    for _ in range(3):
+        Ham.matvec_host(xnp)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        Ham.matvec_host(xnp)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ws * e2e_steps / max_over_ranks(torch, e2e_s, ws), "unit": "matvec/s",
+           "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        path = os.path.join(CACHE, "bench_adaptive.hhm")
+        Ham.save(path)
+        rate, desc, _ = oracle_sample(path, W.config_rhs("adaptive_65k")[:, 0], args.cpu_seconds)
+        cpu = {"value": rate, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+
+    gbs = inf["bytes_per_matvec"] / (ms_amp * 1e-3) / 1e9
+    gbs64 = inf64["bytes_per_matvec"] / (ms_64 * 1e-3) / 1e9
+    out = {
+        "metric": "H_h matvecs/s (adaptive precision), HBM GB/s and fraction of peak, vs uniform fp64",
+        "value": value, "unit": "matvec/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_amp, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "dtype_note": "fp32 accumulation for 32/16/8-bit factors, fp64 for fp64 factors, "
+                                      "the dense diagonal and the output scatter",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["adaptive_65k"], "n": n, "nrhs": 1, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (factor bytes %.2f GB adaptive / %.2f GB fp64 per step)"
+                         % (inf["bytes_per_matvec"] / 1e9, inf64["bytes_per_matvec"] / 1e9)},
+        "gbs": gbs, "hbm_frac": gbs / hbm,
+        "fp64_uniform": {"value": ws * args.steps / (t_64 / 1000.0), "unit": "matvec/s", "ms_per_step": ms_64,
+                         "gbs": gbs64, "hbm_frac": gbs64 / hbm},
+        "speedup_vs_fp64": ms_64 / ms_amp,
+        "bytes_ratio_fp64_over_amp": inf64["bytes_per_matvec"] / inf["bytes_per_matvec"],
+        "storage_ratio_fp64_over_amp": inf["storage_fp64"] / inf["storage_amp"],
+        "blocks_per_fmt": inf["blocks_per_fmt"],
+        "bound_thm44": inf["bound_thm44"],
+        "build_seconds": build_s,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": 4 * args.steps, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU oracle baseline time budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

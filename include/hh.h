@@ -1,0 +1,209 @@
+/*
+ * hh.h -- C-ABI of the GB300 H_h-matrix library.
+ *
+ * The library builds a hybrid hierarchical matrix (H_h) of a kernel matrix
+ * H_ij = f(|x_i - x_j|) (Khan & Carson, Eq. 5.1) with hybrid admissibility
+ * (Eq. 3.1: standard admissibility on levels 1..ell, the remaining
+ * off-diagonal pairs compressed at level ell, weak admissibility below, dense
+ * blocks only on the leaf diagonal; Algorithm 1), stores every admissible
+ * block U_b V_b^T in the precision chosen by the adaptive rule of Algorithm 3
+ * (u_b <= eps / (2^{l/2} xi_b), xi_b = ||H~_b||_F / ||H~||_F), and applies it:
+ * b = H_hat x (Algorithm 4) and the transpose product, on one GPU.
+ *
+ * Conventions for every entry point:
+ *  - Return value: HH_OK (0) on success, a negative HH_E* code otherwise; the
+ *    thread-local message of the last failure is returned by hh_last_error().
+ *  - Vectors are column-major (n x nrhs, leading dimension ld >= n) float64
+ *    arrays in the caller's point order; device pointers unless stated.
+ *    The caller owns them; the library never frees or keeps them.
+ *  - Matrix-vector calls are asynchronous on the given cudaStream_t (NULL =
+ *    the legacy default stream) and never synchronise, allocate or copy to the
+ *    host; they overwrite the output (no accumulation).  Input and output must
+ *    not overlap.
+ *  - A handle owns its host metadata and device arenas; it is immutable after
+ *    construction.  hh_matvec / hh_matvec_T use a per-handle workspace, so
+ *    calls on one handle must be ordered on a single stream; use
+ *    hh_matvec_ws with caller-owned workspaces for concurrent streams.
+ *  - Device-side anomalies (an invalid descriptor) are recorded in a device
+ *    status word and reported by hh_sync_status(); the kernels never trap and
+ *    contain no waits on other blocks.
+ */
+#ifndef HH_H_
+#define HH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HH_OK 0
+#define HH_EINVAL (-1)   /* invalid argument, size or file content           */
+#define HH_ENOMEM (-2)   /* host or device allocation failed                 */
+#define HH_ECUDA (-3)    /* a CUDA runtime call failed                        */
+#define HH_ETIMEOUT (-4) /* reserved: a bounded device wait gave up           */
+#define HH_ENOTSUP (-5)  /* valid but unsupported request (e.g. no device)    */
+#define HH_EIO (-6)      /* file could not be read or written                 */
+#define HH_EDEVICE (-7)  /* the device status word reports an anomaly         */
+
+/* kernel functions f(r) (Section 5; r = |x_i - x_j|_2, p = kernel_param) */
+enum hh_kernel {
+  HH_EXP = 0,    /* exp(-r/p)                 (Matern)                        */
+  HH_INV_R = 1,  /* 1/r,   f = 0 at r = 0     (3-D single-layer Laplace)      */
+  HH_GAUSS = 2,  /* exp(-r^2/p)               (Gaussian)                      */
+  HH_LOG = 3,    /* log r, f = 0 at r = 0     (2-D single-layer Laplace)      */
+  HH_INV_R2 = 4  /* 1/r^2, f = 0 at r = 0                                     */
+};
+
+/* storage formats (Table 1; fp8 e4m3fn stands for the paper's 1-4-3 format) */
+enum hh_fmt { HH_FMT_F64 = 0, HH_FMT_F32 = 1, HH_FMT_F16 = 2, HH_FMT_BF16 = 3, HH_FMT_E4M3 = 4 };
+/* fmt_mask bits: the set U of available precisions; fp64 is always available */
+#define HH_F64 1u
+#define HH_F32 2u
+#define HH_F16 4u
+#define HH_BF16 8u
+#define HH_E4M3 16u
+
+typedef struct hh_matrix* hh_handle;
+
+#define HH_MAX_LEVELS 48
+
+/* Summary of a built matrix (storage in fp64 words as in Section 5.2). */
+typedef struct {
+  int64_t n;                      /* matrix size N                                   */
+  int32_t dim, L, ell, leaf_size; /* point dimension, tree depth, switch level, n_max */
+  int32_t kernel, device;         /* hh_kernel; CUDA device or -1 (host only)         */
+  double eta, tol, kernel_param;
+  int64_t n_lowrank, n_dense;     /* number of admissible / dense blocks             */
+  int64_t blocks_per_fmt[5];      /* admissible blocks per hh_fmt                    */
+  int64_t factor_bytes_per_fmt[5];/* bytes of U and V per hh_fmt (algorithmic)       */
+  int64_t dense_bytes;            /* bytes of the fp64 dense blocks                  */
+  int64_t u_bytes, v_bytes;       /* bytes of all U factors / all V factors          */
+  int64_t max_rank;
+  double storage_amp;             /* sum p(m+n) b/64 + sum m n   (adaptive)          */
+  double storage_fp64;            /* the same with every block in fp64               */
+  double bytes_per_matvec;        /* algorithmic bytes of one single-RHS product     */
+  double flops_per_matvec;        /* 2 (sum p(m+n) + sum m n)                        */
+  double norm_ht;                 /* ||H~||_F (Algorithm 5)                          */
+  int32_t csp[HH_MAX_LEVELS];     /* measured sparsity constant C_sp(l), l = 0..L    */
+  double bound_thm42;             /* (2 sqrt(sum_l C_sp(l)) + 1) eps (Theorem 4.2)   */
+  double bound_thm44;             /* 2 * bound_thm42 (Theorem 4.4, backward error)   */
+  double bound_rounding;          /* sqrt(sum_b ((2+sqrt(p)u)u||H~_b||)^2)/||H~||    */
+  double build_seconds;           /* wall time of hh_build (0 for hh_load)           */
+} hh_info_t;
+
+/*
+ * hh_build -- construct A_h from points (Algorithms 1, 5 and 3).
+ *   points       host, n x dim row-major float64 (user order); read only.
+ *   n, dim       n >= 1, 1 <= dim <= 3.
+ *   kernel       hh_kernel; kernel_param > 0 is p of exp(-r/p) / exp(-r^2/p).
+ *   leaf_size    n_max >= 1: leaves hold at most this many points; the tree is
+ *                a binary KD bisection of depth L = ceil(log2(n / n_max)).
+ *   eta          admissibility parameter of Eq. 2.2 (> 0).
+ *   switch_level ell in [0, L]; -1 selects floor(L/2).  ell = L gives an H_s
+ *                matrix, ell = 0 a HODLR matrix.  ell > L -> HH_ENOTSUP.
+ *   tol          target accuracy eps of LRcompression (0 < tol < 1).
+ *   fmt_mask     HH_F64|HH_F32|... the set U of Algorithm 3; HH_F64 alone
+ *                gives uniform fp64 storage.
+ *   seed         recorded in saved files; the build itself is deterministic.
+ *   device       CUDA device to upload to, or -1 for a host-only handle
+ *                (hh_save / hh_info work; matrix-vector calls return
+ *                HH_ENOTSUP).
+ *   out          receives the new handle (NULL on failure).
+ * Host-synchronous; uses all host cores (HH_BUILD_THREADS overrides).
+ */
+int hh_build(const double* points, int64_t n, int dim, int kernel, double kernel_param,
+             int leaf_size, double eta, int switch_level, double tol, uint32_t fmt_mask,
+             uint64_t seed, int device, hh_handle* out);
+
+/* hh_load -- read a file written by hh_save (or by any writer of the same
+ * documented layout) and upload it to `device` (-1: host only).  The layout
+ * is validated (offsets, alignment, bounds); a bad file gives HH_EINVAL. */
+int hh_load(const char* path, int device, hh_handle* out);
+
+/* hh_reencode -- apply Algorithm 3 again to a matrix stored in uniform fp64
+ * (every factor fp64, as hh_build with fmt_mask = HH_F64 produces) with the
+ * format set fmt_mask, reusing its tree, partition, compression and norms
+ * (||H~_b||, ||H~||): the result equals hh_build with that mask.  ell == L
+ * gives HH_ENOTSUP (there the dense/low-rank choice of leaf neighbours
+ * depends on the format, Section 4.3); a non-uniform source HH_EINVAL.
+ * The new handle is independent of src and uploaded to `device` (-1: none). */
+int hh_reencode(hh_handle src, uint32_t fmt_mask, int device, hh_handle* out);
+
+/* hh_save -- write the handle's matrix (points, tree, block tables, factor
+ * arena in stored formats, dense blocks) to `path`. */
+int hh_save(hh_handle h, const char* path);
+
+/* hh_info -- fill *out with sizes, storage, bounds (Theorems 4.2 / 4.4). */
+int hh_info(hh_handle h, hh_info_t* out);
+
+/* hh_perm -- copy the tree permutation (perm[p] = user index of tree
+ * position p) into the host array perm[n]. */
+int hh_perm(hh_handle h, int32_t* perm);
+
+/*
+ * hh_matvec -- y = A_h x (Algorithm 4), nrhs right-hand sides.
+ *   x  device, n x nrhs, leading dimension ldx >= n;  y device, ldy >= n.
+ *   nrhs >= 1 (any number; processed in chunks of up to 4 columns).
+ *   stream  cudaStream_t (as void*).
+ * Low-rank blocks are computed from their stored format with fp32
+ * accumulation (fp64 for fp64-stored blocks); dense blocks and the final
+ * accumulation into y are fp64.  Uses the handle's workspace.
+ */
+int hh_matvec(hh_handle h, const double* x, double* y, int nrhs, int64_t ldx, int64_t ldy,
+              void* stream);
+
+/* hh_matvec_T -- xbar = A_h^T ybar: every block applied transposed
+ * (V_b (U_b^T ybar_I), H_IJ^T ybar_I).  Same argument rules as hh_matvec. */
+int hh_matvec_T(hh_handle h, const double* ybar, double* xbar, int nrhs, int64_t ldy,
+                int64_t ldx, void* stream);
+
+/* hh_workspace_bytes -- bytes of device workspace hh_matvec_ws needs. */
+int hh_workspace_bytes(hh_handle h, size_t* bytes);
+
+/* hh_matvec_ws -- hh_matvec (transpose != 0: hh_matvec_T) with a
+ * caller-owned device workspace of at least hh_workspace_bytes() bytes,
+ * 256-byte aligned; concurrent calls with distinct workspaces are safe. */
+int hh_matvec_ws(hh_handle h, int transpose, const double* in, double* out, int nrhs,
+                 int64_t ld_in, int64_t ld_out, void* workspace, size_t workspace_bytes,
+                 void* stream);
+
+/* hh_matvec_host -- end-to-end product from HOST buffers: copies x (n x nrhs,
+ * ld = n, pinned or pageable) to the device, applies A_h (or A_h^T when
+ * transpose != 0), copies the result to y_host and synchronises `stream`. */
+int hh_matvec_host(hh_handle h, int transpose, const double* x_host, double* y_host, int nrhs,
+                   void* stream);
+
+/* hh_matvec_timed -- one product (transpose != 0: A_h^T) with CUDA events
+ * recorded on `stream` between its four launches; synchronises the stream
+ * and writes the device time in ms of each launch to ms[4] = {prep,
+ * phase 1 (t_b = V_b^T x), phase 2 (y += U_b t_b and dense blocks),
+ * finish}.  nrhs must be 1, 2 or 4 (one launch sequence).  For measurement;
+ * uses the handle's workspace. */
+int hh_matvec_timed(hh_handle h, int transpose, const double* in, double* out, int nrhs,
+                    int64_t ld_in, int64_t ld_out, void* stream, float* ms);
+
+/* hh_matvec_batched -- y_i = A_i x_i for `count` independent matrices (one
+ * right-hand side each, ld = n_i) in one launch sequence over the
+ * concatenated work lists.  All handles must live on the same device. */
+int hh_matvec_batched(const hh_handle* hs, int count, const double* const* xs,
+                      double* const* ys, void* stream);
+
+/* hh_sync_status -- synchronise `stream` and report the device status word
+ * of the handle (HH_EDEVICE if a kernel recorded an anomaly). */
+int hh_sync_status(hh_handle h, void* stream);
+
+/* hh_free -- release a handle (NULL is a no-op).  Pending work that uses the
+ * handle must be complete. */
+void hh_free(hh_handle h);
+
+/* hh_last_error -- message of the last failing call on this thread. */
+const char* hh_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HH_H_ */

@@ -1,0 +1,686 @@
+// Host builder of the H_h matrix: cluster tree, hybrid partition
+// (Algorithm 1), LRcompression, Frobenius norms (Algorithm 5), adaptive
+// precision assignment (Algorithm 3) and the format-grouped factor arena.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <numeric>
+#include <stdexcept>
+#include <thread>
+
+#include "hh_host.h"
+#include "linalg.h"
+
+namespace hh {
+
+int fmt_bytes(int fmt) {
+  static const int b[NFMT] = {8, 4, 2, 2, 1};
+  return b[fmt];
+}
+int fmt_bits(int fmt) { return 8 * fmt_bytes(fmt); }
+double unit_roundoff(int fmt) {
+  // u = 2^-(mantissa bits + 1) (Table 1; 2^-4 for the 1-4-3 format)
+  static const double u[NFMT] = {0x1p-53, 0x1p-24, 0x1p-11, 0x1p-8, 0x1p-4};
+  return u[fmt];
+}
+
+namespace {
+
+// ---------------------------------------------------------------- kernels
+// Eq. 5.1: H_ij = f(|x_i - x_j|), f(0) = 0 for the singular kernels.
+inline double kernel_value(int kernel, double p, double r) {
+  switch (kernel) {
+    case 0: return std::exp(-r / p);
+    case 1: return r == 0.0 ? 0.0 : 1.0 / r;
+    case 2: return std::exp(-(r * r) / p);
+    case 3: return r == 0.0 ? 0.0 : std::log(r);
+    default: return r == 0.0 ? 0.0 : 1.0 / (r * r);
+  }
+}
+
+struct Geometry {
+  const double* pts;  // tree-ordered points, n x dim
+  int dim;
+  int kernel;
+  double p;
+  double entry(int64_t a, int64_t b) const {
+    const double* x = pts + a * dim;
+    const double* y = pts + b * dim;
+    double s = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      double t = x[d] - y[d];
+      s = s + t * t;
+    }
+    return kernel_value(kernel, p, std::sqrt(s));
+  }
+};
+
+// -------------------------------------------------------------------- tree
+int tree_depth(int64_t n, int64_t leaf) {
+  int L = 0;
+  while ((n + (int64_t(1) << L) - 1) >> L > leaf) ++L;
+  return L;
+}
+
+void build_tree(const double* pts, int64_t n, int dim, int leaf, HostMatrix& h) {
+  const int L = tree_depth(n, leaf);
+  const int64_t nn = (int64_t(2) << L) - 1;
+  h.L = L;
+  h.node_off.assign(nn, 0);
+  h.node_size.assign(nn, 0);
+  h.node_lo.assign(nn * dim, 0.0);
+  h.node_hi.assign(nn * dim, 0.0);
+  std::vector<int64_t> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  h.node_size[0] = n;
+  for (int64_t node = 0; node < nn; ++node) {
+    const int64_t o = h.node_off[node], s = h.node_size[node];
+    double* lo = &h.node_lo[node * dim];
+    double* hi = &h.node_hi[node * dim];
+    if (s > 0) {
+      for (int d = 0; d < dim; ++d) lo[d] = hi[d] = pts[perm[o] * dim + d];
+      for (int64_t q = o; q < o + s; ++q)
+        for (int d = 0; d < dim; ++d) {
+          double v = pts[perm[q] * dim + d];
+          lo[d] = std::min(lo[d], v);
+          hi[d] = std::max(hi[d], v);
+        }
+    }
+    int level = 63 - __builtin_clzll(static_cast<unsigned long long>(node + 1));
+    if (level == L) continue;
+    int axis = 0;
+    double best = hi[0] - lo[0];
+    for (int d = 1; d < dim; ++d)
+      if (hi[d] - lo[d] > best) {
+        best = hi[d] - lo[d];
+        axis = d;
+      }
+    std::sort(perm.begin() + o, perm.begin() + o + s, [&](int64_t a, int64_t b) {
+      double ca = pts[a * dim + axis], cb = pts[b * dim + axis];
+      return ca < cb || (ca == cb && a < b);
+    });
+    const int64_t half = s / 2;
+    h.node_off[2 * node + 1] = o;
+    h.node_size[2 * node + 1] = half;
+    h.node_off[2 * node + 2] = o + half;
+    h.node_size[2 * node + 2] = s - half;
+  }
+  h.perm.resize(n);
+  for (int64_t q = 0; q < n; ++q) h.perm[q] = static_cast<int32_t>(perm[q]);
+}
+
+// --------------------------------------------------------------- partition
+double box_diam(const HostMatrix& h, int64_t node) {
+  double s = 0.0;
+  for (int d = 0; d < h.dim; ++d) {
+    double e = h.node_hi[node * h.dim + d] - h.node_lo[node * h.dim + d];
+    s = s + e * e;
+  }
+  return std::sqrt(s);
+}
+
+double box_dist(const HostMatrix& h, int64_t a, int64_t b) {
+  double s = 0.0;
+  for (int d = 0; d < h.dim; ++d) {
+    double g1 = h.node_lo[b * h.dim + d] - h.node_hi[a * h.dim + d];
+    double g2 = h.node_lo[a * h.dim + d] - h.node_hi[b * h.dim + d];
+    double g = std::max(0.0, std::max(g1, g2));
+    s = s + g * g;
+  }
+  return std::sqrt(s);
+}
+
+// Eq. 2.2, inclusive
+bool adm_s(const HostMatrix& h, int64_t a, int64_t b, double eta) {
+  return std::min(box_diam(h, a), box_diam(h, b)) <= eta * box_dist(h, a, b);
+}
+
+struct Pair {
+  int level, i, j, kind;  // kind: LR kinds, or -1 diagonal dense / KIND_NBR dense candidate
+};
+
+void hybrid_partition(const HostMatrix& h, double eta, int ell, std::vector<Pair>& lr,
+                      std::vector<Pair>& dense) {
+  const int L = h.L;
+  std::vector<Pair> stack{{0, 0, 0, 0}};
+  while (!stack.empty()) {
+    Pair p = stack.back();
+    stack.pop_back();
+    const int l = p.level;
+    const int64_t ni = (int64_t(1) << l) - 1 + p.i, nj = (int64_t(1) << l) - 1 + p.j;
+    if (l >= 1) {
+      if (l <= ell && adm_s(h, ni, nj, eta)) {
+        lr.push_back({l, p.i, p.j, KIND_STD});
+        continue;
+      }
+      if (l == ell && ell < L && p.i != p.j) {
+        lr.push_back({l, p.i, p.j, KIND_FINER});
+        continue;
+      }
+      if (l > ell && p.i != p.j) {
+        lr.push_back({l, p.i, p.j, KIND_WEAK});
+        continue;
+      }
+    }
+    if (l == L) {
+      dense.push_back({l, p.i, p.j, p.i == p.j ? -1 : KIND_NBR});
+      continue;
+    }
+    for (int a = 1; a >= 0; --a)
+      for (int b = 1; b >= 0; --b) stack.push_back({l + 1, 2 * p.i + a, 2 * p.j + b, 0});
+  }
+}
+
+// ------------------------------------------------------------- compression
+struct Compressed {
+  la::Mat U, V;
+  std::vector<double> s;
+};
+
+constexpr int64_t kDenseMax = int64_t(1) << 18;
+constexpr double kAcaShare = 0.01;
+constexpr int kAcaPatience = 3;
+
+// LRcompression to eps (Eq. 2.1): U orthonormal, V = Z Sigma.
+void compress_block(const Geometry& g, int64_t r0, int64_t m, int64_t c0, int64_t n, double eps,
+                    Compressed& out) {
+  la::Mat Ub, Vb;  // small path: A ~= Ub Vb^T with Ub orthonormal
+  if (m * n <= kDenseMax) {
+    // dense block, column-pivoted QR to eps/100 (exact trailing norm), then
+    // the SVD of the R factor
+    la::Mat A(m, n);
+    for (int64_t c = 0; c < n; ++c)
+      for (int64_t r = 0; r < m; ++r) A(r, c) = g.entry(r0 + r, c0 + c);
+    la::Mat Q, R;
+    la::cpqr_trunc(std::move(A), kAcaShare * eps, Q, R);
+    Ub = std::move(Q);
+    Vb = la::Mat(n, R.m);  // Vb = R^T
+    for (int64_t i = 0; i < R.m; ++i)
+      for (int64_t c = 0; c < n; ++c) Vb(c, i) = R(i, c);
+  } else {
+    la::Mat U, V;
+    la::aca([&](int64_t i, double* o) { for (int64_t c = 0; c < n; ++c) o[c] = g.entry(r0 + i, c0 + c); },
+            [&](int64_t j, double* o) { for (int64_t r = 0; r < m; ++r) o[r] = g.entry(r0 + r, c0 + j); },
+            m, n, kAcaShare * eps, kAcaPatience, U, V);
+    if (U.n == 0) {
+      out.U = la::Mat(m, 0);
+      out.V = la::Mat(n, 0);
+      out.s.clear();
+      return;
+    }
+    // A ~= Qu (Ru Rv^T) Qv^T: SVD of the k x k core T = W S Z^T gives
+    // U = Qu W (orthonormal) and V = Qv Z S
+    la::Mat Qu, Ru, Qv, Rv;
+    la::qr_thin(U, Qu, Ru);
+    la::qr_thin(V, Qv, Rv);
+    const int64_t k = U.n;
+    la::Mat T(k, k);
+    for (int64_t c = 0; c < k; ++c)
+      for (int64_t r = 0; r < k; ++r) {
+        double s = 0.0;
+        for (int64_t q = std::max(r, c); q < k; ++q) s += Ru(r, q) * Rv(c, q);
+        T(r, c) = s;
+      }
+    la::Mat W, Z;
+    std::vector<double> s;
+    la::svd_jacobi(T, W, s, Z);
+    const int r = la::trunc_rank(s, (1.0 - kAcaShare) * eps);
+    out.s.assign(s.begin(), s.begin() + r);
+    out.U = la::Mat(m, r);
+    out.V = la::Mat(n, r);
+    la::gemm_nn(Qu, W, r, out.U);
+    la::gemm_nn(Qv, Z, r, out.V);
+    for (int64_t c = 0; c < r; ++c)
+      for (int64_t i = 0; i < n; ++i) out.V(i, c) *= s[c];
+    return;
+  }
+  // A ~= Ub Vb^T with Ub orthonormal: SVD of Vb (n x k) = W S Z^T gives
+  // A ~= (Ub Z) S W^T, U = Ub Z (orthonormal), V = W S.
+  const int64_t k = Vb.n;
+  if (k == 0) {
+    out.U = la::Mat(m, 0);
+    out.V = la::Mat(n, 0);
+    out.s.clear();
+    return;
+  }
+  // k <= min(m, n) for both paths, so Vb has at least as many rows as columns
+  la::Mat W, Z;
+  std::vector<double> s;
+  la::svd_jacobi(Vb, W, s, Z);
+  const int r = la::trunc_rank(s, (1.0 - kAcaShare) * eps);
+  out.s.assign(s.begin(), s.begin() + r);
+  out.U = la::Mat(m, r);
+  la::gemm_nn(Ub, Z, r, out.U);
+  out.V = la::Mat(n, r);
+  for (int64_t c = 0; c < r; ++c)
+    for (int64_t i = 0; i < n; ++i) out.V(i, c) = W(i, c) * s[c];
+}
+
+// ----------------------------------------------------------------- formats
+struct FmtSpec {
+  int mbits, emin;
+  double vmax, target;
+};
+FmtSpec fmt_spec(int fmt) {
+  switch (fmt) {
+    case F32: return {23, -126, 3.4028234663852886e38, 1.0};
+    case F16: return {10, -14, 65504.0, 65504.0};
+    case BF16: return {7, -126, 3.3895313892515355e38, 1.0};
+    default: return {3, -6, 448.0, 448.0};
+  }
+}
+
+// round-to-nearest-even of v into fmt (subnormals kept); exact in double
+double round_to(double v, int fmt) {
+  if (fmt == F64 || v == 0.0) return v;
+  FmtSpec sp = fmt_spec(fmt);
+  int E;
+  std::frexp(v, &E);
+  int e = std::max(E - 1, sp.emin);
+  double q = std::ldexp(1.0, e - sp.mbits);
+  double r = std::nearbyint(v / q) * q;
+  if (std::fabs(r) > sp.vmax) throw std::runtime_error("factor value exceeds format range");
+  return r;
+}
+
+int scale_exponent(double maxabs, int fmt) {
+  if (fmt == F64 || maxabs == 0.0) return 0;
+  const double t = fmt_spec(fmt).target;
+  int E;
+  std::frexp(maxabs / t, &E);
+  int e = E;
+  while (std::ldexp(maxabs, -e) > t) ++e;
+  while (std::ldexp(maxabs, -(e - 1)) <= t) --e;
+  return e;
+}
+
+void store_value(uint8_t* dst, double r, int fmt) {
+  switch (fmt) {
+    case F64: std::memcpy(dst, &r, 8); return;
+    case F32: {
+      float f = static_cast<float>(r);
+      std::memcpy(dst, &f, 4);
+      return;
+    }
+    case BF16: {
+      float f = static_cast<float>(r);
+      uint32_t w;
+      std::memcpy(&w, &f, 4);
+      uint16_t b = static_cast<uint16_t>(w >> 16);
+      std::memcpy(dst, &b, 2);
+      return;
+    }
+    case F16: {
+      uint16_t s = std::signbit(r) ? 0x8000 : 0;
+      double a = std::fabs(r);
+      uint16_t bits;
+      if (a < 0x1p-14) {
+        bits = static_cast<uint16_t>(std::lrint(a / 0x1p-24));
+      } else {
+        int E;
+        std::frexp(a, &E);
+        int e = E - 1;
+        uint16_t mant = static_cast<uint16_t>(std::lrint((std::ldexp(a, -e) - 1.0) * 1024.0));
+        bits = static_cast<uint16_t>(((e + 15) << 10) | mant);
+      }
+      bits |= s;
+      std::memcpy(dst, &bits, 2);
+      return;
+    }
+    default: {  // e4m3fn
+      uint8_t s = std::signbit(r) ? 0x80 : 0;
+      double a = std::fabs(r);
+      uint8_t bits;
+      if (a < 0x1p-6) {
+        bits = static_cast<uint8_t>(std::lrint(a / 0x1p-9));
+      } else {
+        int E;
+        std::frexp(a, &E);
+        int e = E - 1;
+        uint8_t mant = static_cast<uint8_t>(std::lrint((std::ldexp(a, -e) - 1.0) * 8.0));
+        bits = static_cast<uint8_t>(((e + 7) << 3) | mant);
+      }
+      *dst = bits | s;
+      return;
+    }
+  }
+}
+
+int choose_format(double tau, uint32_t mask) {
+  int best = F64;
+  double bu = unit_roundoff(F64);
+  for (int f = F32; f <= E4M3; ++f) {
+    if (!(mask & (1u << f))) continue;
+    double u = unit_roundoff(f);
+    if (u <= tau && u > bu) {
+      best = f;
+      bu = u;
+    }
+  }
+  return best;
+}
+
+double block_tau(double tol, int level, double nb, double nall) {
+  double xi = nb / nall;
+  if (xi == 0.0) return std::numeric_limits<double>::infinity();
+  return tol / (std::sqrt(std::ldexp(1.0, level)) * xi);
+}
+
+int64_t ld_for(int64_t rows, int fmt) {
+  int64_t per = 16 / fmt_bytes(fmt);
+  return (rows + per - 1) / per * per;
+}
+
+template <class F>
+void parallel_for(int64_t count, int threads, F&& fn) {
+  if (count <= 0) return;
+  int nt = threads > 0 ? threads : static_cast<int>(std::thread::hardware_concurrency());
+  if (nt <= 0) nt = 1;
+  nt = static_cast<int>(std::min<int64_t>(nt, count));
+  std::atomic<int64_t> next{0};
+  std::exception_ptr err;
+  std::atomic<bool> failed{false};
+  auto work = [&]() {
+    for (;;) {
+      int64_t t = next.fetch_add(1);
+      if (t >= count || failed.load()) return;
+      try {
+        fn(t);
+      } catch (...) {
+        if (!failed.exchange(true)) err = std::current_exception();
+        return;
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int i = 1; i < nt; ++i) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  if (err) std::rethrow_exception(err);
+}
+
+struct FactorRef {
+  LRBlock meta;      // everything but exponents, offsets and leading dims
+  const double* U;   // m x k column-major (ld = m), the H~ factor
+  const double* V;   // n x k column-major (ld = n)
+};
+
+// Lay out the factor arena grouped by format (fp64 first, 256-byte aligned
+// factors, leading dimensions padded to 16 bytes) and store every factor in
+// its format with a power-of-two scale.
+void layout_and_store(const std::vector<FactorRef>& refs, int threads, HostMatrix& h) {
+  std::vector<size_t> by_fmt(refs.size());
+  std::iota(by_fmt.begin(), by_fmt.end(), 0);
+  std::stable_sort(by_fmt.begin(), by_fmt.end(),
+                   [&](size_t a, size_t b) { return refs[a].meta.fmt < refs[b].meta.fmt; });
+  h.lr.resize(refs.size());
+  int64_t pos = 0;
+  for (size_t t : by_fmt) {
+    LRBlock& B = h.lr[t];
+    B = refs[t].meta;
+    B.ldu = ld_for(B.m, B.fmt);
+    B.ldv = ld_for(B.n, B.fmt);
+    const int sz = fmt_bytes(B.fmt);
+    B.u_off = pos;
+    pos += (B.ldu * B.k * sz + 255) / 256 * 256;
+    B.v_off = pos;
+    pos += (B.ldv * B.k * sz + 255) / 256 * 256;
+  }
+  h.arena.assign(static_cast<size_t>(pos), 0);
+  parallel_for(static_cast<int64_t>(refs.size()), threads, [&](int64_t t) {
+    LRBlock& B = h.lr[t];
+    const int sz = fmt_bytes(B.fmt);
+    auto put = [&](const double* A, int64_t rows, int64_t off, int64_t ld, int32_t& expo) {
+      double mx = 0.0;
+      for (int64_t q = 0; q < rows * B.k; ++q) mx = std::max(mx, std::fabs(A[q]));
+      expo = scale_exponent(mx, B.fmt);
+      for (int64_t c = 0; c < B.k; ++c)
+        for (int64_t r = 0; r < rows; ++r) {
+          double v = round_to(std::ldexp(A[r + c * rows], -expo), B.fmt);
+          store_value(&h.arena[off + (r + c * ld) * sz], v, B.fmt);
+        }
+    };
+    put(refs[t].U, B.m, B.u_off, B.ldu, B.exp_u);
+    put(refs[t].V, B.n, B.v_off, B.ldv, B.exp_v);
+  });
+}
+
+}  // namespace
+
+void build(const double* points, int64_t n, int dim, const BuildParams& p, HostMatrix& h) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (n < 1 || dim < 1 || dim > 3) throw std::invalid_argument("need n >= 1 and 1 <= dim <= 3");
+  if (n > (int64_t(1) << 31) - 64) throw std::invalid_argument("n too large for 32-bit positions");
+  if (p.leaf < 1) throw std::invalid_argument("leaf_size must be >= 1");
+  if (!(p.eta > 0)) throw std::invalid_argument("eta must be > 0");
+  if (!(p.tol > 0 && p.tol < 1)) throw std::invalid_argument("tol must be in (0, 1)");
+  if (p.kernel < 0 || p.kernel > 4) throw std::invalid_argument("unknown kernel");
+  if (!(p.kparam > 0)) throw std::invalid_argument("kernel_param must be > 0");
+  if (p.fmt_mask & ~31u) throw std::invalid_argument("unknown format bits in fmt_mask");
+  for (int64_t i = 0; i < n * dim; ++i)
+    if (!std::isfinite(points[i])) throw std::invalid_argument("points must be finite");
+  h = HostMatrix();
+  h.n = n;
+  h.dim = dim;
+  h.leaf = p.leaf;
+  h.kernel = p.kernel;
+  h.eta = p.eta;
+  h.tol = p.tol;
+  h.kparam = p.kparam;
+  h.fmt_mask = p.fmt_mask | 1u;
+  h.seed = p.seed;
+  h.points.assign(points, points + n * dim);
+  build_tree(points, n, dim, p.leaf, h);
+  if (h.L + 1 > 47) throw std::invalid_argument("tree too deep");
+  int ell = p.ell < 0 ? h.L / 2 : p.ell;
+  if (ell > h.L) throw std::domain_error("switch level exceeds the tree depth L");
+  h.ell = ell;
+
+  std::vector<Pair> lrp, dnp;
+  hybrid_partition(h, p.eta, ell, lrp, dnp);
+
+  std::vector<double> tp(static_cast<size_t>(n * dim));
+  for (int64_t q = 0; q < n; ++q)
+    for (int d = 0; d < dim; ++d) tp[q * dim + d] = points[int64_t(h.perm[q]) * dim + d];
+  Geometry g{tp.data(), dim, p.kernel, p.kparam};
+  auto rng = [&](int level, int i, int64_t& off, int64_t& size) {
+    int64_t node = (int64_t(1) << level) - 1 + i;
+    off = h.node_off[node];
+    size = h.node_size[node];
+  };
+
+  // Algorithm 1: compress the admissible blocks (and, when ell == L, the
+  // leaf neighbours, to decide Section 4.3's special case)
+  std::vector<Pair> jobs = lrp;
+  std::vector<size_t> nbr_idx;
+  for (size_t d = 0; d < dnp.size(); ++d)
+    if (dnp[d].kind == KIND_NBR) {
+      nbr_idx.push_back(d);
+      jobs.push_back(dnp[d]);
+    }
+  std::vector<Compressed> comp(jobs.size());
+  std::vector<int64_t> order(jobs.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::vector<double> cost(jobs.size());
+  for (size_t b = 0; b < jobs.size(); ++b) {
+    int64_t o1, m, o2, nn;
+    rng(jobs[b].level, jobs[b].i, o1, m);
+    rng(jobs[b].level, jobs[b].j, o2, nn);
+    cost[b] = double(m) * double(nn);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+  parallel_for(static_cast<int64_t>(jobs.size()), p.threads, [&](int64_t t) {
+    const Pair& q = jobs[order[t]];
+    int64_t o1, m, o2, nn;
+    rng(q.level, q.i, o1, m);
+    rng(q.level, q.j, o2, nn);
+    compress_block(g, o1, m, o2, nn, p.tol, comp[order[t]]);
+  });
+
+  // dense blocks (diagonal; with ell == L also the leaf neighbours)
+  std::vector<std::vector<double>> dvals(dnp.size());
+  parallel_for(static_cast<int64_t>(dnp.size()), p.threads, [&](int64_t d) {
+    int64_t o1, m, o2, nn;
+    rng(dnp[d].level, dnp[d].i, o1, m);
+    rng(dnp[d].level, dnp[d].j, o2, nn);
+    dvals[d].resize(static_cast<size_t>(m * nn));
+    for (int64_t c = 0; c < nn; ++c)
+      for (int64_t r = 0; r < m; ++r) dvals[d][r + c * m] = g.entry(o1 + r, o2 + c);
+  });
+
+  // Algorithm 5: ||H~||^2 = sum trace(Sigma^2) + sum ||H_II||^2 (+ dense neighbours)
+  std::vector<double> bnorm(jobs.size());
+  double norm2 = 0.0;
+  for (size_t b = 0; b < lrp.size(); ++b) {
+    double s2 = 0.0;
+    for (double s : comp[b].s) s2 += s * s;
+    bnorm[b] = std::sqrt(s2);
+    norm2 += s2;
+  }
+  for (size_t b = lrp.size(); b < jobs.size(); ++b) {
+    double s2 = 0.0;
+    for (double s : comp[b].s) s2 += s * s;
+    bnorm[b] = std::sqrt(s2);
+  }
+  for (size_t d = 0; d < dnp.size(); ++d) {
+    double s2 = 0.0;
+    for (double v : dvals[d]) s2 += v * v;
+    norm2 += s2;
+  }
+  h.norm_ht = std::sqrt(norm2);
+
+  // Algorithm 3: format of every admissible block; Section 4.3 for ell == L
+  struct Chosen {
+    size_t job;
+    int fmt;
+  };
+  std::vector<Chosen> keep;
+  for (size_t b = 0; b < lrp.size(); ++b)
+    keep.push_back({b, choose_format(block_tau(p.tol, lrp[b].level, bnorm[b], h.norm_ht), h.fmt_mask)});
+  std::vector<char> dense_keep(dnp.size(), 1);
+  for (size_t q = 0; q < nbr_idx.size(); ++q) {
+    size_t b = lrp.size() + q;
+    int64_t o1, m, o2, nn;
+    rng(jobs[b].level, jobs[b].i, o1, m);
+    rng(jobs[b].level, jobs[b].j, o2, nn);
+    int f = choose_format(block_tau(p.tol, jobs[b].level, bnorm[b], h.norm_ht), h.fmt_mask);
+    const int64_t pk = comp[b].U.n;
+    if (double(pk) * double(m + nn) * fmt_bits(f) / 64.0 < double(m) * double(nn)) {
+      keep.push_back({b, f});
+      dense_keep[nbr_idx[q]] = 0;
+    }
+  }
+
+  std::vector<FactorRef> refs(keep.size());
+  for (size_t t = 0; t < keep.size(); ++t) {
+    const Chosen& c = keep[t];
+    const Pair& q = jobs[c.job];
+    LRBlock B;
+    std::memset(&B, 0, sizeof(B));
+    B.level = q.level;
+    B.kind = c.job < lrp.size() ? q.kind : KIND_NBR;
+    B.i = q.i;
+    B.j = q.j;
+    rng(q.level, q.i, B.row_off, B.m);
+    rng(q.level, q.j, B.col_off, B.n);
+    B.k = static_cast<int32_t>(comp[c.job].U.n);
+    B.fmt = c.fmt;
+    B.norm = bnorm[c.job];
+    refs[t] = {B, comp[c.job].U.a.data(), comp[c.job].V.a.data()};
+  }
+  layout_and_store(refs, p.threads, h);
+
+  int64_t dpos = 0;
+  for (size_t d = 0; d < dnp.size(); ++d) {
+    if (!dense_keep[d]) continue;
+    DenseBlock D;
+    std::memset(&D, 0, sizeof(D));
+    D.level = dnp[d].level;
+    D.i = dnp[d].i;
+    D.j = dnp[d].j;
+    rng(D.level, D.i, D.row_off, D.m);
+    rng(D.level, D.j, D.col_off, D.n);
+    D.d_off = dpos;
+    dpos += D.m * D.n;
+    h.dense.push_back(D);
+    h.dense_data.insert(h.dense_data.end(), dvals[d].begin(), dvals[d].end());
+  }
+  h.build_seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+void reencode(const HostMatrix& src, uint32_t fmt_mask, int threads, HostMatrix& h) {
+  if (fmt_mask & ~31u) throw std::invalid_argument("unknown format bits in fmt_mask");
+  if (src.ell == src.L && src.L > 0)
+    throw std::domain_error("re-encoding needs ell < L (with ell == L the dense/low-rank choice depends on the format)");
+  for (const LRBlock& b : src.lr)
+    if (b.fmt != F64 || b.exp_u != 0 || b.exp_v != 0)
+      throw std::invalid_argument("re-encoding needs a matrix stored in uniform fp64");
+  h = src;
+  h.fmt_mask = fmt_mask | 1u;
+  h.lr.clear();
+  h.arena.clear();
+  // unpack the exact fp64 factors, then apply Algorithm 3 with the new set U
+  std::vector<std::vector<double>> fac(2 * src.lr.size());
+  std::vector<FactorRef> refs(src.lr.size());
+  for (size_t t = 0; t < src.lr.size(); ++t) {
+    const LRBlock& b = src.lr[t];
+    fac[2 * t].resize(static_cast<size_t>(b.m * b.k));
+    fac[2 * t + 1].resize(static_cast<size_t>(b.n * b.k));
+    for (int64_t c = 0; c < b.k; ++c) {
+      std::memcpy(&fac[2 * t][c * b.m], &src.arena[b.u_off + c * b.ldu * 8], 8 * b.m);
+      std::memcpy(&fac[2 * t + 1][c * b.n], &src.arena[b.v_off + c * b.ldv * 8], 8 * b.n);
+    }
+    LRBlock B = b;
+    B.fmt = choose_format(block_tau(src.tol, b.level, b.norm, src.norm_ht), h.fmt_mask);
+    refs[t] = {B, fac[2 * t].data(), fac[2 * t + 1].data()};
+  }
+  layout_and_store(refs, threads, h);
+}
+
+Summary summarize(const HostMatrix& h) {
+  Summary s;
+  s.csp.assign(static_cast<size_t>(h.L) + 1, 0);
+  std::vector<std::vector<int32_t>> cnt(static_cast<size_t>(h.L) + 1);
+  for (int l = 0; l <= h.L; ++l) cnt[l].assign(size_t(1) << l, 0);
+  for (const LRBlock& b : h.lr) {
+    s.blocks_per_fmt[b.fmt] += 1;
+    const int64_t fb = (b.m + b.n) * int64_t(b.k) * fmt_bytes(b.fmt);
+    s.bytes_per_fmt[b.fmt] += fb;
+    s.u_bytes += b.m * int64_t(b.k) * fmt_bytes(b.fmt);
+    s.v_bytes += b.n * int64_t(b.k) * fmt_bytes(b.fmt);
+    s.max_rank = std::max<int64_t>(s.max_rank, b.k);
+    s.storage_amp += double(b.k) * double(b.m + b.n) * fmt_bits(b.fmt) / 64.0;
+    s.storage_fp64 += double(b.k) * double(b.m + b.n);
+    s.bytes_per_matvec += double(fb);
+    s.flops_per_matvec += 2.0 * double(b.k) * double(b.m + b.n);
+    if (b.level <= h.L) cnt[b.level][b.i] += 1;
+    if (b.fmt != F64) {
+      double u = unit_roundoff(b.fmt);
+      double e = (2.0 + std::sqrt(double(b.k)) * u) * u * b.norm;
+      s.bound_round += e * e;
+    }
+  }
+  for (const DenseBlock& d : h.dense) {
+    s.dense_bytes += 8 * d.m * d.n;
+    s.storage_amp += double(d.m) * double(d.n);
+    s.storage_fp64 += double(d.m) * double(d.n);
+    s.bytes_per_matvec += 8.0 * double(d.m) * double(d.n);
+    s.flops_per_matvec += 2.0 * double(d.m) * double(d.n);
+  }
+  s.bytes_per_matvec += 16.0 * double(h.n);  // x read once, y written once
+  double sum = 0.0;
+  for (int l = 0; l <= h.L; ++l) {
+    for (int32_t c : cnt[l]) s.csp[l] = std::max(s.csp[l], c);
+    sum += s.csp[l];
+  }
+  s.bound42 = (2.0 * std::sqrt(sum) + 1.0) * h.tol;
+  s.bound44 = 2.0 * s.bound42;
+  s.bound_round = h.norm_ht > 0 ? std::sqrt(s.bound_round) / h.norm_ht : 0.0;
+  return s;
+}
+
+}  // namespace hh

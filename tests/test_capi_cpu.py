@@ -1,0 +1,141 @@
+"""C-ABI library checks that need no GPU: it loads, exports every entry
+point declared in include/hh.h, rejects bad arguments with the documented
+codes, and its host builder agrees with the oracle's construction."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import hh_workloads as W
+from oracle import bounds as BD
+from oracle import build as OB
+from oracle import hhfile
+from oracle import matvec as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ALL = W.F64 | W.F32 | W.F16 | W.BF16 | W.E4M3
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2604_09147_gb300 import build as b
+    b.build()
+    import paper_2604_09147_gb300 as pkg
+    return pkg
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hh.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hh_[a-z_A-Z0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(P):
+    import ctypes
+    lib = ctypes.CDLL(P.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_argument_errors(P):
+    pts = W.points(300, 3, 1)
+    with pytest.raises(P.HHError) as e:
+        P.HMatrix.build(pts, tol=0.0, device=-1)
+    assert e.value.code == P.HH_EINVAL
+    with pytest.raises(P.HHError) as e:
+        P.HMatrix.build(np.zeros((10, 4)), device=-1)
+    assert e.value.code == P.HH_EINVAL
+    with pytest.raises(P.HHError) as e:
+        P.HMatrix.build(pts, leaf_size=32, switch_level=9, device=-1)       # L = 4 < 9
+    assert e.value.code == P.HH_ENOTSUP
+    with pytest.raises(P.HHError) as e:
+        P.HMatrix.build(pts, kernel=7, device=-1)
+    assert e.value.code == P.HH_EINVAL
+    H = P.HMatrix.build(pts, leaf_size=32, device=-1)
+    with pytest.raises(P.HHError) as e:
+        H.matvec_host(np.zeros(300))
+    assert e.value.code == P.HH_ENOTSUP
+    with pytest.raises(P.HHError) as e:
+        P.HMatrix.load("/nonexistent/file.hhm", device=-1)
+    assert e.value.code == P.HH_EIO
+
+
+def test_corrupt_file_is_rejected(P, tmp_path):
+    H = P.HMatrix.build(W.points(500, 2, 2), kernel=W.EXP, leaf_size=32, device=-1)
+    path = str(tmp_path / "a.hhm")
+    H.save(path)
+    data = bytearray(open(path, "rb").read())
+    bad = str(tmp_path / "b.hhm")
+    open(bad, "wb").write(bytes(data[:-5]))                  # truncated
+    with pytest.raises(P.HHError):
+        P.HMatrix.load(bad, device=-1)
+    d2 = bytearray(data)
+    d2[0] = ord("X")                                          # bad magic
+    open(bad, "wb").write(bytes(d2))
+    with pytest.raises(P.HHError) as e:
+        P.HMatrix.load(bad, device=-1)
+    assert e.value.code == P.HH_EINVAL
+
+
+@pytest.mark.parametrize("n,dim,kernel,param,leaf,ell,tol,mask", [
+    (4096, 2, W.EXP, 1.0, 64, 3, 1e-8, W.F64),                 # the plain small workload
+    (3000, 3, W.INV_R, 1.0, 64, 2, 1e-3, ALL),
+    (2048, 3, W.GAUSS, 0.01, 64, 3, 1e-4, ALL),
+    (2048, 2, W.LOG, 1.0, 64, 0, 1e-5, W.F64 | W.F32 | W.BF16),   # HODLR special case
+    (2048, 2, W.EXP, 1.0, 64, 5, 1e-2, ALL),                  # H_s special case (ell = L)
+])
+def test_host_builder_matches_oracle(P, tmp_path, n, dim, kernel, param, leaf, ell, tol, mask):
+    pts = W.points(n, dim, 77)
+    H = P.HMatrix.build(pts, kernel, param, leaf, 1.0, ell, tol, mask, device=-1)
+    path = str(tmp_path / "h.hhm")
+    H.save(path)
+    G = hhfile.read(path)
+    O = OB.build(pts, kernel, param, leaf, 1.0, ell, tol, mask)
+    assert np.array_equal(G.perm, O.perm)
+    kg = {(b.level, b.i, b.j): b for b in G.lowrank}
+    ko = {(b.level, b.i, b.j): b for b in O.lowrank}
+    if ell < O.L:
+        assert set(kg) == set(ko)                              # identical partition
+        assert {(d.i, d.j) for d in G.dense} == {(d.i, d.j) for d in O.dense}
+        assert max(abs(kg[k].k - ko[k].k) for k in ko) <= 2   # ranks within +-2
+        agree = np.mean([kg[k].fmt == ko[k].fmt for k in ko])
+        assert agree >= 0.99
+    assert H.info()["norm_ht"] == pytest.approx(O.norm_Ht, rel=10 * tol)
+    # the builder's factors meet the paper's bound against the exact matrix
+    Hd = M.dense_h(pts, kernel, param)
+    err = np.linalg.norm(Hd - M.dense_hhat(G)) / np.linalg.norm(Hd)
+    assert err <= H.info()["bound_thm42"]
+    assert H.info()["bound_thm42"] == pytest.approx(BD.thm42_measured(G), rel=1e-12)
+
+
+def test_oracle_written_file_roundtrips_through_library(P, tmp_path):
+    pts = W.points(2500, 3, 9)
+    O = OB.build(pts, W.GAUSS, 0.02, 64, 1.0, 3, 1e-3, ALL)
+    a = str(tmp_path / "o.hhm")
+    b = str(tmp_path / "l.hhm")
+    hhfile.write(O, a)
+    H = P.HMatrix.load(a, device=-1)
+    H.save(b)
+    assert open(a, "rb").read() == open(b, "rb").read()
+    inf = H.info()
+    assert inf["n_lowrank"] == len(O.lowrank) and inf["n_dense"] == len(O.dense)
+    assert inf["storage_amp"] == pytest.approx(O.storage(), rel=1e-12)
+    assert inf["storage_fp64"] == pytest.approx(O.storage(True), rel=1e-12)
+
+
+def test_reencode_equals_direct_build(P, tmp_path):
+    pts = W.points(3000, 3, 4)
+    A = P.HMatrix.build(pts, W.INV_R, 1.0, 64, 1.0, 3, 1e-3, W.F64, device=-1)
+    B = P.HMatrix.build(pts, W.INV_R, 1.0, 64, 1.0, 3, 1e-3, ALL, device=-1)
+    C = A.reencode(ALL)
+    B.save(str(tmp_path / "b.hhm"))
+    C.save(str(tmp_path / "c.hhm"))
+    gb, gc = hhfile.read(str(tmp_path / "b.hhm")), hhfile.read(str(tmp_path / "c.hhm"))
+    x = W.rhs(3000, 2, "uniform", 1)
+    assert np.array_equal(M.matvec(gb, x), M.matvec(gc, x))
+    assert B.info()["blocks_per_fmt"] == C.info()["blocks_per_fmt"]
+    with pytest.raises(P.HHError):
+        B.reencode(W.F64)                                      # source not uniform fp64

@@ -1,0 +1,200 @@
+"""GPU parity: the CUDA path through the C-ABI against the oracle.
+
+Tolerances:
+  * fp64-stored factors and dense blocks are computed in fp64 on the GPU:
+    ||y_gpu - y_oracle|| / ||y_oracle|| <= 1e-12 over the same stored factors.
+  * 32/16/8-bit factors are computed with fp32 accumulation (input rounded to
+    fp32, products and sums in fp32, fp64 scatter):
+    ||y_gpu - y_oracle|| / ||y_oracle|| <= 1e-6 over the same stored factors,
+    and against the exact kernel matrix the backward error
+    ||H x - y|| / (||H|| ||x||) stays within Theorem 4.4's bound + 1e-6.
+The oracle either builds the matrix itself and writes the file the library
+loads (hh_load), or reads the file the library's host builder wrote.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import hh_workloads as W
+from oracle import build as OB
+from oracle.compress import kernel_entries
+from oracle import hhfile
+from oracle import matvec as M
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+ALL = W.F64 | W.F32 | W.F16 | W.BF16 | W.E4M3
+CACHE = os.environ.get("HH_CACHE_DIR", "/tmp/hh_cache")
+TOL64, TOL32 = 1e-12, 1e-6
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_09147_gb300 import build as b
+    b.build()
+    import paper_2604_09147_gb300 as pkg
+    return pkg
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def oracle_pair(P, tmp_path, pts, kernel, param, leaf, ell, tol, mask):
+    O = OB.build(pts, kernel, param, leaf, 1.0, ell, tol, mask)
+    path = str(tmp_path / "o.hhm")
+    hhfile.write(O, path)
+    return O, P.HMatrix.load(path, 0)
+
+
+def check_against(P, H, O, x, tol):
+    y = H.matvec(gpu(x)).cpu().numpy()
+    assert rel(y, M.matvec(O, x)) <= tol
+    z = H.matvec(gpu(x), transpose=True).cpu().numpy()
+    assert rel(z, M.matvec_T(O, x)) <= tol
+    H.sync_status()
+
+
+def test_fp64_path_matches_oracle_file(P, tmp_path):
+    c = W.CONFIGS["plain_small"]
+    pts = W.config_points("plain_small")
+    O, H = oracle_pair(P, tmp_path, pts, c["kernel"], c["kernel_param"], c["leaf"], c["ell"], c["tol"], W.F64)
+    x = W.config_rhs("plain_small")
+    check_against(P, H, O, x[:, 0], TOL64)
+    # several right-hand sides with a leading dimension larger than n
+    for nrhs in (2, 3, 4, 5, 8):
+        xs = W.rhs(len(pts), nrhs, "uniform", 100 + nrhs)
+        buf = torch.zeros((nrhs, len(pts) + 7), dtype=torch.float64, device="cuda")
+        buf[:, :len(pts)] = gpu(xs.T)
+        xv = buf.t()[:len(pts)]
+        assert xv.stride(1) == len(pts) + 7
+        y = H.matvec(xv).cpu().numpy()
+        assert rel(y, M.matvec(O, xs)) <= TOL64
+
+
+@pytest.mark.parametrize("n,dim,kernel,param,ell,tol", [(8192, 3, W.GAUSS, 0.01, 4, 1e-3),
+                                                        (6000, 3, W.INV_R, 1.0, 3, 1e-2),
+                                                        (5000, 2, W.LOG, 1.0, 3, 1e-4)])
+def test_adaptive_formats_match_oracle_file(P, tmp_path, n, dim, kernel, param, ell, tol):
+    pts = W.points(n, dim, 5)
+    O, H = oracle_pair(P, tmp_path, pts, kernel, param, 64, ell, tol, ALL)
+    used = {b.fmt for b in O.lowrank}
+    assert len(used) >= 3
+    x = W.rhs(n, 1, "uniform", 6)[:, 0]
+    check_against(P, H, O, x, TOL32)
+    xs = W.rhs(n, 4, "normal", 7)
+    assert rel(H.matvec(gpu(xs)).cpu().numpy(), M.matvec(O, xs)) <= TOL32
+
+
+@pytest.mark.parametrize("n,dim,leaf,ell,mask", [
+    (50, 2, 64, -1, W.F64),            # one dense block (L = 0)
+    (5000, 3, 128, 3, ALL),            # ragged cluster sizes
+    (3001, 2, 64, 0, W.F64 | W.F32),   # HODLR (ell = 0), odd n
+    (2048, 2, 64, 5, ALL),             # H_s (ell = L) with neighbour blocks
+    (129, 3, 128, 1, W.F64),           # two leaves of 64 / 65 points
+])
+def test_edge_cases(P, tmp_path, n, dim, leaf, ell, mask):
+    pts = W.points(n, dim, 8)
+    kernel = W.EXP if dim == 2 else W.INV_R
+    O, H = oracle_pair(P, tmp_path, pts, kernel, 1.0, leaf, ell, 1e-4, mask)
+    x = W.rhs(n, 1, "uniform", 9)[:, 0]
+    tol = TOL64 if mask == W.F64 else TOL32
+    check_against(P, H, O, x, tol)
+    assert np.all(H.matvec(torch.zeros(n, dtype=torch.float64, device="cuda")).cpu().numpy() == 0)
+
+
+def test_library_builder_plain_small(P, tmp_path):
+    """hh_build on the plain small workload; oracle reads the saved factors."""
+    c = W.CONFIGS["plain_small"]
+    pts = W.config_points("plain_small")
+    H = P.HMatrix.build(pts, c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"], c["tol"], c["fmts"], device=0)
+    path = str(tmp_path / "b.hhm")
+    H.save(path)
+    G = hhfile.read(path)
+    x = W.config_rhs("plain_small")[:, 0]
+    y = H.matvec(gpu(x)).cpu().numpy()
+    assert rel(y, M.matvec(G, x)) <= TOL64
+    Hd = M.dense_h(pts, c["kernel"], c["kernel_param"])
+    bx = Hd @ x
+    inf = H.info()
+    assert np.linalg.norm(bx - y) / (np.linalg.norm(Hd) * np.linalg.norm(x)) <= inf["bound_thm44"]
+    assert rel(y, bx) <= 50 * c["tol"]
+
+
+@pytest.fixture(scope="module")
+def adaptive_65k(P):
+    c = W.CONFIGS["adaptive_65k"]
+    pts = W.config_points("adaptive_65k")
+    H64 = P.HMatrix.build_cached(pts, CACHE, c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"],
+                                 c["tol"], W.F64, device=0)
+    Ham = H64.reencode(c["fmts"], 0)
+    return c, pts, H64, Ham
+
+
+def test_full_size_adaptive_65k(P, adaptive_65k, tmp_path):
+    """Full size, bench launch configuration: both layouts against the oracle
+    over the same stored factors, and the backward error on sampled rows."""
+    c, pts, H64, Ham = adaptive_65k
+    x = W.config_rhs("adaptive_65k")[:, 0]
+    for H, tol in ((H64, TOL64), (Ham, TOL32)):
+        path = str(tmp_path / "f.hhm")
+        H.save(path)
+        G = hhfile.read(path)
+        y = H.matvec(gpu(x)).cpu().numpy()
+        yo = M.matvec(G, x)
+        assert rel(y, yo) <= tol
+        z = H.matvec(gpu(x), transpose=True).cpu().numpy()
+        assert rel(z, M.matvec_T(G, x)) <= tol
+        del G
+    # backward error against the exact kernel on 1024 sampled rows
+    rows = np.random.default_rng(0).choice(len(pts), 1024, replace=False)
+    y = Ham.matvec(gpu(x)).cpu().numpy()
+    bx = M.h_rows_times(pts, c["kernel"], c["kernel_param"], rows, x)
+    # ||H||_F estimated from the same rows (unbiased for uniform sampling)
+    hn = 0.0
+    for s in range(0, len(rows), 128):
+        blk = kernel_entries(c["kernel"], c["kernel_param"], pts[rows[s:s + 128]], pts)
+        hn += float(np.sum(blk * blk))
+    hn = np.sqrt(hn * len(pts) / len(rows))
+    be = np.linalg.norm(bx - y[rows]) * np.sqrt(len(pts) / len(rows)) / (hn * np.linalg.norm(x))
+    assert be <= Ham.info()["bound_thm44"] + 1e-6
+
+
+def test_autograd_backward_is_transpose(P, tmp_path):
+    pts = W.points(4000, 3, 12)
+    O, H = oracle_pair(P, tmp_path, pts, W.EXP, 1.0, 64, 3, 1e-5, W.F64 | W.F32 | W.BF16)
+    x = gpu(W.rhs(4000, 1, "uniform", 1)[:, 0]).requires_grad_(True)
+    ybar = W.rhs(4000, 1, "normal", 2)[:, 0]
+    y = P.hh_apply(H, x)
+    y.backward(gpu(ybar))
+    assert rel(x.grad.cpu().numpy(), M.matvec_T(O, ybar)) <= TOL32
+    # adjoint identity on 16 random directions
+    for k in range(16):
+        d = W.rhs(4000, 1, "uniform", 50 + k)[:, 0]
+        lhs = float(np.dot(ybar, H.matvec(gpu(d)).cpu().numpy()))
+        rhs = float(np.dot(H.matvec(gpu(ybar), transpose=True).cpu().numpy(), d))
+        assert abs(lhs - rhs) <= 1e-6 * abs(lhs) + 1e-12
+
+
+def test_host_api_and_batched(P, tmp_path):
+    mats, xs, oracles = [], [], []
+    for i, n in enumerate((2100, 3333, 1500)):
+        pts = W.points(n, 2 + i % 2, 20 + i)
+        O, H = oracle_pair(P, tmp_path, pts, W.EXP if i % 2 == 0 else W.INV_R, 1.0, 64, -1, 1e-6,
+                           W.F64 | W.F32 | W.F16 | W.BF16)
+        mats.append(H)
+        oracles.append(O)
+        xs.append(W.rhs(n, 1, "uniform", 30 + i)[:, 0])
+    ys = P.matvec_batched(mats, [gpu(x) for x in xs])
+    for H, O, x, y in zip(mats, oracles, xs, ys):
+        assert rel(y.cpu().numpy(), M.matvec(O, x)) <= TOL32
+        assert rel(H.matvec_host(x), M.matvec(O, x)) <= TOL32
+        assert rel(H.matvec_ws(gpu(x)).cpu().numpy(), M.matvec(O, x)) <= TOL32
+        H.sync_status()

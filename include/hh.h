@@ -191,6 +191,25 @@ int hh_matvec_timed(hh_handle h, int transpose, const double* in, double* out, i
 int hh_matvec_batched(const hh_handle* hs, int count, const double* const* xs,
                       double* const* ys, void* stream);
 
+/* hh_matvec_noalloc -- y = A_h x (transpose != 0: A_h^T x) for ONE
+ * right-hand side (x, y device, ld = n) that allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library call.  It is meant for callers
+ * that cannot allocate device memory when they call (a host framework that
+ * owns all device memory, or a loop that must not pay cudaMalloc's implicit
+ * synchronisation).  The paper has no counterpart: this is a deployment
+ * variant of hh_matvec.
+ *   Scratch: a fixed 32 MiB file-scope device array inside the library,
+ *   which every GPU that loads the library holds until the process exits;
+ *   matrices whose scratch (about 40 bytes per point plus 16 to 32 bytes per
+ *   unit of rank) exceeds it are rejected with HH_EINVAL and a message.
+ *   The first call on a device looks up the array's device address (one
+ *   cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the one array: calls that overlap on the GPU (other
+ *   streams, other handles) race and give wrong results; order them on one
+ *   stream.  Everything the product needs zeroed is cleared by each call.
+ *   Asynchronous on `stream`; errors as for hh_matvec. */
+int hh_matvec_noalloc(hh_handle h, int transpose, const double* in, double* out, void* stream);
+
 /* hh_sync_status -- synchronise `stream` and report the device status word
  * of the handle (HH_EDEVICE if a kernel recorded an anomaly). */
 int hh_sync_status(hh_handle h, void* stream);

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <exception>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -580,3 +581,103 @@ void hh_free(hh_handle h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free product (hh_matvec_noalloc, see include/hh.h).
+//
+// Some callers cannot allocate device memory at call time: a host framework
+// that owns every device allocation (a serving runtime with a fixed memory
+// budget, a plugin host), or a latency-critical loop in which cudaMalloc's
+// implicit device synchronisation is not acceptable.  For them the product's
+// scratch (shifted input copies, output accumulator, t arenas for one
+// right-hand side) lives in one fixed file-scope device array that every GPU
+// holds from the moment it loads this library until the process exits.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB per device
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};  // device address of g_noalloc_scratch per device
+
+// Device address of the scratch array on the current device (looked up once
+// per device; host code must not use the symbol itself as an address).
+int noalloc_scratch(int device, void** ptr) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return fail(HH_ENOTSUP, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(HH_ECUDA, std::string("cudaGetSymbolAddress(scratch) failed: ") + cudaGetErrorString(e));
+    g_noalloc_addr[device] = p;
+  }
+  *ptr = g_noalloc_addr[device];
+  return HH_OK;
+}
+
+}  // namespace
+
+extern "C" int hh_matvec_noalloc(hh_handle h, int transpose, const double* in, double* out, void* stream) {
+  if (!h || !in || !out) return fail(HH_EINVAL, "null argument");
+  // scratch for one right-hand side, in the layout of the handle workspace
+  const int64_t npad = (h->H.n + 32 + 3) / 4 * 4;
+  int64_t t32 = 0, t64 = 0;
+  for (const hh::LRBlock& b : h->H.lr) (b.fmt == hh::F64 ? t64 : t32) += b.k;
+  const size_t need = align256(sizeof(float) * 4 * npad) + align256(sizeof(double) * 2 * npad) +
+                      align256(sizeof(double) * npad) +
+                      align256(sizeof(float) * std::max<int64_t>(1, t32 * hh::dev::kMaxNR)) +
+                      align256(sizeof(double) * std::max<int64_t>(1, t64 * hh::dev::kMaxNR));
+  if (need > kNoAllocScratchBytes)
+    return fail(HH_EINVAL, "hh_matvec_noalloc: this matrix needs " + std::to_string(need) +
+                               " bytes of scratch, more than the fixed " +
+                               std::to_string(kNoAllocScratchBytes) + " bytes; use hh_matvec or hh_matvec_ws");
+  if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data (built with device = -1)");
+  const char* a0 = (const char*)in;
+  const char* b0 = (const char*)out;
+  const size_t span = (size_t)h->H.n * sizeof(double);
+  if (a0 < b0 + span && b0 < a0 + span) return fail(HH_EINVAL, "input and output overlap");
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != h->device && cudaSetDevice(h->device) != cudaSuccess) return fail(HH_ECUDA, "cudaSetDevice failed");
+  void* base = nullptr;
+  int rc = noalloc_scratch(h->device, &base);
+  if (rc == HH_OK) {
+    char* p = (char*)base;
+    float* xs = (float*)p;
+    p += align256(sizeof(float) * 4 * npad);
+    double* xs64 = (double*)p;
+    p += align256(sizeof(double) * 2 * npad);
+    double* acc = (double*)p;
+    p += align256(sizeof(double) * npad);
+    float* tt32 = (float*)p;
+    p += align256(sizeof(float) * std::max<int64_t>(1, t32 * hh::dev::kMaxNR));
+    double* tt64 = (double*)p;
+    const int dir = transpose ? 1 : 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.blk = h->d_blk[dir];
+    a.dns = h->d_dns[dir];
+    a.nr = 1;
+    a.npad = npad;
+    a.xs = xs;
+    a.xs64 = xs64;
+    a.t32 = tt32;
+    a.t64 = tt64;
+    a.acc = acc;  // cleared by the prep launch on every call
+    a.status = h->d_status;
+    cudaError_t e = hh::dev::launch_prep(in, h->H.n, 1, h->d_perm, h->H.n, npad, xs, xs64, acc, st);
+    for (int phase = 1; phase <= 2 && e == cudaSuccess; ++phase) {
+      a.items = h->d_items[dir][phase - 1];
+      a.n_items = h->n_items[dir][phase - 1];
+      int grid = std::max(1, std::min(h->grid[phase][1], (a.n_items + 7) / 8));
+      e = hh::dev::launch_pass(phase, h->fset, a, grid, st);
+    }
+    if (e == cudaSuccess) e = hh::dev::launch_finish(acc, 1, h->d_perm, h->H.n, npad, out, h->H.n, st);
+    if (e != cudaSuccess) rc = fail(HH_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+  }
+  if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+  return rc;
+}

@@ -38,7 +38,12 @@ CACHE = os.environ.get("HH_CACHE_DIR", "/tmp/hh_cache")
 WORKLOADS = {
     "adaptive_65k": "N=65,536 points U[0,1]^3, kernel 1/r (K(x,x)=0), leaf 128, eta 1, switch level 4, "
                     "tol 1e-6, adaptive {fp64,fp32,fp16,bf16} vs uniform fp64, 1 RHS U(-1,1)",
+    # the same matrix family at N = 16,384 (factors 0.24 GB, still larger
+    # than L2): the size used for full ncu captures
+    "adaptive_16k": "N=16,384 points U[0,1]^3, kernel 1/r (K(x,x)=0), leaf 128, eta 1, switch level 4, "
+                    "tol 1e-6, adaptive {fp64,fp32,fp16,bf16} vs uniform fp64, 1 RHS U(-1,1)",
 }
+WORKLOAD_N = {"adaptive_65k": 65536, "adaptive_16k": 16384}
 
 
 def dist_env():
@@ -105,9 +110,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_matrices(P, torch, rank, ws, dev):
+def build_matrices(P, torch, rank, ws, dev, workload):
     c = W.CONFIGS["adaptive_65k"]
-    pts = W.config_points("adaptive_65k")
+    pts = W.config_points("adaptive_65k", WORKLOAD_N[workload])
     args = (c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"], c["tol"], W.F64)
     if ws > 1 and rank != 0:
         torch.distributed.barrier()       # rank 0 builds the cache file first
@@ -194,20 +199,20 @@ def run_reference(args):
         return 0
     import paper_2604_09147_gb300 as P
     c = W.CONFIGS["adaptive_65k"]
-    pts = W.config_points("adaptive_65k")
+    pts = W.config_points("adaptive_65k", WORKLOAD_N[args.workload])
     H64 = P.HMatrix.build_cached(pts, CACHE, c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"],
                                  c["tol"], W.F64, device=-1)
     Ham = H64.reencode(c["fmts"], -1)
     path = os.path.join(CACHE, "bench_adaptive_ref.hhm")
     Ham.save(path)
-    x = W.config_rhs("adaptive_65k")[:, 0]
+    x = W.config_rhs("adaptive_65k", n=len(pts))[:, 0]
     per_step = max(0.5, 120.0 / max(1, args.steps + args.warmup))
     rate, desc, el = oracle_sample(path, x, per_step * args.steps)
     out = {"impl": "reference", "metric": "H_h matvecs/s (adaptive precision)", "value": rate,
            "unit": "matvec/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1000.0 / rate, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOADS["adaptive_65k"]},
+           "config": {"workload": WORKLOADS[args.workload]},
            "cpu_baseline": {"value": rate, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle",
                             "sample": desc},
            "e2e": {"value": rate, "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -225,9 +230,10 @@ def run_ours(args):
     import paper_2604_09147_gb300 as P
     from paper_2604_09147_gb300 import build as B
     B.build()
-    c, pts, H64, Ham, build_s = build_matrices(P, torch, rank, ws, dev)
+    c, pts, H64, Ham, build_s = build_matrices(P, torch, rank, ws, dev, args.workload)
     n = len(pts)
-    x = torch.from_numpy(W.config_rhs("adaptive_65k")[:, 0].copy()).cuda()
+    xh0 = W.config_rhs("adaptive_65k", n=n)[:, 0]
+    x = torch.from_numpy(xh0.copy()).cuda()
     y = torch.empty_like(x)
     inf, inf64 = Ham.info(), H64.info()
     for _ in range(args.warmup):
@@ -283,7 +289,7 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         path = os.path.join(CACHE, "bench_adaptive.hhm")
         Ham.save(path)
-        rate, desc, _ = oracle_sample(path, W.config_rhs("adaptive_65k")[:, 0], args.cpu_seconds)
+        rate, desc, _ = oracle_sample(path, xh0, args.cpu_seconds)
         cpu = {"value": rate, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
 
     gbs = inf["bytes_per_matvec"] / (ms_amp * 1e-3) / 1e9
@@ -295,7 +301,7 @@ def run_ours(args):
         "dtype": "f32", "dtype_note": "fp32 accumulation for 32/16/8-bit factors, fp64 for fp64 factors, "
                                       "the dense diagonal and the output scatter",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS["adaptive_65k"], "n": n, "nrhs": 1, "parallelism": f"replicas x{ws}",
+        "config": {"workload": WORKLOADS[args.workload], "n": n, "nrhs": 1, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (factor bytes %.2f GB adaptive / %.2f GB fp64 per step)"
                          % (inf["bytes_per_matvec"] / 1e9, inf64["bytes_per_matvec"] / 1e9)},
         "gbs": gbs, "hbm_frac": gbs / hbm,
@@ -323,6 +329,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="adaptive_65k")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU oracle baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

@@ -14,9 +14,11 @@ casts on float32-exact inputs (where torch rounds once).
 
 Block scales (power-of-two, exact): fp16 and e4m3 have a narrow exponent range,
 so a block's factor is scaled so that its largest magnitude lands at most at
-the format's maximum; fp32 and bf16 are scaled so that it lands in [0.5, 1]
-(no overflow risk when upcast products are accumulated in fp32); fp64 blocks
-are not scaled.
+the format's maximum; fp32, bf16 and fp64 are scaled so that it lands in
+(0.5, 1] (no overflow risk when upcast products are accumulated in fp32; an
+fp64 factor then also lies in the fp32 exponent range, where its value can be
+split into two fp32 halves).  Scaling by a power of two changes no value:
+decoded = stored * 2^exponent exactly.
 """
 from __future__ import annotations
 
@@ -41,7 +43,7 @@ _SPEC = {
     E4M3: (3, -6, 448.0),
 }
 # value the largest magnitude of a scaled factor may reach
-SCALE_TARGET = {FP32: 1.0, BF16: 1.0, FP16: 65504.0, E4M3: 448.0}
+SCALE_TARGET = {FP64: 1.0, FP32: 1.0, BF16: 1.0, FP16: 65504.0, E4M3: 448.0}
 
 
 def round_to(v: np.ndarray, fmt: int) -> np.ndarray:
@@ -71,8 +73,8 @@ def round_to(v: np.ndarray, fmt: int) -> np.ndarray:
 
 def scale_exponent(maxabs: float, fmt: int) -> int:
     """Power-of-two exponent e so that maxabs * 2^-e <= SCALE_TARGET[fmt] and
-    maxabs * 2^-e > SCALE_TARGET[fmt] / 2 (fp64: always 0; zero block: 0)."""
-    if fmt == FP64 or maxabs == 0.0:
+    maxabs * 2^-e > SCALE_TARGET[fmt] / 2 (zero block: 0)."""
+    if maxabs == 0.0:
         return 0
     t = SCALE_TARGET[fmt]
     _, E = np.frexp(maxabs / t)              # maxabs/t = f * 2^E, f in [0.5, 1)

@@ -266,6 +266,7 @@ struct FmtSpec {
 };
 FmtSpec fmt_spec(int fmt) {
   switch (fmt) {
+    case F64: return {52, -1022, 1.7976931348623157e308, 1.0};
     case F32: return {23, -126, 3.4028234663852886e38, 1.0};
     case F16: return {10, -14, 65504.0, 65504.0};
     case BF16: return {7, -126, 3.3895313892515355e38, 1.0};
@@ -286,8 +287,10 @@ double round_to(double v, int fmt) {
   return r;
 }
 
+// power-of-two scale: every factor's largest magnitude lands in (t/2, t],
+// t = the format's maximum for fp16 / e4m3, 1 for fp32 / bf16 / fp64
 int scale_exponent(double maxabs, int fmt) {
-  if (fmt == F64 || maxabs == 0.0) return 0;
+  if (maxabs == 0.0) return 0;
   const double t = fmt_spec(fmt).target;
   int E;
   std::frexp(maxabs / t, &E);
@@ -617,8 +620,7 @@ void reencode(const HostMatrix& src, uint32_t fmt_mask, int threads, HostMatrix&
   if (src.ell == src.L && src.L > 0)
     throw std::domain_error("re-encoding needs ell < L (with ell == L the dense/low-rank choice depends on the format)");
   for (const LRBlock& b : src.lr)
-    if (b.fmt != F64 || b.exp_u != 0 || b.exp_v != 0)
-      throw std::invalid_argument("re-encoding needs a matrix stored in uniform fp64");
+    if (b.fmt != F64) throw std::invalid_argument("re-encoding needs a matrix stored in uniform fp64");
   h = src;
   h.fmt_mask = fmt_mask | 1u;
   h.lr.clear();
@@ -634,6 +636,8 @@ void reencode(const HostMatrix& src, uint32_t fmt_mask, int threads, HostMatrix&
       std::memcpy(&fac[2 * t][c * b.m], &src.arena[b.u_off + c * b.ldu * 8], 8 * b.m);
       std::memcpy(&fac[2 * t + 1][c * b.n], &src.arena[b.v_off + c * b.ldv * 8], 8 * b.n);
     }
+    for (double& v : fac[2 * t]) v = std::ldexp(v, b.exp_u);       // exact: undo the scales
+    for (double& v : fac[2 * t + 1]) v = std::ldexp(v, b.exp_v);
     LRBlock B = b;
     B.fmt = choose_format(block_tau(src.tol, b.level, b.norm, src.norm_ht), h.fmt_mask);
     refs[t] = {B, fac[2 * t].data(), fac[2 * t + 1].data()};

@@ -16,10 +16,7 @@
 #include "hh_device.h"
 #include "hh_host.h"
 
-using hh::dev::BlkDesc;
-using hh::dev::DenseDesc;
 using hh::dev::Item;
-using hh::dev::PassArgs;
 
 namespace {
 
@@ -50,18 +47,18 @@ struct hh_matrix {
   int64_t npad = 0;
   int64_t t32_elems = 0, t64_elems = 0;  // per right-hand side
   uint8_t* d_arena = nullptr;
-  double* d_dense = nullptr;
   int32_t* d_perm = nullptr;
-  BlkDesc* d_blk[2] = {nullptr, nullptr};
-  DenseDesc* d_dns[2] = {nullptr, nullptr};
-  Item* d_items[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  int n_items[2][2] = {{0, 0}, {0, 0}};
   int* d_status = nullptr;
   void* d_ws = nullptr;
   size_t ws_bytes = 0;
   double* d_stage = nullptr;  // hh_matvec_host staging buffers (2 x n x stage_cols)
   int stage_cols = 0;
-  int grid[3][5] = {};  // [phase][nr]
+  // streaming passes (stream.cu): descriptors and items per [direction][phase]
+  hh::dev::StreamDesc* d_sdesc[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  Item* d_sitems[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int n_sitems[2][2] = {{0, 0}, {0, 0}};
+  double* d_dense_pad = nullptr;  // dense blocks, column-major, ld rounded up to even
+  int sgrid[3][5] = {};
   unsigned fset = hh::dev::kSetAll;  // kernel variant covering the formats present
 };
 
@@ -73,13 +70,13 @@ void free_device(hh_matrix* h) {
   cudaGetDevice(&cur);
   if (cur != h->device) cudaSetDevice(h->device);
   cudaFree(h->d_arena);
-  cudaFree(h->d_dense);
   cudaFree(h->d_perm);
-  for (int d = 0; d < 2; ++d) {
-    cudaFree(h->d_blk[d]);
-    cudaFree(h->d_dns[d]);
-    for (int p = 0; p < 2; ++p) cudaFree(h->d_items[d][p]);
-  }
+  for (int d = 0; d < 2; ++d)
+    for (int p = 0; p < 2; ++p) {
+      cudaFree(h->d_sdesc[d][p]);
+      cudaFree(h->d_sitems[d][p]);
+    }
+  cudaFree(h->d_dense_pad);
   cudaFree(h->d_status);
   cudaFree(h->d_ws);
   cudaFree(h->d_stage);
@@ -101,59 +98,119 @@ int next_pow2_32(int64_t v) {
   return g;
 }
 
-// Work lists of one direction (0: forward, 1: transpose).
-void make_items(const hh::HostMatrix& H, int dir, std::vector<Item>& p1, std::vector<Item>& p2) {
-  struct Costed {
-    Item it;
-    double cost;
-  };
-  std::vector<Costed> c1, c2;
-  for (size_t b = 0; b < H.lr.size(); ++b) {
-    const hh::LRBlock& B = H.lr[b];
-    if (B.k == 0) continue;
-    const int sz = hh::fmt_bytes(B.fmt);
-    const int64_t n1 = dir == 0 ? B.n : B.m;
-    const int64_t n2 = dir == 0 ? B.m : B.n;
-    // phase 1: columns of f1, about 32 KB of factor data per item
-    const int vw1 = 16 / sz;
-    const int C1 = 32 / next_pow2_32((n1 + vw1 - 1) / vw1);
-    int64_t cols = std::max<int64_t>(1, 32768 / std::max<int64_t>(1, n1 * sz));
-    cols = std::max<int64_t>(C1, cols / C1 * C1);
-    for (int64_t j = 0; j < B.k; j += cols) {
-      int64_t hi = std::min<int64_t>(B.k, j + cols);
-      c1.push_back({{0, (int32_t)b, (int32_t)j, (int32_t)hi}, double(hi - j) * double(n1 * sz)});
+// Descriptors and work items of the streaming passes (stream.cu).
+void upload_stream(hh_matrix* h, const std::vector<int64_t>& toff) {
+  using hh::dev::StreamDesc;
+  const hh::HostMatrix& H = h->H;
+  // dense blocks with an even leading dimension (16-byte aligned columns)
+  std::vector<int64_t> doff(H.dense.size());
+  int64_t dtot = 0;
+  for (size_t q = 0; q < H.dense.size(); ++q) {
+    doff[q] = dtot;
+    dtot += ((H.dense[q].m + 1) / 2 * 2) * H.dense[q].n;
+  }
+  // each block scaled by a power of two so that its largest magnitude lies in
+  // (1/2, 1] (exact; the kernels split fp64 values into fp32 halves)
+  std::vector<double> dpad(static_cast<size_t>(dtot), 0.0);
+  std::vector<int32_t> dexp(H.dense.size(), 0);
+  for (size_t q = 0; q < H.dense.size(); ++q) {
+    const hh::DenseBlock& D = H.dense[q];
+    const int64_t ld = (D.m + 1) / 2 * 2;
+    double mx = 0.0;
+    for (int64_t i = 0; i < D.m * D.n; ++i) mx = std::max(mx, std::fabs(H.dense_data[D.d_off + i]));
+    int ex = 0;
+    if (mx > 0.0) {
+      std::frexp(mx, &ex);  // mx = f 2^ex, f in [1/2, 1)
+      while (std::ldexp(mx, -ex) > 1.0) ++ex;
     }
-    // phase 2: rows of f2, one 16-byte vector per lane (8 bytes for e4m3)
-    const int lb = B.fmt == hh::E4M3 ? 8 : 16;
-    const int64_t rows = 32 * (lb / sz);
-    for (int64_t r = 0; r < n2; r += rows) {
-      int64_t hi = std::min<int64_t>(n2, r + rows);
-      c2.push_back({{1, (int32_t)b, (int32_t)r, (int32_t)hi}, double(hi - r) * double(B.k * sz)});
+    dexp[q] = ex;
+    for (int64_t c = 0; c < D.n; ++c)
+      for (int64_t r = 0; r < D.m; ++r)
+        dpad[doff[q] + c * ld + r] = std::ldexp(H.dense_data[D.d_off + c * D.m + r], -ex);
+  }
+  h->d_dense_pad = upload(dpad);
+  const int cols1 = hh::dev::stream_cols_per_item();
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<StreamDesc> desc[2];
+    struct Costed {
+      Item it;
+      double cost;
+    };
+    std::vector<Costed> items[2];
+    auto add_cols = [&](int phase, int di, int64_t rows, int64_t cols, int sz) {
+      for (int64_t j = 0; j < cols; j += cols1) {
+        int64_t hi = std::min<int64_t>(cols, j + cols1);
+        items[phase].push_back({{0, di, (int32_t)j, (int32_t)hi}, double(hi - j) * double(rows * sz)});
+      }
+    };
+    auto add_rows = [&](int phase, int di, int64_t rows, int64_t cols, int fmt) {
+      const int64_t rt = hh::dev::stream_rows_per_item(fmt);
+      for (int64_t r = 0; r < rows; r += rt) {
+        int64_t hi = std::min<int64_t>(rows, r + rt);
+        items[phase].push_back({{0, di, (int32_t)r, (int32_t)hi}, double(hi - r) * double(cols * hh::fmt_bytes(fmt))});
+      }
+    };
+    for (size_t b = 0; b < H.lr.size(); ++b) {
+      const hh::LRBlock& B = H.lr[b];
+      if (B.k == 0) continue;
+      const uint8_t* U = h->d_arena + B.u_off;
+      const uint8_t* V = h->d_arena + B.v_off;
+      StreamDesc s1, s2;
+      std::memset(&s1, 0, sizeof(s1));
+      std::memset(&s2, 0, sizeof(s2));
+      s1.f = dir == 0 ? V : U;
+      s1.ld = dir == 0 ? B.ldv : B.ldu;
+      s1.rows = (int32_t)(dir == 0 ? B.n : B.m);
+      s1.cols = B.k;
+      s1.fmt = B.fmt;
+      s1.in_off = (int32_t)(dir == 0 ? B.col_off : B.row_off);
+      s1.toff = toff[b];
+      s2.f = dir == 0 ? U : V;
+      s2.ld = dir == 0 ? B.ldu : B.ldv;
+      s2.rows = (int32_t)(dir == 0 ? B.m : B.n);
+      s2.cols = B.k;
+      s2.fmt = B.fmt;
+      s2.e = B.exp_u + B.exp_v;
+      s2.out_off = (int32_t)(dir == 0 ? B.row_off : B.col_off);
+      s2.toff = toff[b];
+      desc[0].push_back(s1);
+      add_cols(0, (int)desc[0].size() - 1, s1.rows, s1.cols, hh::fmt_bytes(B.fmt));
+      desc[1].push_back(s2);
+      add_rows(1, (int)desc[1].size() - 1, s2.rows, s2.cols, B.fmt);
+    }
+    for (size_t q = 0; q < H.dense.size(); ++q) {
+      const hh::DenseBlock& D = H.dense[q];
+      StreamDesc s;
+      std::memset(&s, 0, sizeof(s));
+      s.f = reinterpret_cast<const uint8_t*>(h->d_dense_pad + doff[q]);
+      s.ld = (D.m + 1) / 2 * 2;
+      s.rows = (int32_t)D.m;
+      s.cols = (int32_t)D.n;
+      s.fmt = hh::F64;
+      s.mode = 1;
+      s.e = dexp[q];
+      if (dir == 0) {  // forward: phase 2, y[row_off + i] += sum_j D x[col_off + j]
+        s.in_off = (int32_t)D.col_off;
+        s.out_off = (int32_t)D.row_off;
+        desc[1].push_back(s);
+        add_rows(1, (int)desc[1].size() - 1, s.rows, s.cols, hh::F64);
+      } else {         // transpose: phase 1, xbar[col_off + j] += sum_i D y[row_off + i]
+        s.in_off = (int32_t)D.row_off;
+        s.out_off = (int32_t)D.col_off;
+        desc[0].push_back(s);
+        add_cols(0, (int)desc[0].size() - 1, s.rows, s.cols, 8);
+      }
+    }
+    for (int p = 0; p < 2; ++p) {
+      std::stable_sort(items[p].begin(), items[p].end(),
+                       [](const Costed& x, const Costed& y) { return x.cost > y.cost; });
+      std::vector<Item> flat;
+      for (auto& c : items[p]) flat.push_back(c.it);
+      h->d_sdesc[dir][p] = upload(desc[p]);
+      h->d_sitems[dir][p] = upload(flat);
+      h->n_sitems[dir][p] = (int)flat.size();
     }
   }
-  for (size_t d = 0; d < H.dense.size(); ++d) {
-    const hh::DenseBlock& D = H.dense[d];
-    if (dir == 0) {
-      for (int64_t r = 0; r < D.m; r += 32) {
-        int64_t hi = std::min<int64_t>(D.m, r + 32);
-        c2.push_back({{2, (int32_t)d, (int32_t)r, (int32_t)hi}, double(hi - r) * double(D.n * 8)});
-      }
-    } else {
-      const int C = 32 / next_pow2_32(D.m);
-      const int64_t cols = std::max<int64_t>(C, 8);
-      for (int64_t c = 0; c < D.n; c += cols) {
-        int64_t hi = std::min<int64_t>(D.n, c + cols);
-        c2.push_back({{3, (int32_t)d, (int32_t)c, (int32_t)hi}, double(hi - c) * double(D.m * 8)});
-      }
-    }
-  }
-  auto by_cost = [](const Costed& a, const Costed& b) { return a.cost > b.cost; };
-  std::stable_sort(c1.begin(), c1.end(), by_cost);
-  std::stable_sort(c2.begin(), c2.end(), by_cost);
-  p1.clear();
-  p2.clear();
-  for (auto& c : c1) p1.push_back(c.it);
-  for (auto& c : c2) p2.push_back(c.it);
 }
 
 void upload_matrix(hh_matrix* h, int device) {
@@ -162,7 +219,6 @@ void upload_matrix(hh_matrix* h, int device) {
   h->device = device;
   ck(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device), "device attribute");
   h->d_arena = upload(H.arena);
-  h->d_dense = upload(H.dense_data);
   h->d_perm = upload(H.perm);
   h->npad = (H.n + 32 + 3) / 4 * 4;
   // t offsets per block (room for kMaxNR right-hand sides)
@@ -173,53 +229,14 @@ void upload_matrix(hh_matrix* h, int device) {
     toff[b] = tot * hh::dev::kMaxNR;
     tot += H.lr[b].k;
   }
-  for (int dir = 0; dir < 2; ++dir) {
-    std::vector<BlkDesc> bd(H.lr.size());
-    for (size_t b = 0; b < H.lr.size(); ++b) {
-      const hh::LRBlock& B = H.lr[b];
-      const uint8_t* U = h->d_arena + B.u_off;
-      const uint8_t* V = h->d_arena + B.v_off;
-      BlkDesc& d = bd[b];
-      std::memset(&d, 0, sizeof(d));
-      d.f1 = dir == 0 ? V : U;
-      d.f2 = dir == 0 ? U : V;
-      d.ld1 = dir == 0 ? B.ldv : B.ldu;
-      d.ld2 = dir == 0 ? B.ldu : B.ldv;
-      d.n1 = (int32_t)(dir == 0 ? B.n : B.m);
-      d.n2 = (int32_t)(dir == 0 ? B.m : B.n);
-      d.c1 = (int32_t)(dir == 0 ? B.col_off : B.row_off);
-      d.c2 = (int32_t)(dir == 0 ? B.row_off : B.col_off);
-      d.k = B.k;
-      d.fmt = B.fmt;
-      d.e = B.exp_u + B.exp_v;
-      d.toff = toff[b];
-    }
-    h->d_blk[dir] = upload(bd);
-    std::vector<DenseDesc> dd(H.dense.size());
-    for (size_t q = 0; q < H.dense.size(); ++q) {
-      const hh::DenseBlock& D = H.dense[q];
-      dd[q].d = h->d_dense + D.d_off;
-      dd[q].ld = D.m;
-      dd[q].m = (int32_t)D.m;
-      dd[q].n = (int32_t)D.n;
-      dd[q].r0 = (int32_t)(dir == 0 ? D.row_off : D.row_off);
-      dd[q].c0 = (int32_t)(dir == 0 ? D.col_off : D.col_off);
-    }
-    h->d_dns[dir] = upload(dd);
-    std::vector<Item> p1, p2;
-    make_items(H, dir, p1, p2);
-    h->d_items[dir][0] = upload(p1);
-    h->d_items[dir][1] = upload(p2);
-    h->n_items[dir][0] = (int)p1.size();
-    h->n_items[dir][1] = (int)p2.size();
-  }
+  upload_stream(h, toff);
   ck(cudaMalloc(&h->d_status, 256), "cudaMalloc");
   ck(cudaMemset(h->d_status, 0, 256), "cudaMemset");
   unsigned present = 0;
   for (const hh::LRBlock& B : H.lr) present |= 1u << B.fmt;
   h->fset = hh::dev::pass_set_for(present);
   for (int phase = 1; phase <= 2; ++phase)
-    for (int nr : {1, 2, 4}) h->grid[phase][nr] = h->sms * hh::dev::pass_blocks_per_sm(phase, h->fset, nr);
+    for (int nr : {1, 2, 4}) h->sgrid[phase][nr] = h->sms * hh::dev::stream_blocks_per_sm(phase, h->fset, nr);
   size_t ws = 0;
   hh_workspace_bytes(h, &ws);
   ck(cudaMalloc(&h->d_ws, ws), "cudaMalloc workspace");
@@ -229,10 +246,11 @@ void upload_matrix(hh_matrix* h, int device) {
 
 struct WsView {
   float* xs;
-  double* xs64;
+  float* xs_lo;
   double* acc;
   float* t32;
-  double* t64;
+  float2* t64;
+  int* counters;
 };
 
 size_t ws_layout(const hh_matrix* h, WsView* v, char* base) {
@@ -244,11 +262,12 @@ size_t ws_layout(const hh_matrix* h, WsView* v, char* base) {
     return base ? base + o : nullptr;
   };
   float* xs = (float*)take(sizeof(float) * 4 * R * h->npad);
-  double* xs64 = (double*)take(sizeof(double) * 2 * R * h->npad);
+  float* xs_lo = (float*)take(sizeof(float) * 4 * R * h->npad);
   double* acc = (double*)take(sizeof(double) * R * h->npad);
   float* t32 = (float*)take(sizeof(float) * std::max<int64_t>(1, h->t32_elems * R));
-  double* t64 = (double*)take(sizeof(double) * std::max<int64_t>(1, h->t64_elems * R));
-  if (v) *v = {xs, xs64, acc, t32, t64};
+  float2* t64 = (float2*)take(sizeof(float2) * std::max<int64_t>(1, h->t64_elems * R));
+  int* counters = (int*)take(256);
+  if (v) *v = {xs, xs_lo, acc, t32, t64, counters};
   return off;
 }
 
@@ -273,28 +292,27 @@ int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, 
   for (int rb = 0; rb < nrhs;) {
     const int rem = nrhs - rb;
     const int nr = rem >= 4 ? 4 : (rem >= 2 ? 2 : 1);
-    PassArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.blk = h->d_blk[dir];
-    a.dns = h->d_dns[dir];
-    a.nr = nr;
-    a.npad = h->npad;
-    a.xs = w.xs;
-    a.xs64 = w.xs64;
-    a.t32 = w.t32;
-    a.t64 = w.t64;
-    a.acc = w.acc;
-    a.status = h->d_status;
     if (ev) cudaEventRecord(ev[0], st);
     cudaError_t e = hh::dev::launch_prep(in + (int64_t)rb * ld_in, ld_in, nr, h->d_perm, h->H.n, h->npad,
-                                         w.xs, w.xs64, w.acc, st);
+                                         w.xs, w.xs_lo, w.acc, st, w.counters);
     for (int phase = 1; phase <= 2 && e == cudaSuccess; ++phase) {
       if (ev) cudaEventRecord(ev[phase], st);
-      a.items = h->d_items[dir][phase - 1];
-      a.n_items = h->n_items[dir][phase - 1];
-      int grid = std::min(h->grid[phase][nr], (a.n_items + 7) / 8);
-      if (grid < 1) grid = 1;
-      e = hh::dev::launch_pass(phase, h->fset, a, grid, st);
+      hh::dev::StreamArgs s;
+      std::memset(&s, 0, sizeof(s));
+      s.desc = h->d_sdesc[dir][phase - 1];
+      s.items = h->d_sitems[dir][phase - 1];
+      s.n_items = h->n_sitems[dir][phase - 1];
+      s.nr = nr;
+      s.npad = h->npad;
+      s.xs = w.xs;
+      s.xs_lo = w.xs_lo;
+      s.t32 = w.t32;
+      s.t64 = w.t64;
+      s.acc = w.acc;
+      s.status = h->d_status;
+      s.counter = w.counters + (phase - 1);
+      int grid = std::max(1, std::min(h->sgrid[phase][nr], s.n_items));
+      e = hh::dev::launch_stream(phase, h->fset, s, grid, st);
     }
     if (ev) cudaEventRecord(ev[3], st);
     if (e == cudaSuccess)
@@ -570,6 +588,7 @@ int hh_sync_status(hh_handle h, void* stream) {
   if (e == cudaSuccess) e = cudaMemcpy(&word, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
   if (e != cudaSuccess) return fail(HH_ECUDA, std::string("sync failed: ") + cudaGetErrorString(e));
+  if (word & 4) return fail(HH_ETIMEOUT, "a bounded device wait expired (status word " + std::to_string(word) + ")");
   if (word != 0) return fail(HH_EDEVICE, "device status word " + std::to_string(word));
   return HH_OK;
 }
@@ -625,10 +644,10 @@ extern "C" int hh_matvec_noalloc(hh_handle h, int transpose, const double* in, d
   const int64_t npad = (h->H.n + 32 + 3) / 4 * 4;
   int64_t t32 = 0, t64 = 0;
   for (const hh::LRBlock& b : h->H.lr) (b.fmt == hh::F64 ? t64 : t32) += b.k;
-  const size_t need = align256(sizeof(float) * 4 * npad) + align256(sizeof(double) * 2 * npad) +
+  const size_t need = align256(sizeof(float) * 4 * npad) + align256(sizeof(float) * 4 * npad) +
                       align256(sizeof(double) * npad) +
                       align256(sizeof(float) * std::max<int64_t>(1, t32 * hh::dev::kMaxNR)) +
-                      align256(sizeof(double) * std::max<int64_t>(1, t64 * hh::dev::kMaxNR));
+                      align256(sizeof(float2) * std::max<int64_t>(1, t64 * hh::dev::kMaxNR)) + 256;
   if (need > kNoAllocScratchBytes)
     return fail(HH_EINVAL, "hh_matvec_noalloc: this matrix needs " + std::to_string(need) +
                                " bytes of scratch, more than the fixed " +
@@ -647,33 +666,34 @@ extern "C" int hh_matvec_noalloc(hh_handle h, int transpose, const double* in, d
     char* p = (char*)base;
     float* xs = (float*)p;
     p += align256(sizeof(float) * 4 * npad);
-    double* xs64 = (double*)p;
-    p += align256(sizeof(double) * 2 * npad);
+    float* xs_lo = (float*)p;
+    p += align256(sizeof(float) * 4 * npad);
     double* acc = (double*)p;
     p += align256(sizeof(double) * npad);
     float* tt32 = (float*)p;
     p += align256(sizeof(float) * std::max<int64_t>(1, t32 * hh::dev::kMaxNR));
-    double* tt64 = (double*)p;
+    float2* tt64 = (float2*)p;
     const int dir = transpose ? 1 : 0;
     cudaStream_t st = (cudaStream_t)stream;
-    PassArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.blk = h->d_blk[dir];
-    a.dns = h->d_dns[dir];
-    a.nr = 1;
-    a.npad = npad;
-    a.xs = xs;
-    a.xs64 = xs64;
-    a.t32 = tt32;
-    a.t64 = tt64;
-    a.acc = acc;  // cleared by the prep launch on every call
-    a.status = h->d_status;
-    cudaError_t e = hh::dev::launch_prep(in, h->H.n, 1, h->d_perm, h->H.n, npad, xs, xs64, acc, st);
+    int* counters = (int*)(p + align256(sizeof(float2) * std::max<int64_t>(1, t64 * hh::dev::kMaxNR)));
+    cudaError_t e = hh::dev::launch_prep(in, h->H.n, 1, h->d_perm, h->H.n, npad, xs, xs_lo, acc, st, counters);
     for (int phase = 1; phase <= 2 && e == cudaSuccess; ++phase) {
-      a.items = h->d_items[dir][phase - 1];
-      a.n_items = h->n_items[dir][phase - 1];
-      int grid = std::max(1, std::min(h->grid[phase][1], (a.n_items + 7) / 8));
-      e = hh::dev::launch_pass(phase, h->fset, a, grid, st);
+      hh::dev::StreamArgs s;
+      std::memset(&s, 0, sizeof(s));
+      s.desc = h->d_sdesc[dir][phase - 1];
+      s.items = h->d_sitems[dir][phase - 1];
+      s.n_items = h->n_sitems[dir][phase - 1];
+      s.nr = 1;
+      s.npad = npad;
+      s.xs = xs;
+      s.xs_lo = xs_lo;
+      s.t32 = tt32;
+      s.t64 = tt64;
+      s.acc = acc;  // cleared by the prep launch on every call
+      s.status = h->d_status;
+      s.counter = counters + (phase - 1);
+      int grid = std::max(1, std::min(h->sgrid[phase][1], s.n_items));
+      e = hh::dev::launch_stream(phase, h->fset, s, grid, st);
     }
     if (e == cudaSuccess) e = hh::dev::launch_finish(acc, 1, h->d_perm, h->H.n, npad, out, h->H.n, st);
     if (e != cudaSuccess) rc = fail(HH_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));

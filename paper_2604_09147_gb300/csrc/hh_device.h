@@ -8,77 +8,62 @@
 namespace hh {
 namespace dev {
 
-// One low-rank block seen from one direction of the product.
-// Forward (y = A x):     f1 = V (rows n1 = |J|, input segment c1 = off(J)),
-//                        f2 = U (rows n2 = |I|, output segment c2 = off(I)).
-// Transpose (x = A^T y): f1 = U, f2 = V, c1 = off(I), c2 = off(J).
-// Phase 1 computes t_j = sum_i f1[i, j] in[c1 + i] (scaled units),
-// phase 2 adds 2^e * sum_j f2[i, j] t_j into out[c2 + i].
-struct BlkDesc {
-  const uint8_t* f1;
-  const uint8_t* f2;
-  int64_t ld1, ld2;  // leading dimensions in elements (multiples of 16 bytes)
-  int32_t n1, n2;    // rows of f1 / f2
-  int32_t c1, c2;    // tree positions of the input / output segments
-  int32_t k, fmt;
-  int32_t e;         // exp_u + exp_v: value = 2^e * stored products
-  int32_t pad;
-  int64_t toff;      // offset of t_b in the t arena of its precision (per RHS)
-};
-static_assert(sizeof(BlkDesc) == 72, "descriptor size");
-
-// One dense fp64 block, column-major with leading dimension ld.
-// Forward: out[r0 + i] += sum_j D[i, j] in[c0 + j];  transpose: roles of
-// (r0, m) and (c0, n) swap and D is read as D^T.
-struct DenseDesc {
-  const double* d;
-  int64_t ld;
-  int32_t m, n, r0, c0;
-};
-static_assert(sizeof(DenseDesc) == 32, "descriptor size");
-
-// A unit of work for one warp.
-//   kind 0: phase-1 columns [lo, hi) of low-rank block idx
-//   kind 1: phase-2 rows [lo, hi) of low-rank block idx
-//   kind 2: dense block idx, forward, rows [lo, hi)
-//   kind 3: dense block idx, transposed, columns [lo, hi) of D
+// A unit of work of a streaming pass: columns (phase 1) or rows (phase 2)
+// [lo, hi) of the factor described by StreamDesc idx.
 struct Item {
   int32_t kind, idx, lo, hi;
 };
 
-// Arguments of one pass (phase 1 or phase 2) over a list of items.
-struct PassArgs {
-  const BlkDesc* blk;
-  const DenseDesc* dns;
-  const Item* items;
+// One factor (or dense block) as seen by a streaming pass.
+//   phase 1: columns j of f (rows x cols, column-major, ld elements) dotted
+//            with in[in_off + i]; mode 0: t[toff + j*nr + r] = sum (scaled
+//            units), mode 1: acc[out_off + j] += sum (dense block, A^T).
+//   phase 2: acc[out_off + i] += 2^e sum_j f[i, j] t_j; mode 0: t from the
+//            t arena at toff, mode 1: t_j = in[in_off + j] (dense block, A).
+struct StreamDesc {
+  const uint8_t* f;
+  int64_t ld;
+  int32_t rows, cols;
+  int32_t fmt, e;
+  int32_t in_off, out_off;
+  int64_t toff;
+  int32_t mode, pad;
+};
+static_assert(sizeof(StreamDesc) == 56, "descriptor size");
+
+struct StreamArgs {
+  const StreamDesc* desc;
+  const Item* items;  // {unused, desc index, lo, hi}
   int32_t n_items;
-  int32_t nr;           // right-hand sides in this chunk (1, 2 or 4)
-  int64_t npad;         // padded vector length (multiple of 4, >= n + 32)
-  const float* xs;      // [4][nr][npad] fp32 copies of the input, shifted by s
-  const double* xs64;   // [2][nr][npad] fp64 copies, shifted by s
-  float* t32;           // t of non-fp64 blocks  [toff + j * nr + r]
-  double* t64;          // t of fp64 blocks
-  double* acc;          // [nr][npad] fp64 output accumulator (tree order)
-  int* status;          // device status word (bit 0: bad descriptor)
+  int32_t nr;
+  int64_t npad;
+  const float* xs;     // [4][nr][npad] fp32 (leading half) of the input, shifted by s
+  const float* xs_lo;  // [4][nr][npad] the input minus its leading half, shifted by s
+  float* t32;
+  float2* t64;         // t of fp64 blocks as (leading, trailing) fp32 halves
+  double* acc;
+  int* status;   // bit 0 bad descriptor, bit 2 a bounded wait expired
+  int* counter;  // work counter of this pass (zeroed by the prep launch)
 };
 
-// host-callable launchers (kernels.cu)
+// host-callable launchers (kernels.cu, stream.cu)
 cudaError_t launch_prep(const double* in, int64_t ld, int nr, const int32_t* perm, int64_t n,
-                        int64_t npad, float* xs, double* xs64, double* acc, cudaStream_t st);
+                        int64_t npad, float* xs, float* xs_lo, double* acc, cudaStream_t st,
+                        int* counters = nullptr);
+cudaError_t launch_stream(int phase, unsigned fset, const StreamArgs& a, int grid, cudaStream_t st);
+int stream_blocks_per_sm(int phase, unsigned fset, int nr);
+int stream_rows_per_item(int fmt);   // phase-2 rows per item (1 KB of factor data per column)
+int stream_cols_per_item();          // phase-1 columns per item
 // kernel variants by the set of factor formats they contain (bit f = fmt f)
 constexpr unsigned kSetF64 = 1u;         // fp64 factors (and dense blocks)
 constexpr unsigned kSetF32 = 1u | 2u;    // fp64 + fp32
 constexpr unsigned kSetAll = 31u;        // every format
 unsigned pass_set_for(unsigned fmts_present);
-cudaError_t launch_pass(int phase, unsigned fset, const PassArgs& a, int grid, cudaStream_t st);
+
 cudaError_t launch_finish(const double* acc, int nr, const int32_t* perm, int64_t n, int64_t npad,
                           double* out, int64_t ld, cudaStream_t st);
-// blocks per SM the pass kernels reach at 256 threads (occupancy query)
-int pass_blocks_per_sm(int phase, unsigned fset, int nr);
 
-constexpr int kThreads = 128;
-constexpr int kMinBlocks = 4;  // pass kernels: at most 128 registers per thread
-constexpr int kMaxNR = 4;
+constexpr int kMaxNR = 4;  // right-hand sides per launch sequence
 
 }  // namespace dev
 }  // namespace hh

@@ -85,13 +85,16 @@ def test_bit_encoding_matches_torch(fmt, dt):
 
 def test_scale_exponent_lands_below_target():
     rng = np.random.default_rng(4)
-    for fmt in (F.FP32, F.FP16, F.BF16, F.E4M3):
+    for fmt in (F.FP64, F.FP32, F.FP16, F.BF16, F.E4M3):
         for m in np.concatenate([np.ldexp(rng.random(300) + 0.5, rng.integers(-300, 300, 300)),
                                  [F.SCALE_TARGET[fmt], F.SCALE_TARGET[fmt] * 2, 1e-310]]):
             e = F.scale_exponent(float(m), fmt)
             s = np.ldexp(m, -e)
             assert F.SCALE_TARGET[fmt] / 2 < s <= F.SCALE_TARGET[fmt]
-    assert F.scale_exponent(3.0, F.FP64) == 0
+    assert F.scale_exponent(0.0, F.FP64) == 0
+    a = np.random.default_rng(9).standard_normal(50) * 1e-130          # fp64 scaling is exact
+    s, e = F.quantize_factor(a, F.FP64)
+    assert np.array_equal(np.ldexp(s, e), a) and 0.5 < np.max(np.abs(s)) <= 1.0
 
 
 def test_quantize_factor_error_is_within_unit_roundoff():

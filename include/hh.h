@@ -92,6 +92,8 @@ typedef struct {
   double bound_thm44;             /* 2 * bound_thm42 (Theorem 4.4, backward error)   */
   double bound_rounding;          /* sqrt(sum_b ((2+sqrt(p)u)u||H~_b||)^2)/||H~||    */
   double build_seconds;           /* wall time of hh_build (0 for hh_load)           */
+  int64_t tc_blocks;              /* admissible blocks the tensor-core path takes    */
+  int64_t tc_factor_bytes;        /* their factor bytes                              */
 } hh_info_t;
 
 /*

@@ -48,6 +48,7 @@ class _Info(ctypes.Structure):
         ("norm_ht", ctypes.c_double), ("csp", ctypes.c_int32 * MAX_LEVELS),
         ("bound_thm42", ctypes.c_double), ("bound_thm44", ctypes.c_double),
         ("bound_rounding", ctypes.c_double), ("build_seconds", ctypes.c_double),
+        ("tc_blocks", ctypes.c_int64), ("tc_factor_bytes", ctypes.c_int64),
     ]
 
 

@@ -39,6 +39,27 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
 
+// Descriptors and work items of the two streaming passes (stream.cu) for one
+// direction, with the kernel variant and grid sizes that fit them.
+struct StreamSet {
+  hh::dev::StreamDesc* d_desc[2] = {nullptr, nullptr};  // [phase]
+  Item* d_items[2] = {nullptr, nullptr};
+  int n_items[2] = {0, 0};
+  unsigned fset = hh::dev::kSetAll;
+  int grid[3][5] = {};  // [phase][nr]
+};
+
+// Work tables of the tensor-core path (tc.cu) for one direction.
+struct TcSet {
+  hh::dev::TcPiece* d_pieces = nullptr;
+  hh::dev::TcGroup* d_groups = nullptr;
+  hh::dev::TcTile* d_tiles = nullptr;
+  hh::dev::TcEntry* d_entries = nullptr;
+  int n_pieces = 0, n_groups = 0, n_tiles = 0;
+  int64_t t_bytes = 0;                  // T images of all pieces
+  int64_t n_blocks = 0, factor_bytes = 0;
+};
+
 struct hh_matrix {
   hh::HostMatrix H;
   hh::Summary S;
@@ -53,13 +74,12 @@ struct hh_matrix {
   size_t ws_bytes = 0;
   double* d_stage = nullptr;  // hh_matvec_host staging buffers (2 x n x stage_cols)
   int stage_cols = 0;
-  // streaming passes (stream.cu): descriptors and items per [direction][phase]
-  hh::dev::StreamDesc* d_sdesc[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  Item* d_sitems[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  int n_sitems[2][2] = {{0, 0}, {0, 0}};
   double* d_dense_pad = nullptr;  // dense blocks, column-major, ld rounded up to even
-  int sgrid[3][5] = {};
-  unsigned fset = hh::dev::kSetAll;  // kernel variant covering the formats present
+  StreamSet ss[2];     // [direction]: every block on the streaming passes
+  StreamSet ss_rest[2];  // [direction]: the blocks the tensor-core path leaves to them
+  TcSet tc[2];         // [direction]
+  void* d_tc_ws = nullptr;  // tensor-core workspace, allocated on first use
+  size_t tc_ws_bytes = 0;
 };
 
 namespace {
@@ -71,11 +91,19 @@ void free_device(hh_matrix* h) {
   if (cur != h->device) cudaSetDevice(h->device);
   cudaFree(h->d_arena);
   cudaFree(h->d_perm);
-  for (int d = 0; d < 2; ++d)
+  for (int d = 0; d < 2; ++d) {
     for (int p = 0; p < 2; ++p) {
-      cudaFree(h->d_sdesc[d][p]);
-      cudaFree(h->d_sitems[d][p]);
+      cudaFree(h->ss[d].d_desc[p]);
+      cudaFree(h->ss[d].d_items[p]);
+      cudaFree(h->ss_rest[d].d_desc[p]);
+      cudaFree(h->ss_rest[d].d_items[p]);
     }
+    cudaFree(h->tc[d].d_pieces);
+    cudaFree(h->tc[d].d_groups);
+    cudaFree(h->tc[d].d_tiles);
+    cudaFree(h->tc[d].d_entries);
+  }
+  cudaFree(h->d_tc_ws);
   cudaFree(h->d_dense_pad);
   cudaFree(h->d_status);
   cudaFree(h->d_ws);
@@ -98,21 +126,19 @@ int next_pow2_32(int64_t v) {
   return g;
 }
 
-// Descriptors and work items of the streaming passes (stream.cu).
-void upload_stream(hh_matrix* h, const std::vector<int64_t>& toff) {
-  using hh::dev::StreamDesc;
+// Dense blocks with an even leading dimension (16-byte aligned columns), each
+// scaled by a power of two so that its largest magnitude lies in (1/2, 1]
+// (exact; the kernels split fp64 values into fp32 halves).
+void upload_dense(hh_matrix* h, std::vector<int64_t>& doff, std::vector<int32_t>& dexp) {
   const hh::HostMatrix& H = h->H;
-  // dense blocks with an even leading dimension (16-byte aligned columns)
-  std::vector<int64_t> doff(H.dense.size());
+  doff.assign(H.dense.size(), 0);
+  dexp.assign(H.dense.size(), 0);
   int64_t dtot = 0;
   for (size_t q = 0; q < H.dense.size(); ++q) {
     doff[q] = dtot;
     dtot += ((H.dense[q].m + 1) / 2 * 2) * H.dense[q].n;
   }
-  // each block scaled by a power of two so that its largest magnitude lies in
-  // (1/2, 1] (exact; the kernels split fp64 values into fp32 halves)
   std::vector<double> dpad(static_cast<size_t>(dtot), 0.0);
-  std::vector<int32_t> dexp(H.dense.size(), 0);
   for (size_t q = 0; q < H.dense.size(); ++q) {
     const hh::DenseBlock& D = H.dense[q];
     const int64_t ld = (D.m + 1) / 2 * 2;
@@ -129,88 +155,240 @@ void upload_stream(hh_matrix* h, const std::vector<int64_t>& toff) {
         dpad[doff[q] + c * ld + r] = std::ldexp(H.dense_data[D.d_off + c * D.m + r], -ex);
   }
   h->d_dense_pad = upload(dpad);
+}
+
+// Descriptors and work items of the streaming passes (stream.cu) for one
+// direction: every dense block and the low-rank blocks `take` selects.
+void build_stream_set(hh_matrix* h, int dir, const std::vector<int64_t>& toff, const std::vector<int64_t>& doff,
+                      const std::vector<int32_t>& dexp, const std::vector<char>& take, StreamSet& out) {
+  using hh::dev::StreamDesc;
+  const hh::HostMatrix& H = h->H;
   const int cols1 = hh::dev::stream_cols_per_item();
-  for (int dir = 0; dir < 2; ++dir) {
-    std::vector<StreamDesc> desc[2];
-    struct Costed {
-      Item it;
-      double cost;
-    };
-    std::vector<Costed> items[2];
-    auto add_cols = [&](int phase, int di, int64_t rows, int64_t cols, int sz) {
-      for (int64_t j = 0; j < cols; j += cols1) {
-        int64_t hi = std::min<int64_t>(cols, j + cols1);
-        items[phase].push_back({{0, di, (int32_t)j, (int32_t)hi}, double(hi - j) * double(rows * sz)});
-      }
-    };
-    auto add_rows = [&](int phase, int di, int64_t rows, int64_t cols, int fmt) {
-      const int64_t rt = hh::dev::stream_rows_per_item(fmt);
-      for (int64_t r = 0; r < rows; r += rt) {
-        int64_t hi = std::min<int64_t>(rows, r + rt);
-        items[phase].push_back({{0, di, (int32_t)r, (int32_t)hi}, double(hi - r) * double(cols * hh::fmt_bytes(fmt))});
-      }
-    };
-    for (size_t b = 0; b < H.lr.size(); ++b) {
-      const hh::LRBlock& B = H.lr[b];
-      if (B.k == 0) continue;
-      const uint8_t* U = h->d_arena + B.u_off;
-      const uint8_t* V = h->d_arena + B.v_off;
-      StreamDesc s1, s2;
-      std::memset(&s1, 0, sizeof(s1));
-      std::memset(&s2, 0, sizeof(s2));
-      s1.f = dir == 0 ? V : U;
-      s1.ld = dir == 0 ? B.ldv : B.ldu;
-      s1.rows = (int32_t)(dir == 0 ? B.n : B.m);
-      s1.cols = B.k;
-      s1.fmt = B.fmt;
-      s1.in_off = (int32_t)(dir == 0 ? B.col_off : B.row_off);
-      s1.toff = toff[b];
-      s2.f = dir == 0 ? U : V;
-      s2.ld = dir == 0 ? B.ldu : B.ldv;
-      s2.rows = (int32_t)(dir == 0 ? B.m : B.n);
-      s2.cols = B.k;
-      s2.fmt = B.fmt;
-      s2.e = B.exp_u + B.exp_v;
-      s2.out_off = (int32_t)(dir == 0 ? B.row_off : B.col_off);
-      s2.toff = toff[b];
-      desc[0].push_back(s1);
-      add_cols(0, (int)desc[0].size() - 1, s1.rows, s1.cols, hh::fmt_bytes(B.fmt));
-      desc[1].push_back(s2);
-      add_rows(1, (int)desc[1].size() - 1, s2.rows, s2.cols, B.fmt);
+  std::vector<StreamDesc> desc[2];
+  struct Costed {
+    Item it;
+    double cost;
+  };
+  std::vector<Costed> items[2];
+  auto add_cols = [&](int phase, int di, int64_t rows, int64_t cols, int sz) {
+    for (int64_t j = 0; j < cols; j += cols1) {
+      int64_t hi = std::min<int64_t>(cols, j + cols1);
+      items[phase].push_back({{0, di, (int32_t)j, (int32_t)hi}, double(hi - j) * double(rows * sz)});
     }
-    for (size_t q = 0; q < H.dense.size(); ++q) {
-      const hh::DenseBlock& D = H.dense[q];
-      StreamDesc s;
-      std::memset(&s, 0, sizeof(s));
-      s.f = reinterpret_cast<const uint8_t*>(h->d_dense_pad + doff[q]);
-      s.ld = (D.m + 1) / 2 * 2;
-      s.rows = (int32_t)D.m;
-      s.cols = (int32_t)D.n;
-      s.fmt = hh::F64;
-      s.mode = 1;
-      s.e = dexp[q];
-      if (dir == 0) {  // forward: phase 2, y[row_off + i] += sum_j D x[col_off + j]
-        s.in_off = (int32_t)D.col_off;
-        s.out_off = (int32_t)D.row_off;
-        desc[1].push_back(s);
-        add_rows(1, (int)desc[1].size() - 1, s.rows, s.cols, hh::F64);
-      } else {         // transpose: phase 1, xbar[col_off + j] += sum_i D y[row_off + i]
-        s.in_off = (int32_t)D.row_off;
-        s.out_off = (int32_t)D.col_off;
-        desc[0].push_back(s);
-        add_cols(0, (int)desc[0].size() - 1, s.rows, s.cols, 8);
-      }
+  };
+  auto add_rows = [&](int phase, int di, int64_t rows, int64_t cols, int fmt) {
+    const int64_t rt = hh::dev::stream_rows_per_item(fmt);
+    for (int64_t r = 0; r < rows; r += rt) {
+      int64_t hi = std::min<int64_t>(rows, r + rt);
+      items[phase].push_back({{0, di, (int32_t)r, (int32_t)hi}, double(hi - r) * double(cols * hh::fmt_bytes(fmt))});
     }
-    for (int p = 0; p < 2; ++p) {
-      std::stable_sort(items[p].begin(), items[p].end(),
-                       [](const Costed& x, const Costed& y) { return x.cost > y.cost; });
-      std::vector<Item> flat;
-      for (auto& c : items[p]) flat.push_back(c.it);
-      h->d_sdesc[dir][p] = upload(desc[p]);
-      h->d_sitems[dir][p] = upload(flat);
-      h->n_sitems[dir][p] = (int)flat.size();
+  };
+  unsigned present = 0;
+  for (size_t b = 0; b < H.lr.size(); ++b) {
+    const hh::LRBlock& B = H.lr[b];
+    if (B.k == 0 || !take[b]) continue;
+    present |= 1u << B.fmt;
+    const uint8_t* U = h->d_arena + B.u_off;
+    const uint8_t* V = h->d_arena + B.v_off;
+    StreamDesc s1, s2;
+    std::memset(&s1, 0, sizeof(s1));
+    std::memset(&s2, 0, sizeof(s2));
+    s1.f = dir == 0 ? V : U;
+    s1.ld = dir == 0 ? B.ldv : B.ldu;
+    s1.rows = (int32_t)(dir == 0 ? B.n : B.m);
+    s1.cols = B.k;
+    s1.fmt = B.fmt;
+    s1.in_off = (int32_t)(dir == 0 ? B.col_off : B.row_off);
+    s1.toff = toff[b];
+    s2.f = dir == 0 ? U : V;
+    s2.ld = dir == 0 ? B.ldu : B.ldv;
+    s2.rows = (int32_t)(dir == 0 ? B.m : B.n);
+    s2.cols = B.k;
+    s2.fmt = B.fmt;
+    s2.e = B.exp_u + B.exp_v;
+    s2.out_off = (int32_t)(dir == 0 ? B.row_off : B.col_off);
+    s2.toff = toff[b];
+    desc[0].push_back(s1);
+    add_cols(0, (int)desc[0].size() - 1, s1.rows, s1.cols, hh::fmt_bytes(B.fmt));
+    desc[1].push_back(s2);
+    add_rows(1, (int)desc[1].size() - 1, s2.rows, s2.cols, B.fmt);
+  }
+  for (size_t q = 0; q < H.dense.size(); ++q) {
+    const hh::DenseBlock& D = H.dense[q];
+    StreamDesc s;
+    std::memset(&s, 0, sizeof(s));
+    s.f = reinterpret_cast<const uint8_t*>(h->d_dense_pad + doff[q]);
+    s.ld = (D.m + 1) / 2 * 2;
+    s.rows = (int32_t)D.m;
+    s.cols = (int32_t)D.n;
+    s.fmt = hh::F64;
+    s.mode = 1;
+    s.e = dexp[q];
+    if (dir == 0) {  // forward: phase 2, y[row_off + i] += sum_j D x[col_off + j]
+      s.in_off = (int32_t)D.col_off;
+      s.out_off = (int32_t)D.row_off;
+      desc[1].push_back(s);
+      add_rows(1, (int)desc[1].size() - 1, s.rows, s.cols, hh::F64);
+    } else {         // transpose: phase 1, xbar[col_off + j] += sum_i D y[row_off + i]
+      s.in_off = (int32_t)D.row_off;
+      s.out_off = (int32_t)D.col_off;
+      desc[0].push_back(s);
+      add_cols(0, (int)desc[0].size() - 1, s.rows, s.cols, 8);
     }
   }
+  for (int p = 0; p < 2; ++p) {
+    std::stable_sort(items[p].begin(), items[p].end(),
+                     [](const Costed& x, const Costed& y) { return x.cost > y.cost; });
+    std::vector<Item> flat;
+    for (auto& c : items[p]) flat.push_back(c.it);
+    out.d_desc[p] = upload(desc[p]);
+    out.d_items[p] = upload(flat);
+    out.n_items[p] = (int)flat.size();
+  }
+  out.fset = hh::dev::pass_set_for(present);
+  for (int phase = 1; phase <= 2; ++phase)
+    for (int nr : {1, 2, 4}) out.grid[phase][nr] = h->sms * hh::dev::stream_blocks_per_sm(phase, out.fset, nr);
+}
+
+// Formats the tensor-core path takes and the most ranks of one piece.
+// fp32 blocks stay on the streaming passes: the tensor core's truncating
+// accumulation is accurate to about 2^-17 of a block's product, below the unit
+// roundoff of the 16- and 8-bit formats but not of fp32.
+bool tc_format(int fmt) { return fmt == hh::F16 || fmt == hh::BF16 || fmt == hh::E4M3; }
+int tc_piece_cap(int fmt) { return fmt == hh::F32 ? 128 : 256; }
+int tc_input_slices(int fmt) { return fmt == hh::F32 ? 3 : 2; }
+
+// A block goes to the tensor cores when its format is one they take and both
+// of its clusters start at a tree position that is a multiple of 16 (the
+// operand images are built in 16-position blocks).
+bool tc_eligible(const hh::LRBlock& B) {
+  return B.k > 0 && tc_format(B.fmt) && B.row_off % 16 == 0 && B.col_off % 16 == 0;
+}
+
+// Work tables of the tensor-core path for one direction: pieces of at most
+// tc_piece_cap ranks, grouped by (input cluster, format) into phase-1 groups
+// of at most 256 ranks, and the 256-row output tiles of phase 2 with the
+// piece rows that fall in them.
+void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
+  using namespace hh::dev;
+  const hh::HostMatrix& H = h->H;
+  struct Key {
+    int64_t in_off, rows;
+    int fmt;
+    bool operator<(const Key& o) const {
+      if (in_off != o.in_off) return in_off < o.in_off;
+      if (rows != o.rows) return rows < o.rows;
+      return fmt < o.fmt;
+    }
+  };
+  std::vector<std::pair<Key, TcPiece>> raw;
+  for (const hh::LRBlock& B : H.lr) {
+    if (!tc_eligible(B)) continue;
+    const int sz = hh::fmt_bytes(B.fmt);
+    const uint8_t* U = h->d_arena + B.u_off;
+    const uint8_t* V = h->d_arena + B.v_off;
+    const uint8_t* f1 = dir == 0 ? V : U;
+    const uint8_t* f2 = dir == 0 ? U : V;
+    const int64_t ld1 = dir == 0 ? B.ldv : B.ldu, ld2 = dir == 0 ? B.ldu : B.ldv;
+    out.n_blocks += 1;
+    out.factor_bytes += (B.m + B.n) * int64_t(B.k) * sz;
+    for (int r0 = 0; r0 < B.k; r0 += tc_piece_cap(B.fmt)) {
+      TcPiece q;
+      std::memset(&q, 0, sizeof(q));
+      q.k = std::min(tc_piece_cap(B.fmt), B.k - r0);
+      q.kp = (q.k + 15) / 16 * 16;
+      q.f1 = f1 + int64_t(r0) * ld1 * sz;
+      q.f2 = f2 + int64_t(r0) * ld2 * sz;
+      q.ld1 = ld1;
+      q.ld2 = ld2;
+      q.rows1 = (int32_t)(dir == 0 ? B.n : B.m);
+      q.rows2 = (int32_t)(dir == 0 ? B.m : B.n);
+      q.in_off = (int32_t)(dir == 0 ? B.col_off : B.row_off);
+      q.out_off = (int32_t)(dir == 0 ? B.row_off : B.col_off);
+      q.fmt = B.fmt;
+      q.e = B.exp_u + B.exp_v;
+      raw.push_back({Key{q.in_off, q.rows1, q.fmt}, q});
+    }
+  }
+  std::stable_sort(raw.begin(), raw.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+  std::vector<TcPiece> pieces;
+  struct CGroup {
+    TcGroup g;
+    double cost;
+  };
+  std::vector<CGroup> groups;
+  int64_t toff = 0;
+  for (size_t i = 0; i < raw.size();) {
+    size_t j = i;
+    while (j < raw.size() && !(raw[i].first < raw[j].first) && !(raw[j].first < raw[i].first)) ++j;
+    // pieces [i, j) share the input cluster and the format: pack into groups
+    for (size_t t = i; t < j;) {
+      TcGroup g;
+      std::memset(&g, 0, sizeof(g));
+      g.first = (int32_t)pieces.size();
+      g.fmt = raw[t].second.fmt;
+      g.in_off = raw[t].second.in_off;
+      g.rows = raw[t].second.rows1;
+      const int cap = tc_piece_cap(g.fmt);
+      while (t < j && g.nk + raw[t].second.kp <= cap) {
+        TcPiece q = raw[t].second;
+        q.col = g.nk;
+        q.toff = toff;
+        toff += int64_t(tc_input_slices(q.fmt)) * (q.kp / 16) * 4096;
+        g.nk += q.kp;
+        g.count += 1;
+        pieces.push_back(q);
+        ++t;
+      }
+      groups.push_back({g, double(g.rows) * g.nk * hh::fmt_bytes(g.fmt)});
+    }
+    i = j;
+  }
+  std::stable_sort(groups.begin(), groups.end(), [](const CGroup& x, const CGroup& y) { return x.cost > y.cost; });
+  // phase-2 tiles
+  const int64_t ntiles = (H.n + kTcRows - 1) / kTcRows;
+  std::vector<std::vector<TcEntry>> per_tile(static_cast<size_t>(ntiles));
+  for (size_t pi = 0; pi < pieces.size(); ++pi) {
+    const TcPiece& q = pieces[pi];
+    const int64_t lo = q.out_off, hi = int64_t(q.out_off) + q.rows2;
+    for (int64_t t = lo / kTcRows; t * kTcRows < hi; ++t) {
+      const int64_t r0 = t * kTcRows, a = std::max(lo, r0), b = std::min(hi, r0 + kTcRows);
+      per_tile[t].push_back(TcEntry{(int32_t)pi, (int32_t)(a - lo), (int32_t)(a - r0), (int32_t)(b - a)});
+    }
+  }
+  struct CTile {
+    TcTile t;
+    double cost;
+  };
+  std::vector<CTile> tiles;
+  std::vector<TcEntry> entries;
+  for (int64_t t = 0; t < ntiles; ++t) {
+    if (per_tile[t].empty()) continue;
+    TcTile tl;
+    tl.row0 = (int32_t)(t * kTcRows);
+    tl.rows = (int32_t)std::min<int64_t>(kTcRows, H.n - t * kTcRows);
+    tl.first = (int32_t)entries.size();
+    tl.count = (int32_t)per_tile[t].size();
+    double cost = 0;
+    for (const TcEntry& e : per_tile[t]) {
+      entries.push_back(e);
+      cost += double(pieces[e.piece].kp) * (kTcRows * hh::fmt_bytes(pieces[e.piece].fmt) + 4096.0);
+    }
+    tiles.push_back({tl, cost});
+  }
+  std::stable_sort(tiles.begin(), tiles.end(), [](const CTile& x, const CTile& y) { return x.cost > y.cost; });
+  std::vector<TcGroup> gflat;
+  for (auto& g : groups) gflat.push_back(g.g);
+  std::vector<TcTile> tflat;
+  for (auto& t : tiles) tflat.push_back(t.t);
+  out.d_pieces = upload(pieces);
+  out.d_groups = upload(gflat);
+  out.d_tiles = upload(tflat);
+  out.d_entries = upload(entries);
+  out.n_pieces = (int)pieces.size();
+  out.n_groups = (int)gflat.size();
+  out.n_tiles = (int)tflat.size();
+  out.t_bytes = toff;
 }
 
 void upload_matrix(hh_matrix* h, int device) {
@@ -229,14 +407,18 @@ void upload_matrix(hh_matrix* h, int device) {
     toff[b] = tot * hh::dev::kMaxNR;
     tot += H.lr[b].k;
   }
-  upload_stream(h, toff);
+  std::vector<int64_t> doff;
+  std::vector<int32_t> dexp;
+  upload_dense(h, doff, dexp);
+  std::vector<char> all(H.lr.size(), 1), rest(H.lr.size(), 1);
+  for (size_t b = 0; b < H.lr.size(); ++b) rest[b] = !tc_eligible(H.lr[b]);
+  for (int dir = 0; dir < 2; ++dir) {
+    build_stream_set(h, dir, toff, doff, dexp, all, h->ss[dir]);
+    build_stream_set(h, dir, toff, doff, dexp, rest, h->ss_rest[dir]);
+    build_tc_set(h, dir, h->tc[dir]);
+  }
   ck(cudaMalloc(&h->d_status, 256), "cudaMalloc");
   ck(cudaMemset(h->d_status, 0, 256), "cudaMemset");
-  unsigned present = 0;
-  for (const hh::LRBlock& B : H.lr) present |= 1u << B.fmt;
-  h->fset = hh::dev::pass_set_for(present);
-  for (int phase = 1; phase <= 2; ++phase)
-    for (int nr : {1, 2, 4}) h->sgrid[phase][nr] = h->sms * hh::dev::stream_blocks_per_sm(phase, h->fset, nr);
   size_t ws = 0;
   hh_workspace_bytes(h, &ws);
   ck(cudaMalloc(&h->d_ws, ws), "cudaMalloc workspace");
@@ -271,8 +453,109 @@ size_t ws_layout(const hh_matrix* h, WsView* v, char* base) {
   return off;
 }
 
+// prep -> phase 1 -> phase 2 of the streaming passes over the blocks of `set`
+// for nr <= 4 right-hand sides; the products are added into acc [nr][npad]
+// (cleared by the prep launch).
+cudaError_t run_stream(hh_matrix* h, const StreamSet& set, const double* in, int64_t ld_in, int nr, double* acc,
+                       const WsView& w, cudaStream_t st, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], st);
+  cudaError_t e = hh::dev::launch_prep(in, ld_in, nr, h->d_perm, h->H.n, h->npad, w.xs, w.xs_lo, acc, st, w.counters);
+  for (int phase = 1; phase <= 2 && e == cudaSuccess; ++phase) {
+    if (ev) cudaEventRecord(ev[phase], st);
+    hh::dev::StreamArgs s;
+    std::memset(&s, 0, sizeof(s));
+    s.desc = set.d_desc[phase - 1];
+    s.items = set.d_items[phase - 1];
+    s.n_items = set.n_items[phase - 1];
+    s.nr = nr;
+    s.npad = h->npad;
+    s.xs = w.xs;
+    s.xs_lo = w.xs_lo;
+    s.t32 = w.t32;
+    s.t64 = w.t64;
+    s.acc = acc;
+    s.status = h->d_status;
+    s.counter = w.counters + (phase - 1);
+    if (s.n_items == 0) continue;
+    int grid = std::max(1, std::min(set.grid[phase][nr], s.n_items));
+    e = hh::dev::launch_stream(phase, set.fset, s, grid, st);
+  }
+  return e;
+}
+
+// Right-hand-side count from which hh_matvec / hh_matvec_T use the tensor
+// cores (HH_TC_MIN_NRHS overrides; 0 disables the path).
+int tc_min_nrhs() {
+  static const int v = [] {
+    const char* s = std::getenv("HH_TC_MIN_NRHS");
+    return s ? std::atoi(s) : 32;
+  }();
+  return v;
+}
+
+struct TcWs {
+  uint8_t* ximg;
+  uint8_t* timg;
+  double* acc;
+  int64_t nblk;
+};
+
+size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
+  const int64_t nblk = (h->npad + 15) / 16 + 4;
+  const int64_t tb = std::max(h->tc[0].t_bytes, h->tc[1].t_bytes);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return base ? base + o : nullptr;
+  };
+  uint8_t* ximg = (uint8_t*)take(size_t(3) * nblk * 4096);
+  uint8_t* timg = (uint8_t*)take(std::max<size_t>(256, size_t(tb)));
+  double* acc = (double*)take(sizeof(double) * hh::dev::kTcMaxRhs * h->npad);
+  if (v) *v = {ximg, timg, acc, nblk};
+  return off;
+}
+
+// Tensor-core product for nrhs <= 128 right-hand sides: prep of the input
+// image, the streaming passes for the blocks the tensor cores leave (fp64
+// blocks, dense blocks, unaligned clusters) in chunks of up to 4 right-hand
+// sides, the two tensor-core phases, and the output permutation.
+cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr, int64_t ld_in, int64_t ld_out,
+                   const WsView& w, const TcWs& t, cudaStream_t st) {
+  cudaError_t e = hh::dev::launch_tc_prep(in, ld_in, nr, h->d_perm, h->H.n, t.nblk, t.ximg, t.acc, h->npad, st);
+  const StreamSet& rest = h->ss_rest[dir];
+  if (rest.n_items[0] + rest.n_items[1] > 0)
+    for (int rb = 0; rb < nr && e == cudaSuccess;) {
+      const int rem = nr - rb, c = rem >= 4 ? 4 : (rem >= 2 ? 2 : 1);
+      e = run_stream(h, rest, in + int64_t(rb) * ld_in, ld_in, c, t.acc + int64_t(rb) * h->npad, w, st, nullptr);
+      rb += c;
+    }
+  hh::dev::TcArgs a;
+  std::memset(&a, 0, sizeof(a));
+  const TcSet& ts = h->tc[dir];
+  a.pieces = ts.d_pieces;
+  a.groups = ts.d_groups;
+  a.tiles = ts.d_tiles;
+  a.entries = ts.d_entries;
+  a.n_groups = ts.n_groups;
+  a.n_tiles = ts.n_tiles;
+  a.nr = nr;
+  a.rp = (nr + 15) / 16 * 16;
+  a.ximg = t.ximg;
+  a.nblk = t.nblk;
+  a.timg = t.timg;
+  a.acc = t.acc;
+  a.npad = h->npad;
+  a.status = h->d_status;
+  if (e == cudaSuccess) e = hh::dev::launch_tc(1, a, st);
+  if (e == cudaSuccess) e = hh::dev::launch_tc(2, a, st);
+  if (e == cudaSuccess) e = hh::dev::launch_finish(t.acc, nr, h->d_perm, h->H.n, h->npad, out, ld_out, st);
+  return e;
+}
+
 int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, int64_t ld_in,
-                int64_t ld_out, void* ws, size_t ws_bytes, cudaStream_t st, cudaEvent_t* ev = nullptr) {
+                int64_t ld_out, void* ws, size_t ws_bytes, cudaStream_t st, cudaEvent_t* ev = nullptr,
+                bool allow_tc = false) {
   if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data (built with device = -1)");
   if (!in || !out || nrhs < 1 || ld_in < h->H.n || ld_out < h->H.n)
     return fail(HH_EINVAL, "bad vector arguments (null pointer, nrhs < 1 or ld < n)");
@@ -289,35 +572,39 @@ int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, 
     return fail(HH_ECUDA, "cudaSetDevice failed");
   WsView w;
   ws_layout(h, &w, (char*)ws);
+  const int tmin = tc_min_nrhs();
+  const bool use_tc = allow_tc && tmin > 0 && nrhs >= tmin && h->tc[dir].n_pieces > 0;
+  TcWs t{};
+  if (use_tc) {
+    const size_t tneed = tc_ws_layout(h, nullptr, nullptr);
+    if (h->tc_ws_bytes < tneed) {
+      cudaStreamSynchronize(st);
+      cudaFree(h->d_tc_ws);
+      h->d_tc_ws = nullptr;
+      h->tc_ws_bytes = 0;
+      if (cudaMalloc(&h->d_tc_ws, tneed) != cudaSuccess) {
+        if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+        return fail(HH_ENOMEM, "cannot allocate the tensor-core workspace");
+      }
+      h->tc_ws_bytes = tneed;
+    }
+    tc_ws_layout(h, &t, (char*)h->d_tc_ws);
+  }
   for (int rb = 0; rb < nrhs;) {
     const int rem = nrhs - rb;
-    const int nr = rem >= 4 ? 4 : (rem >= 2 ? 2 : 1);
-    if (ev) cudaEventRecord(ev[0], st);
-    cudaError_t e = hh::dev::launch_prep(in + (int64_t)rb * ld_in, ld_in, nr, h->d_perm, h->H.n, h->npad,
-                                         w.xs, w.xs_lo, w.acc, st, w.counters);
-    for (int phase = 1; phase <= 2 && e == cudaSuccess; ++phase) {
-      if (ev) cudaEventRecord(ev[phase], st);
-      hh::dev::StreamArgs s;
-      std::memset(&s, 0, sizeof(s));
-      s.desc = h->d_sdesc[dir][phase - 1];
-      s.items = h->d_sitems[dir][phase - 1];
-      s.n_items = h->n_sitems[dir][phase - 1];
-      s.nr = nr;
-      s.npad = h->npad;
-      s.xs = w.xs;
-      s.xs_lo = w.xs_lo;
-      s.t32 = w.t32;
-      s.t64 = w.t64;
-      s.acc = w.acc;
-      s.status = h->d_status;
-      s.counter = w.counters + (phase - 1);
-      int grid = std::max(1, std::min(h->sgrid[phase][nr], s.n_items));
-      e = hh::dev::launch_stream(phase, h->fset, s, grid, st);
+    cudaError_t e;
+    int nr;
+    if (use_tc) {
+      nr = std::min(rem, hh::dev::kTcMaxRhs);
+      e = run_tc(h, dir, in + (int64_t)rb * ld_in, out + (int64_t)rb * ld_out, nr, ld_in, ld_out, w, t, st);
+    } else {
+      nr = rem >= 4 ? 4 : (rem >= 2 ? 2 : 1);
+      e = run_stream(h, h->ss[dir], in + (int64_t)rb * ld_in, ld_in, nr, w.acc, w, st, ev);
+      if (ev) cudaEventRecord(ev[3], st);
+      if (e == cudaSuccess)
+        e = hh::dev::launch_finish(w.acc, nr, h->d_perm, h->H.n, h->npad, out + (int64_t)rb * ld_out, ld_out, st);
+      if (ev) cudaEventRecord(ev[4], st);
     }
-    if (ev) cudaEventRecord(ev[3], st);
-    if (e == cudaSuccess)
-      e = hh::dev::launch_finish(w.acc, nr, h->d_perm, h->H.n, h->npad, out + (int64_t)rb * ld_out, ld_out, st);
-    if (ev) cudaEventRecord(ev[4], st);
     if (e != cudaSuccess) {
       if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
       return fail(HH_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
@@ -472,6 +759,14 @@ int hh_info(hh_handle h, hh_info_t* o) {
   o->bound_thm44 = S.bound44;
   o->bound_rounding = S.bound_round;
   o->build_seconds = H.build_seconds;
+  o->tc_blocks = h->tc[0].n_blocks;
+  o->tc_factor_bytes = h->tc[0].factor_bytes;
+  if (h->device < 0)
+    for (const hh::LRBlock& B : H.lr)
+      if (tc_eligible(B)) {
+        o->tc_blocks += 1;
+        o->tc_factor_bytes += (B.m + B.n) * int64_t(B.k) * hh::fmt_bytes(B.fmt);
+      }
   return HH_OK;
 }
 
@@ -489,13 +784,13 @@ int hh_workspace_bytes(hh_handle h, size_t* bytes) {
 
 int hh_matvec(hh_handle h, const double* x, double* y, int nrhs, int64_t ldx, int64_t ldy, void* stream) {
   if (!h) return fail(HH_EINVAL, "null handle");
-  return run_product(h, 0, x, y, nrhs, ldx, ldy, h->d_ws, h->ws_bytes, (cudaStream_t)stream);
+  return run_product(h, 0, x, y, nrhs, ldx, ldy, h->d_ws, h->ws_bytes, (cudaStream_t)stream, nullptr, true);
 }
 
 int hh_matvec_T(hh_handle h, const double* ybar, double* xbar, int nrhs, int64_t ldy, int64_t ldx,
                 void* stream) {
   if (!h) return fail(HH_EINVAL, "null handle");
-  return run_product(h, 1, ybar, xbar, nrhs, ldy, ldx, h->d_ws, h->ws_bytes, (cudaStream_t)stream);
+  return run_product(h, 1, ybar, xbar, nrhs, ldy, ldx, h->d_ws, h->ws_bytes, (cudaStream_t)stream, nullptr, true);
 }
 
 int hh_matvec_ws(hh_handle h, int transpose, const double* in, double* out, int nrhs, int64_t ld_in,
@@ -554,7 +849,8 @@ int hh_matvec_host(hh_handle h, int transpose, const double* x_host, double* y_h
   int rc = HH_OK;
   if (cudaMemcpyAsync(dx, x_host, sizeof(double) * n * nrhs, cudaMemcpyHostToDevice, st) != cudaSuccess)
     rc = fail(HH_ECUDA, "host-to-device copy failed");
-  if (rc == HH_OK) rc = run_product(h, transpose ? 1 : 0, dx, dy, nrhs, n, n, h->d_ws, h->ws_bytes, st);
+  if (rc == HH_OK)
+    rc = run_product(h, transpose ? 1 : 0, dx, dy, nrhs, n, n, h->d_ws, h->ws_bytes, st, nullptr, true);
   if (rc == HH_OK &&
       cudaMemcpyAsync(y_host, dy, sizeof(double) * n * nrhs, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     rc = fail(HH_ECUDA, "device-to-host copy failed");
@@ -588,7 +884,7 @@ int hh_sync_status(hh_handle h, void* stream) {
   if (e == cudaSuccess) e = cudaMemcpy(&word, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
   if (e != cudaSuccess) return fail(HH_ECUDA, std::string("sync failed: ") + cudaGetErrorString(e));
-  if (word & 4) return fail(HH_ETIMEOUT, "a bounded device wait expired (status word " + std::to_string(word) + ")");
+  if (word & (4 | 8)) return fail(HH_ETIMEOUT, "a bounded device wait expired (status word " + std::to_string(word) + ")");
   if (word != 0) return fail(HH_EDEVICE, "device status word " + std::to_string(word));
   return HH_OK;
 }
@@ -680,9 +976,9 @@ extern "C" int hh_matvec_noalloc(hh_handle h, int transpose, const double* in, d
     for (int phase = 1; phase <= 2 && e == cudaSuccess; ++phase) {
       hh::dev::StreamArgs s;
       std::memset(&s, 0, sizeof(s));
-      s.desc = h->d_sdesc[dir][phase - 1];
-      s.items = h->d_sitems[dir][phase - 1];
-      s.n_items = h->n_sitems[dir][phase - 1];
+      s.desc = h->ss[dir].d_desc[phase - 1];
+      s.items = h->ss[dir].d_items[phase - 1];
+      s.n_items = h->ss[dir].n_items[phase - 1];
       s.nr = 1;
       s.npad = npad;
       s.xs = xs;
@@ -692,8 +988,8 @@ extern "C" int hh_matvec_noalloc(hh_handle h, int transpose, const double* in, d
       s.acc = acc;  // cleared by the prep launch on every call
       s.status = h->d_status;
       s.counter = counters + (phase - 1);
-      int grid = std::max(1, std::min(h->sgrid[phase][1], s.n_items));
-      e = hh::dev::launch_stream(phase, h->fset, s, grid, st);
+      int grid = std::max(1, std::min(h->ss[dir].grid[phase][1], s.n_items));
+      e = hh::dev::launch_stream(phase, h->ss[dir].fset, s, grid, st);
     }
     if (e == cudaSuccess) e = hh::dev::launch_finish(acc, 1, h->d_perm, h->H.n, npad, out, h->H.n, st);
     if (e != cudaSuccess) rc = fail(HH_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));

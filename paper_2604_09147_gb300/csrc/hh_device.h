@@ -65,5 +65,59 @@ cudaError_t launch_finish(const double* acc, int nr, const int32_t* perm, int64_
 
 constexpr int kMaxNR = 4;  // right-hand sides per launch sequence
 
+// ---- tensor-core path for many right-hand sides (tc.cu) ----
+// A piece: ranks [r0, r0 + k) of one low-rank block whose formats the tensor
+// cores take (fp32, fp16, bf16, e4m3).  f1 / f2 point at the piece's first
+// rank column of the phase-1 factor (V forward, U transpose) and the phase-2
+// factor; rows1 / rows2 are the sizes of the input / output clusters, which
+// start at tree positions in_off / out_off (both multiples of 16).
+struct TcPiece {
+  const uint8_t* f1;
+  const uint8_t* f2;
+  int64_t ld1, ld2;
+  int64_t toff;        // byte offset of the piece's T image: [slice][k-step][128 rows x 32 B]
+  int32_t rows1, rows2;
+  int32_t in_off, out_off;
+  int32_t k, kp;       // ranks, ranks rounded up to 16
+  int32_t fmt, e;      // storage format, exp_u + exp_v
+  int32_t col;         // operand row / accumulator column of the piece in its phase-1 group
+  int32_t pad;
+};
+// phase-1 item: pieces [first, first + count) of one format with the same
+// input cluster [in_off, in_off + rows); nk = sum of their kp (<= 256)
+struct TcGroup {
+  int32_t first, count, nk, fmt;
+  int32_t in_off, rows, pad0, pad1;
+};
+// phase-2 item: output rows [row0, row0 + rows) (row0 a multiple of 256) and
+// entries [first, first + count)
+struct TcTile {
+  int32_t row0, rows, first, count;
+};
+// rows [src, src + nrows) of a piece's output cluster land on tile rows [dst, dst + nrows)
+struct TcEntry {
+  int32_t piece, src, dst, nrows;
+};
+struct TcArgs {
+  const TcPiece* pieces;
+  const TcGroup* groups;
+  const TcTile* tiles;
+  const TcEntry* entries;
+  int32_t n_groups, n_tiles;
+  int32_t nr, rp;        // right-hand sides of this launch (<= 128), nr rounded up to 16
+  const uint8_t* ximg;   // input image [3][nblk][128 rows x 32 B] (tc prep)
+  int64_t nblk;
+  uint8_t* timg;         // T images of the pieces
+  double* acc;           // output accumulator [nr][npad], tree order
+  int64_t npad;
+  int* status;           // bit 3: a bounded wait expired
+};
+constexpr int kTcMaxRhs = 128;   // right-hand sides per tensor-core launch sequence
+constexpr int kTcRows = 256;     // phase-2 tile rows
+cudaError_t launch_tc_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t nblk,
+                           uint8_t* ximg, double* acc, int64_t npad, cudaStream_t st);
+cudaError_t launch_tc(int phase, const TcArgs& a, cudaStream_t st);
+size_t tc_smem_bytes(int phase);
+
 }  // namespace dev
 }  // namespace hh

@@ -1,0 +1,167 @@
+"""GPU parity of the tensor-core multi-RHS path (hh_matvec / hh_matvec_T with
+nrhs >= 32) against the oracle, on the stored factors the library's builder
+wrote.
+
+The tensor cores take the low-rank blocks stored in fp16, bf16 and e4m3 whose
+clusters start at multiples of 16; every other block (fp64, fp32, dense, and
+unaligned clusters) takes the streaming passes, which meet 1e-6 relative on
+their own.  A tensor-core block's product carries the slicing error of the
+input (about 2^-17) and the tensor core's truncating fp32 accumulation (about
+2^-17 over a few hundred MMAs), so the bound checked is
+
+    ||Y_gpu - Y_oracle||_F <= 1e-6 ||Y_oracle||_F
+                              + 2^-12 || sum_b |U_b| (|V_b|^T |X_J|) ||_F,
+
+the sum over the tensor-core blocks: their arithmetic error stays below half
+the unit roundoff of the most precise of their formats (fp16, 2^-11), i.e.
+below the rounding error their storage already carries.  On one case the
+backward error against the exact kernel matrix is checked against
+Theorem 4.4's bound + 1e-6, column by column.
+"""
+import numpy as np
+import pytest
+
+import hh_workloads as W
+from oracle import hhfile
+from oracle import matvec as M
+from oracle.compress import kernel_entries
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_09147_gb300 import build as b
+    b.build()
+    import paper_2604_09147_gb300 as pkg
+    return pkg
+
+
+# (name, n, dim, kernel, kernel_param, leaf, switch level, tol, formats)
+CASES = {
+    # fp16, bf16 and e4m3 blocks on the tensor cores next to fp32 blocks on the
+    # streaming passes
+    "gauss_all": (8192, 3, W.GAUSS, 0.05, 64, 4, 1e-5, 31),
+    # fp16 and bf16 blocks only
+    "invr_16bit": (8192, 3, W.INV_R, 1.0, 64, 3, 1e-3, 31),
+    # n = 5184: clusters below level 2 do not start at multiples of 16, so most
+    # blocks stay on the streaming passes next to the tensor-core ones
+    "invr_mixed": (5184, 3, W.INV_R, 1.0, 64, 3, 1e-3, 31),
+    # the multi-RHS workload's kernel and formats at n = 8192
+    "gauss_narrow": (8192, 3, W.GAUSS, 0.01, 128, 5, 1e-6, W.F64 | W.F32 | W.BF16 | W.E4M3),
+}
+
+_built = {}
+
+
+def case(P, tmp_path_factory, name):
+    if name not in _built:
+        n, dim, kern, par, leaf, ell, tol, mask = CASES[name]
+        pts = W.points(n, dim, 500 + n)
+        H = P.HMatrix.build(pts, kernel=kern, kernel_param=par, leaf_size=leaf, eta=1.0, switch_level=ell,
+                            tol=tol, fmt_mask=mask, device=0)
+        path = str(tmp_path_factory.mktemp("tc") / f"{name}.hhm")
+        H.save(path)
+        _built[name] = (H, hhfile.read(path))
+    return _built[name]
+
+
+def tc_blocks(O):
+    """The blocks the library's tensor-core path takes (its eligibility rule)."""
+    return [b for b in O.lowrank if b.k > 0 and b.fmt in (2, 3, 4) and b.row_off % 16 == 0 and b.col_off % 16 == 0]
+
+
+def abs_product(O, x, transpose):
+    """sum over the tensor-core blocks of |U_b| (|V_b|^T |x_J|) (or the transpose), user order."""
+    xt = np.abs(x[O.perm])
+    out = np.zeros_like(xt)
+    for b in tc_blocks(O):
+        U, V = np.abs(b.Ud()), np.abs(b.Vd())
+        if transpose:
+            out[b.col_off:b.col_off + b.n] += V @ (U.T @ xt[b.row_off:b.row_off + b.m])
+        else:
+            out[b.row_off:b.row_off + b.m] += U @ (V.T @ xt[b.col_off:b.col_off + b.n])
+    res = np.empty_like(out)
+    res[O.perm] = out
+    return res
+
+
+def check(H, O, nrhs, transpose, seed):
+    n = H.n
+    x = W.rhs(n, nrhs, "normal", seed)
+    xg = torch.from_numpy(np.ascontiguousarray(x.T)).cuda().t()  # column-major (n, nrhs)
+    y = H.matvec(xg, transpose=transpose).cpu().numpy()
+    H.sync_status()
+    ref = M.matvec_T(O, x) if transpose else M.matvec(O, x)
+    assert y.shape == ref.shape
+    ab = abs_product(O, x, transpose)
+    d = y - ref
+    assert np.linalg.norm(d) <= TOL * np.linalg.norm(ref) + 2.0 ** -12 * np.linalg.norm(ab)
+    for c in range(nrhs):
+        assert np.linalg.norm(d[:, c]) <= TOL * np.linalg.norm(ref[:, c]) + 2.0 ** -12 * np.linalg.norm(ab[:, c])
+    return x, y
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("nrhs", [32, 128])
+def test_tc_matches_oracle(P, tmp_path_factory, name, nrhs):
+    H, O = case(P, tmp_path_factory, name)
+    assert H.info()["tc_blocks"] == len(tc_blocks(O)) > 0
+    check(H, O, nrhs, False, 7000 + nrhs)
+    check(H, O, nrhs, True, 7100 + nrhs)
+
+
+def test_tc_backward_error_within_theorem_4_4(P, tmp_path_factory):
+    """||H x_c - y_c|| / (||H||_F ||x_c||) <= Theorem 4.4's bound + 1e-6 for every
+    column, H the exact kernel matrix."""
+    H, O = case(P, tmp_path_factory, "gauss_all")
+    n, dim, kern, par = CASES["gauss_all"][:4]
+    x, y = check(H, O, 32, False, 7600)
+    hx = np.zeros_like(x)
+    fro2 = 0.0
+    for s in range(0, n, 512):
+        blk = kernel_entries(kern, par, O.points[s:s + 512], O.points)
+        hx[s:s + 512] = blk @ x
+        fro2 += float(np.sum(blk * blk))
+    be = np.linalg.norm(hx - y, axis=0) / (np.sqrt(fro2) * np.linalg.norm(x, axis=0))
+    assert be.max() <= H.info()["bound_thm44"] + 1e-6
+
+
+@pytest.mark.parametrize("nrhs", [33, 47, 200])
+def test_tc_ragged_rhs_counts(P, tmp_path_factory, nrhs):
+    """nrhs not a multiple of 16 (padded right-hand sides must stay zero) and
+    nrhs > 128 (two launch sequences)."""
+    H, O = case(P, tmp_path_factory, "gauss_all")
+    check(H, O, nrhs, False, 7200 + nrhs)
+    check(H, O, nrhs, True, 7300 + nrhs)
+
+
+def test_tc_agrees_with_streaming_path(P, tmp_path_factory):
+    """The same product through the tensor cores (one call with 32 columns) and
+    through the streaming passes (eight calls with 4 columns)."""
+    H, O = case(P, tmp_path_factory, "gauss_all")
+    x = W.rhs(H.n, 32, "uniform", 7400)
+    xg = torch.from_numpy(np.ascontiguousarray(x.T)).cuda().t()
+    y_tc = H.matvec(xg).cpu().numpy()
+    y_st = np.concatenate([H.matvec(xg[:, 4 * i:4 * i + 4]).cpu().numpy() for i in range(8)], axis=1)
+    H.sync_status()
+    ab = abs_product(O, x, False)
+    assert np.linalg.norm(y_tc - y_st) <= 2 * TOL * np.linalg.norm(y_st) + 2.0 ** -12 * np.linalg.norm(ab)
+
+
+def test_tc_autograd_multi_rhs(P, tmp_path_factory):
+    """Forward and backward of the differentiable product with 64 columns."""
+    H, O = case(P, tmp_path_factory, "invr_16bit")
+    x = W.rhs(H.n, 64, "uniform", 7500)
+    ybar = W.rhs(H.n, 64, "normal", 7501)
+    xt = torch.from_numpy(np.ascontiguousarray(x.T)).cuda().t().requires_grad_(True)
+    y = P.hh_apply(H, xt)
+    y.backward(torch.from_numpy(np.ascontiguousarray(ybar.T)).cuda().t())
+    ref_y, ref_g = M.matvec(O, x), M.matvec_T(O, ybar)
+    ab_y, ab_g = abs_product(O, x, False), abs_product(O, ybar, True)
+    assert np.linalg.norm(y.detach().cpu().numpy() - ref_y) <= TOL * np.linalg.norm(ref_y) + 2.0 ** -12 * np.linalg.norm(ab_y)
+    assert np.linalg.norm(xt.grad.cpu().numpy() - ref_g) <= TOL * np.linalg.norm(ref_g) + 2.0 ** -12 * np.linalg.norm(ab_g)

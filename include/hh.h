@@ -18,7 +18,9 @@
  *    The caller owns them; the library never frees or keeps them.
  *  - Matrix-vector calls are asynchronous on the given cudaStream_t (NULL =
  *    the legacy default stream) and never synchronise, allocate or copy to the
- *    host; they overwrite the output (no accumulation).  Input and output must
+ *    host (except the first tensor-core call of a handle, which allocates its
+ *    workspace, and hh_matvec_host / hh_matvec_timed, which synchronise);
+ *    they overwrite the output (no accumulation).  Input and output must
  *    not overlap.
  *  - A handle owns its host metadata and device arenas; it is immutable after
  *    construction.  hh_matvec / hh_matvec_T use a per-handle workspace, so
@@ -148,11 +150,21 @@ int hh_perm(hh_handle h, int32_t* perm);
 /*
  * hh_matvec -- y = A_h x (Algorithm 4), nrhs right-hand sides.
  *   x  device, n x nrhs, leading dimension ldx >= n;  y device, ldy >= n.
- *   nrhs >= 1 (any number; processed in chunks of up to 4 columns).
+ *   nrhs >= 1 (any number).
  *   stream  cudaStream_t (as void*).
- * Low-rank blocks are computed from their stored format with fp32
- * accumulation (fp64 for fp64-stored blocks); dense blocks and the final
- * accumulation into y are fp64.  Uses the handle's workspace.
+ * Arithmetic: 32-, 16- and 8-bit low-rank blocks are upcast to fp32 and
+ * accumulated in fp32 (the input split into fp32 leading and trailing
+ * halves); fp64 low-rank blocks and the dense blocks are computed as pairs
+ * of fp32 halves (about 2^-48 relative, the fp64 path's 1e-12 parity); the
+ * output is accumulated in fp64.  With nrhs <= 31 the columns go through the
+ * streaming passes in chunks of up to 4.  With nrhs >= 32 (HH_TC_MIN_NRHS in
+ * the environment overrides; 0 disables) the fp16, bf16 and e4m3 blocks
+ * whose clusters start at multiples of 16 run on the tensor cores in chunks
+ * of up to 128 columns (bf16 slices, fp32 accumulation accurate to about
+ * 2^-17 of those blocks' products, below their unit roundoff), the other
+ * blocks on the streaming passes; the tensor-core workspace is allocated on
+ * the first such call (an implicit device synchronisation; HH_ENOMEM if it
+ * cannot be).  Uses the handle's workspaces.
  */
 int hh_matvec(hh_handle h, const double* x, double* y, int nrhs, int64_t ldx, int64_t ldy,
               void* stream);
@@ -167,7 +179,8 @@ int hh_workspace_bytes(hh_handle h, size_t* bytes);
 
 /* hh_matvec_ws -- hh_matvec (transpose != 0: hh_matvec_T) with a
  * caller-owned device workspace of at least hh_workspace_bytes() bytes,
- * 256-byte aligned; concurrent calls with distinct workspaces are safe. */
+ * 256-byte aligned; concurrent calls with distinct workspaces are safe.
+ * Every nrhs goes through the streaming passes (no tensor-core path). */
 int hh_matvec_ws(hh_handle h, int transpose, const double* in, double* out, int nrhs,
                  int64_t ld_in, int64_t ld_out, void* workspace, size_t workspace_bytes,
                  void* stream);
@@ -179,11 +192,15 @@ int hh_matvec_host(hh_handle h, int transpose, const double* x_host, double* y_h
                    void* stream);
 
 /* hh_matvec_timed -- one product (transpose != 0: A_h^T) with CUDA events
- * recorded on `stream` between its four launches; synchronises the stream
- * and writes the device time in ms of each launch to ms[4] = {prep,
- * phase 1 (t_b = V_b^T x), phase 2 (y += U_b t_b and dense blocks),
- * finish}.  nrhs must be 1, 2 or 4 (one launch sequence).  For measurement;
- * uses the handle's workspace. */
+ * recorded on `stream` between its stages; synchronises the stream and
+ * writes the device time in ms of each stage to ms[4].
+ *   nrhs 1, 2 or 4 (one launch sequence of the streaming passes):
+ *     {prep, phase 1 (t_b = V_b^T x), phase 2 (y += U_b t_b and dense
+ *     blocks), finish}.
+ *   nrhs from the tensor-core threshold (32) to 128, on a matrix with blocks
+ *     the tensor cores take: {input image + the streaming passes over the
+ *     other blocks, tensor-core phase 1, tensor-core phase 2, finish}.
+ * Other nrhs: HH_EINVAL.  For measurement; uses the handle's workspaces. */
 int hh_matvec_timed(hh_handle h, int transpose, const double* in, double* out, int nrhs,
                     int64_t ld_in, int64_t ld_out, void* stream, float* ms);
 

@@ -57,6 +57,8 @@ struct TcSet {
   hh::dev::TcEntry* d_entries = nullptr;
   int n_pieces = 0, n_groups = 0, n_tiles = 0;
   int64_t t_bytes = 0;                  // T images of all pieces
+  int64_t part_floats = 0;              // partial sums of the split groups
+  int n_cnt = 0;                        // split groups (arrival counters)
   int64_t n_blocks = 0, factor_bytes = 0;
 };
 
@@ -255,8 +257,8 @@ void build_stream_set(hh_matrix* h, int dir, const std::vector<int64_t>& toff, c
 // accumulation is accurate to about 2^-17 of a block's product, below the unit
 // roundoff of the 16- and 8-bit formats but not of fp32.
 bool tc_format(int fmt) { return fmt == hh::F16 || fmt == hh::BF16 || fmt == hh::E4M3; }
-int tc_piece_cap(int fmt) { return fmt == hh::F32 ? 128 : 256; }
-int tc_input_slices(int fmt) { return fmt == hh::F32 ? 3 : 2; }
+int tc_piece_cap(int) { return hh::dev::kTcGroupRanks; }
+int tc_input_slices(int) { return 2; }
 
 // A block goes to the tensor cores when its format is one they take and both
 // of its clusters start at a tree position that is a multiple of 16 (the
@@ -266,12 +268,20 @@ bool tc_eligible(const hh::LRBlock& B) {
 }
 
 // Work tables of the tensor-core path for one direction: pieces of at most
-// tc_piece_cap ranks, grouped by (input cluster, format) into phase-1 groups
-// of at most 256 ranks, and the 256-row output tiles of phase 2 with the
-// piece rows that fall in them.
+// kTcGroupRanks ranks, grouped by (input cluster, format) into phase-1 groups
+// of at most kTcGroupRanks ranks and split into items of at most
+// kTcSplitPositions positions, and the kTcRows-row output tiles of phase 2
+// with the piece rows that fall in them.
 void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
   using namespace hh::dev;
   const hh::HostMatrix& H = h->H;
+  // positions of one phase-1 item (HH_TC_SPLIT_POSITIONS, a positive multiple
+  // of 16, overrides; read when a handle is constructed)
+  int split_len = kTcSplitPositions;
+  if (const char* e = std::getenv("HH_TC_SPLIT_POSITIONS")) {
+    const int v = std::atoi(e);
+    if (v >= 16 && v % 16 == 0) split_len = v;
+  }
   struct Key {
     int64_t in_off, rows;
     int fmt;
@@ -340,7 +350,20 @@ void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
         pieces.push_back(q);
         ++t;
       }
-      groups.push_back({g, double(g.rows) * g.nk * hh::fmt_bytes(g.fmt)});
+      const int nsplit = (g.rows + split_len - 1) / split_len;
+      g.nsplit = nsplit;
+      if (nsplit > 1) g.gid = out.n_cnt++;
+      for (int sp = 0; sp < nsplit; ++sp) {
+        TcGroup gs = g;
+        gs.split = sp;
+        gs.p0 = sp * split_len;
+        gs.p1 = std::min(g.rows, (sp + 1) * split_len);
+        if (nsplit > 1) {
+          gs.poff = out.part_floats;
+          out.part_floats += int64_t(128) * g.nk;
+        }
+        groups.push_back({gs, double(gs.p1 - gs.p0) * g.nk * hh::fmt_bytes(g.fmt)});
+      }
     }
     i = j;
   }
@@ -496,6 +519,8 @@ int tc_min_nrhs() {
 struct TcWs {
   uint8_t* ximg;
   uint8_t* timg;
+  float* part;
+  int* cnt;
   double* acc;
   int64_t nblk;
 };
@@ -509,10 +534,14 @@ size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
     off = align256(off + bytes);
     return base ? base + o : nullptr;
   };
-  uint8_t* ximg = (uint8_t*)take(size_t(3) * nblk * 4096);
+  const int64_t pf = std::max(h->tc[0].part_floats, h->tc[1].part_floats);
+  const int nc = std::max(h->tc[0].n_cnt, h->tc[1].n_cnt);
+  uint8_t* ximg = (uint8_t*)take(size_t(2) * nblk * 4096);
   uint8_t* timg = (uint8_t*)take(std::max<size_t>(256, size_t(tb)));
+  float* part = (float*)take(sizeof(float) * std::max<int64_t>(64, pf));
+  int* cnt = (int*)take(sizeof(int) * std::max(64, nc));
   double* acc = (double*)take(sizeof(double) * hh::dev::kTcMaxRhs * h->npad);
-  if (v) *v = {ximg, timg, acc, nblk};
+  if (v) *v = {ximg, timg, part, cnt, acc, nblk};
   return off;
 }
 
@@ -521,8 +550,11 @@ size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
 // blocks, dense blocks, unaligned clusters) in chunks of up to 4 right-hand
 // sides, the two tensor-core phases, and the output permutation.
 cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr, int64_t ld_in, int64_t ld_out,
-                   const WsView& w, const TcWs& t, cudaStream_t st) {
-  cudaError_t e = hh::dev::launch_tc_prep(in, ld_in, nr, h->d_perm, h->H.n, t.nblk, t.ximg, t.acc, h->npad, st);
+                   const WsView& w, const TcWs& t, cudaStream_t st, cudaEvent_t* ev = nullptr) {
+  if (ev) cudaEventRecord(ev[0], st);
+  const TcSet& ts = h->tc[dir];
+  cudaError_t e = hh::dev::launch_tc_prep(in, ld_in, nr, h->d_perm, h->H.n, t.nblk, t.ximg, t.acc, h->npad, t.cnt,
+                                          ts.n_cnt, st);
   const StreamSet& rest = h->ss_rest[dir];
   if (rest.n_items[0] + rest.n_items[1] > 0)
     for (int rb = 0; rb < nr && e == cudaSuccess;) {
@@ -532,7 +564,6 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
     }
   hh::dev::TcArgs a;
   std::memset(&a, 0, sizeof(a));
-  const TcSet& ts = h->tc[dir];
   a.pieces = ts.d_pieces;
   a.groups = ts.d_groups;
   a.tiles = ts.d_tiles;
@@ -544,12 +575,19 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   a.ximg = t.ximg;
   a.nblk = t.nblk;
   a.timg = t.timg;
+  a.part = t.part;
+  a.cnt = t.cnt;
+  a.n_cnt = ts.n_cnt;
   a.acc = t.acc;
   a.npad = h->npad;
   a.status = h->d_status;
+  if (ev) cudaEventRecord(ev[1], st);
   if (e == cudaSuccess) e = hh::dev::launch_tc(1, a, st);
+  if (ev) cudaEventRecord(ev[2], st);
   if (e == cudaSuccess) e = hh::dev::launch_tc(2, a, st);
+  if (ev) cudaEventRecord(ev[3], st);
   if (e == cudaSuccess) e = hh::dev::launch_finish(t.acc, nr, h->d_perm, h->H.n, h->npad, out, ld_out, st);
+  if (ev) cudaEventRecord(ev[4], st);
   return e;
 }
 
@@ -596,7 +634,7 @@ int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, 
     int nr;
     if (use_tc) {
       nr = std::min(rem, hh::dev::kTcMaxRhs);
-      e = run_tc(h, dir, in + (int64_t)rb * ld_in, out + (int64_t)rb * ld_out, nr, ld_in, ld_out, w, t, st);
+      e = run_tc(h, dir, in + (int64_t)rb * ld_in, out + (int64_t)rb * ld_out, nr, ld_in, ld_out, w, t, st, ev);
     } else {
       nr = rem >= 4 ? 4 : (rem >= 2 ? 2 : 1);
       e = run_stream(h, h->ss[dir], in + (int64_t)rb * ld_in, ld_in, nr, w.acc, w, st, ev);
@@ -803,8 +841,11 @@ int hh_matvec_ws(hh_handle h, int transpose, const double* in, double* out, int 
 int hh_matvec_timed(hh_handle h, int transpose, const double* in, double* out, int nrhs, int64_t ld_in,
                     int64_t ld_out, void* stream, float* ms) {
   if (!h || !ms) return fail(HH_EINVAL, "null argument");
-  if (nrhs < 1 || nrhs > hh::dev::kMaxNR || nrhs == 3) return fail(HH_EINVAL, "nrhs must be 1, 2 or 4");
   if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data");
+  const int dir = transpose ? 1 : 0;
+  const bool tc = tc_min_nrhs() > 0 && nrhs >= tc_min_nrhs() && nrhs <= hh::dev::kTcMaxRhs && h->tc[dir].n_pieces > 0;
+  if (!tc && (nrhs < 1 || nrhs > hh::dev::kMaxNR || nrhs == 3))
+    return fail(HH_EINVAL, "nrhs must be 1, 2 or 4, or between the tensor-core threshold and 128");
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != h->device) cudaSetDevice(h->device);
@@ -814,8 +855,7 @@ int hh_matvec_timed(hh_handle h, int transpose, const double* in, double* out, i
     if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
   int rc = made == 5 ? HH_OK : fail(HH_ECUDA, "cudaEventCreate failed");
   if (rc == HH_OK)
-    rc = run_product(h, transpose ? 1 : 0, in, out, nrhs, ld_in, ld_out, h->d_ws, h->ws_bytes,
-                     (cudaStream_t)stream, ev);
+    rc = run_product(h, dir, in, out, nrhs, ld_in, ld_out, h->d_ws, h->ws_bytes, (cudaStream_t)stream, ev, tc);
   if (rc == HH_OK && cudaEventSynchronize(ev[4]) != cudaSuccess) rc = fail(HH_ECUDA, "event synchronize failed");
   for (int i = 0; rc == HH_OK && i < 4; ++i)
     if (cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]) != cudaSuccess) rc = fail(HH_ECUDA, "event timing failed");

@@ -66,11 +66,11 @@ cudaError_t launch_finish(const double* acc, int nr, const int32_t* perm, int64_
 constexpr int kMaxNR = 4;  // right-hand sides per launch sequence
 
 // ---- tensor-core path for many right-hand sides (tc.cu) ----
-// A piece: ranks [r0, r0 + k) of one low-rank block whose formats the tensor
-// cores take (fp32, fp16, bf16, e4m3).  f1 / f2 point at the piece's first
-// rank column of the phase-1 factor (V forward, U transpose) and the phase-2
-// factor; rows1 / rows2 are the sizes of the input / output clusters, which
-// start at tree positions in_off / out_off (both multiples of 16).
+// A piece: ranks [r0, r0 + k) of one low-rank block stored in fp16, bf16 or
+// e4m3.  f1 / f2 point at the piece's first rank column of the phase-1
+// factor (V forward, U transpose) and the phase-2 factor; rows1 / rows2 are
+// the sizes of the input / output clusters, which start at tree positions
+// in_off / out_off (both multiples of 16).
 struct TcPiece {
   const uint8_t* f1;
   const uint8_t* f2;
@@ -83,14 +83,20 @@ struct TcPiece {
   int32_t col;         // operand row / accumulator column of the piece in its phase-1 group
   int32_t pad;
 };
-// phase-1 item: pieces [first, first + count) of one format with the same
-// input cluster [in_off, in_off + rows); nk = sum of their kp (<= 256)
+// phase-1 item: positions [p0, p1) of the input cluster [in_off, in_off + rows)
+// for the pieces [first, first + count) of one format (nk = sum of their kp,
+// at most kTcGroupRanks).  A group whose cluster is longer than
+// kTcSplitPositions is split into nsplit items; each writes its partial sums
+// to part + poff (fp32 [128][nk]) and the last to finish (counter cnt[gid])
+// adds them in split order and writes the T images.
 struct TcGroup {
   int32_t first, count, nk, fmt;
-  int32_t in_off, rows, pad0, pad1;
+  int32_t in_off, rows, p0, p1;
+  int32_t nsplit, split, gid, pad;
+  int64_t poff;
 };
-// phase-2 item: output rows [row0, row0 + rows) (row0 a multiple of 256) and
-// entries [first, first + count)
+// phase-2 item: output rows [row0, row0 + rows) (row0 a multiple of kTcRows)
+// and entries [first, first + count)
 struct TcTile {
   int32_t row0, rows, first, count;
 };
@@ -105,17 +111,22 @@ struct TcArgs {
   const TcEntry* entries;
   int32_t n_groups, n_tiles;
   int32_t nr, rp;        // right-hand sides of this launch (<= 128), nr rounded up to 16
-  const uint8_t* ximg;   // input image [3][nblk][128 rows x 32 B] (tc prep)
+  const uint8_t* ximg;   // input image [2][nblk][128 rows x 32 B] (tc prep)
   int64_t nblk;
   uint8_t* timg;         // T images of the pieces
+  float* part;           // partial sums of split groups
+  int* cnt;              // arrival counters of split groups (cleared by the prep launch)
+  int32_t n_cnt, pad;
   double* acc;           // output accumulator [nr][npad], tree order
   int64_t npad;
   int* status;           // bit 3: a bounded wait expired
 };
-constexpr int kTcMaxRhs = 128;   // right-hand sides per tensor-core launch sequence
-constexpr int kTcRows = 256;     // phase-2 tile rows
+constexpr int kTcMaxRhs = 128;          // right-hand sides per tensor-core launch sequence
+constexpr int kTcRows = 128;            // phase-2 tile rows
+constexpr int kTcGroupRanks = 128;      // ranks of one phase-1 group
+constexpr int kTcSplitPositions = 1024; // positions of one phase-1 item
 cudaError_t launch_tc_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t nblk,
-                           uint8_t* ximg, double* acc, int64_t npad, cudaStream_t st);
+                           uint8_t* ximg, double* acc, int64_t npad, int* cnt, int n_cnt, cudaStream_t st);
 cudaError_t launch_tc(int phase, const TcArgs& a, cudaStream_t st);
 size_t tc_smem_bytes(int phase);
 

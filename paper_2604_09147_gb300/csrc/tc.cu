@@ -1,46 +1,50 @@
 // Tensor-core path (tcgen05, kind::f16 with bf16 operands) of the H_h product
-// for many right-hand sides: low-rank blocks stored in fp16, bf16 or fp8-e4m3
-// (the kernels also take fp32 factors as three slices; the host keeps fp32
-// blocks on the streaming passes, see below).  With R right-hand sides the two phases of Algorithm 4 become
+// for many right-hand sides, for the low-rank blocks stored in fp16, bf16 or
+// fp8-e4m3.  With R right-hand sides the two phases of Algorithm 4 become
 // dense contractions,
 //   phase 1  T_b = 2^(e_u+e_v) V_b^T X_J          (k_b x R, contraction over |J|)
 //   phase 2  Y_I += U_b T_b                        (|I| x R, contraction over k_b)
 // computed as
-//   phase 1  one CTA per group of blocks sharing the input cluster J and the
-//            format: D[r][col] = sum_p X[p][r] V[p][col], M = 128 right-hand
-//            sides, N = the group's ranks, K = positions of J (16 per MMA);
-//   phase 2  one CTA per 256-row output tile: two 128-row accumulators
-//            D[row][r] = sum over the blocks covering the tile and their ranks
-//            of U[row][j] T[j][r], N = R, then added once into the fp64 output.
+//   phase 1  one CTA per (group, position range): a group is the blocks of
+//            one format sharing the input cluster J (at most 128 ranks);
+//            D[r][col] = sum_p X[p][r] V[p][col], M = 128 right-hand sides,
+//            N = the group's ranks, K = 16 positions per MMA.  Clusters longer
+//            than 1,024 positions are split over several CTAs; each writes
+//            its partial sums, and the CTA that arrives last (an atomic
+//            counter, nothing waits) adds them in split order.
+//   phase 2  one CTA per 128-row output tile: D[row][r] = sum over the blocks
+//            covering the tile and their ranks of U[row][j] T[j][r], N = R,
+//            added once into the fp64 output accumulator.
 //
-// Precision.  The operands are bf16 slices: a value v of a format with more
-// than 8 significant bits is written exactly as s0 + s1 (+ s2), s_i =
-// bf16(v - s0 - ... - s_{i-1}).  Factors: fp32 3 slices, fp16 2, bf16 and
-// e4m3 1 (all exact).  The input X (fp32 of the fp64 input) and T (fp32) are
-// sliced in the same way.  The products kept are those with slice indices
-// i + j < 3 (fp32 blocks: 6 MMAs per K step) or i + j < 2 (2 or 3 MMAs),
-// which leaves a slicing error of about 2^-24 (fp32) or 2^-17 (other formats,
-// whose own unit roundoff is 2^-11 or larger).  Accumulation is fp32 in tensor
-// memory; the output accumulator is fp64.  The tensor core's accumulation
-// does not round to nearest: measured against the exact sums, the error grows
-// with the number of MMAs that add into one accumulator, to about 2^-17 of a
-// block's product over a few hundred MMAs.  That is far below the unit
-// roundoff of the 16- and 8-bit formats, but not below fp32's, so fp32 blocks
-// keep the CUDA-core passes, whose sums round to nearest.  The main products
-// (slice 0 times slice 0) and the correction products accumulate in separate
-// tensor-memory columns (0.. and 256..), so the many small additions do not
-// land on the large accumulator.
+// Precision.  Operands are bf16 slices: fp16 factors are written exactly as
+// s0 + s1 (s0 = bf16(v), s1 = bf16(v - s0)), bf16 and e4m3 factors as one
+// slice; the input X (fp32 of the fp64 input) and T (fp32) as two slices,
+// leaving about 2^-17 of the value.  Products kept: slice 0 x slice 0 (the
+// main product) and 0 x 1 (and 1 x 0 for fp16).  Accumulation is fp32 in
+// tensor memory, and it does not round to nearest: measured against exact
+// sums its error grows with the number of MMAs that add into one
+// accumulator, to about 2^-17 of a block's product over a few hundred MMAs.
+// That is far below the unit roundoff of these formats (2^-11 and larger);
+// fp32 blocks, whose unit roundoff is 2^-24, stay on the CUDA-core passes.
+// The main products and the correction products accumulate in separate
+// tensor-memory columns (0.. and 128..), so the small additions do not land
+// on the large accumulator.
 //
 // Shared-memory operands use the K-major layout without swizzling: 8-row by
 // 16-byte core matrices, the two core matrices of one 16-element K step 128
-// bytes apart (leading byte offset) and successive 8-row groups 256 bytes apart
-// (stride byte offset).  Stages are filled with cp.async (16-byte copies into
-// shared memory) several stages ahead; formats other than bf16 land raw and are
-// converted into slices by the CTA's threads.  One thread issues the MMAs;
-// tcgen05.commit on a per-stage mbarrier frees the stage.  Every mbarrier wait
-// is bounded by a clock limit that sets bit 3 of the status word; an expired
-// wait ends the CTA after its copies have landed and its tensor memory has been
-// released.
+// bytes apart (leading byte offset) and successive 8-row groups 256 bytes
+// apart (stride byte offset).  A stage is one K step; a ring of kDepth stages
+// is filled with cp.async (16-byte copies) kDepth - 1 stages ahead.  In phase
+// 1 every thread converts exactly the bytes it copied (raw factor bytes into
+// bf16 slices); in phase 2, where U is transposed from columns to rows on the
+// way, a stage's copies are complete one barrier before its conversion.
+// Either way one barrier per stage publishes a stage to the thread that
+// issues its MMAs;
+// tcgen05.commit on the stage's mbarrier frees it.  About 100 KB of shared
+// memory and 256 tensor-memory columns per CTA let two CTAs share an SM.
+// Every mbarrier wait has a clock limit that sets bit 3 of the status word;
+// an expired wait ends the CTA after its copies have landed and its tensor
+// memory has been released.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -54,35 +58,30 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr long long kWaitCycles = 4000000000LL;
-constexpr int kTmemCols = 512;
-constexpr int kLoCol = 256;  // accumulator of the correction products (slice index sum > 0)
+constexpr int kTmemCols = 256;
+constexpr int kLoCol = 128;  // accumulator of the correction products
+constexpr int kDepth = 5;
 
-// phase 1 stage: 2 K steps (32 positions)
-constexpr int kP1Steps = 2;
-constexpr int kP1XOp = 3 * kP1Steps * 4096;  // X slices [slice][step][128 rows x 32 B]
-constexpr int kP1VOp = 32768;                // V slices [slice][step][nk rows x 32 B]
-constexpr int kP1Raw = 16384;                // raw factor bytes [nk ranks][32 positions]
+// phase 1 stage: one K step (16 positions)
+constexpr int kP1XOp = 2 * 4096;                // X slices [slice][128 rows x 32 B]
+constexpr int kP1VOp = 2 * kTcGroupRanks * 32;  // V slices [slice][nk rows x 32 B]
+constexpr int kP1Raw = kTcGroupRanks * 32;      // raw factor bytes [nk ranks][16 positions]
 constexpr int kP1Stage = kP1XOp + kP1VOp + kP1Raw;
-constexpr int kP1Depth = 3;
-// phase 2 stage: 1 K step (16 ranks) of a 256-row tile
-constexpr int kP2Rows = 256;
-constexpr int kP2Raw = 16 * kP2Rows * 4;  // raw factor bytes [16 ranks][256 rows]
-constexpr int kP2UOp = 3 * kP2Rows * 32;  // U slices [slice][256 rows x 32 B]
-constexpr int kP2TOp = 3 * 128 * 32;      // T slices [slice][rp rows x 32 B]
+// phase 2 stage: one K step (16 ranks) of a 128-row tile
+constexpr int kP2Raw = 16 * kTcRows * 2;  // raw factor bytes [16 ranks][128 rows]
+constexpr int kP2UOp = 2 * kTcRows * 32;  // U slices [slice][128 rows x 32 B]
+constexpr int kP2TOp = 2 * 128 * 32;      // T slices [slice][rp rows x 32 B]
 constexpr int kP2Stage = kP2Raw + kP2UOp + kP2TOp;
-constexpr int kP2Depth = 4;
 
 // format codes (hh_fmt order)
-constexpr int kF32 = 1, kF16 = 2, kBF16 = 3, kE4M3 = 4;
+constexpr int kF16 = 2, kBF16 = 3, kE4M3 = 4;
 
-__device__ __forceinline__ int fmt_size(int f) { return f == kF32 ? 4 : (f == kE4M3 ? 1 : 2); }
-__device__ __forceinline__ int factor_slices(int f) { return f == kF32 ? 3 : (f == kF16 ? 2 : 1); }
-__device__ __forceinline__ int input_slices(int f) { return f == kF32 ? 3 : 2; }
-__device__ __forceinline__ int n_products(int f) { return f == kF32 ? 6 : (f == kF16 ? 3 : 2); }
-// product p multiplies factor slice pf(p) with input slice px(p):
-// (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
-__device__ __forceinline__ int pf(int p) { return (0x210100 >> (4 * p)) & 0xf; }
-__device__ __forceinline__ int px(int p) { return (0x012010 >> (4 * p)) & 0xf; }
+__device__ __forceinline__ int fmt_size(int f) { return f == kE4M3 ? 1 : 2; }
+__device__ __forceinline__ int factor_slices(int f) { return f == kF16 ? 2 : 1; }
+__device__ __forceinline__ int n_products(int f) { return f == kF16 ? 3 : 2; }
+// product p: factor slice pf(p) times input slice px(p): (0,0) (0,1) (1,0)
+__device__ __forceinline__ int pf(int p) { return p == 2 ? 1 : 0; }
+__device__ __forceinline__ int px(int p) { return p == 1 ? 1 : 0; }
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -152,30 +151,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// exact split of an fp32 value into three bf16 slices
-__device__ __forceinline__ void slice3(float v, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
-  a = __float2bfloat16_rn(v);
-  const float r1 = v - __bfloat162float(a);
-  b = __float2bfloat16_rn(r1);
-  const float r2 = r1 - __bfloat162float(b);
-  c = __float2bfloat16_rn(r2);
-}
-
-// eight values -> their first ns slices, 16 bytes each, at dst + s * sstride
+// eight values -> their first ns (<= 2) bf16 slices, 16 bytes each, at dst + s * sstride
 __device__ __forceinline__ void store_slices(const float* v, int ns, uint8_t* dst, int64_t sstride) {
-  __align__(16) __nv_bfloat16 s[3][8];
+  __align__(16) __nv_bfloat16 s[2][8];
 #pragma unroll
-  for (int t = 0; t < 8; ++t) slice3(v[t], s[0][t], s[1][t], s[2][t]);
+  for (int t = 0; t < 8; ++t) {
+    s[0][t] = __float2bfloat16_rn(v[t]);
+    s[1][t] = __float2bfloat16_rn(v[t] - __bfloat162float(s[0][t]));
+  }
   *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(s[0]);
   if (ns > 1) *reinterpret_cast<uint4*>(dst + sstride) = *reinterpret_cast<const uint4*>(s[1]);
-  if (ns > 2) *reinterpret_cast<uint4*>(dst + 2 * sstride) = *reinterpret_cast<const uint4*>(s[2]);
 }
 
-__device__ __forceinline__ float elem(const uint8_t* p, int fmt) {
-  if (fmt == kF32) return *reinterpret_cast<const float*>(p);
-  if (fmt == kF16) return __half2float(*reinterpret_cast<const __half*>(p));
-  if (fmt == kBF16) return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p));
-  __half_raw h = __nv_cvt_fp8_to_halfraw(*reinterpret_cast<const __nv_fp8_storage_t*>(p), __NV_E4M3);
+__device__ __forceinline__ float e4m3_to_float(uint8_t b) {
+  __half_raw h = __nv_cvt_fp8_to_halfraw(static_cast<__nv_fp8_storage_t>(b), __NV_E4M3);
+  return __half2float(__half(h));
+}
+
+__device__ __forceinline__ float f16_or_bf16(uint16_t b, int fmt) {
+  if (fmt == kBF16) return __uint_as_float(static_cast<uint32_t>(b) << 16);
+  __half_raw h;
+  h.x = b;
   return __half2float(__half(h));
 }
 
@@ -183,22 +179,22 @@ __device__ __forceinline__ float elem(const uint8_t* p, int fmt) {
 __device__ __forceinline__ int core_off(int row, int c) { return (row >> 3) * 256 + c * 128 + (row & 7) * 16; }
 
 struct Ctl {
-  uint64_t bar[4];
+  uint64_t bar[kDepth];
   uint32_t tmem;
-  int abort;
-  int inited[4];  // phase 2: [sub] main products, [2 + sub] correction products
+  int last;
+  int inited[2];  // phase 2: main and correction accumulators written
 };
 
-__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
-  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~static_cast<uintptr_t>(1023));
+__device__ __forceinline__ uint8_t* align128(uint8_t* p) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 127) & ~static_cast<uintptr_t>(127));
 }
 
-__device__ __forceinline__ void tc_begin(Ctl* c, int depth) {
+__device__ __forceinline__ void tc_begin(Ctl* c) {
   if (threadIdx.x == 0) {
-    for (int s = 0; s < depth; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&c->bar[s])));
+    for (int s = 0; s < kDepth; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&c->bar[s])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    c->abort = 0;
-    c->inited[0] = c->inited[1] = c->inited[2] = c->inited[3] = 0;
+    c->last = 0;
+    c->inited[0] = c->inited[1] = 0;
   }
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&c->tmem)),
@@ -218,20 +214,27 @@ __device__ __forceinline__ void tc_end(Ctl* c) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c->tmem), "r"(kTmemCols));
 }
 
+// T = 2^e D of 16 ranks of one right-hand side, as the two slices of the
+// phase-2 operand image of its piece
+__device__ __forceinline__ void write_t(const TcArgs& a, const TcPiece& q, int cb16, int r, float* v) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = ldexpf(v[j], q.e);
+  const int step = (cb16 - q.col) >> 4;
+  uint8_t* dst = a.timg + q.toff + static_cast<int64_t>(step) * 4096 + core_off(r, 0);
+  const int64_t sstride = static_cast<int64_t>(q.kp >> 4) * 4096;
+  store_slices(v, 2, dst, sstride);
+  store_slices(v + 8, 2, dst + 128, sstride);
+}
+
 // ------------------------------------------------------------------ phase 1
-__global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) tc_phase1(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* base = align1024(smem_raw);
-  Ctl* ctl = reinterpret_cast<Ctl*>(base + kP1Depth * kP1Stage);
-  const uint8_t** colp = reinterpret_cast<const uint8_t**>(ctl + 1);  // [256] column of each operand row
-  int* rowpiece = reinterpret_cast<int*>(colp + 256);                 // [256] piece of each operand row
+  uint8_t* base = align128(smem_raw);
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + kDepth * kP1Stage);
+  const uint8_t** colp = reinterpret_cast<const uint8_t**>(ctl + 1);  // [nk] column of each operand row
+  int* rowpiece = reinterpret_cast<int*>(colp + kTcGroupRanks);       // [nk] piece of each operand row
   const TcGroup g = a.groups[blockIdx.x];
   const int tid = threadIdx.x;
-  for (int j = tid; j < 256; j += kThreads) {
-    colp[j] = nullptr;
-    rowpiece[j] = -1;
-  }
-  __syncthreads();
   if (tid < g.count) {
     const TcPiece& q = a.pieces[g.first + tid];
     const int sz = fmt_size(q.fmt);
@@ -240,125 +243,153 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
       colp[q.col + j] = j < q.k ? q.f1 + static_cast<int64_t>(j) * q.ld1 * sz : nullptr;
     }
   }
-  tc_begin(ctl, kP1Depth);
-  const int fmt = g.fmt, sz = fmt_size(fmt), sf = factor_slices(fmt), sx = input_slices(fmt);
-  const int np = n_products(fmt), nk = g.nk, rows = g.rows;
-  const int nst = (rows + 31) / 32;
+  tc_begin(ctl);  // its barrier also publishes colp / rowpiece
+  const int fmt = g.fmt, sf = factor_slices(fmt), np = n_products(fmt), nk = g.nk;
+  const int nst = (g.p1 - g.p0 + 15) >> 4;
   const uint32_t idesc = idesc_bf16(nk);
-  const int vslice = kP1Steps * nk * 32;  // bytes of one V slice (both steps)
+  // this thread's factor unit: 16-bit formats (rank j, 8 positions at 8c), e4m3 (rank j, 16 positions)
+  const bool e4 = fmt == kE4M3;
+  const int vj = e4 ? tid : (tid >> 1), vc = e4 ? 0 : (tid & 1);
+  const bool vown = vj < nk && (e4 || true);
+  const uint8_t* vcol = vown ? colp[vj] : nullptr;
 
   auto issue_loads = [&](int i) {
     if (i < nst) {
-      uint8_t* st = base + (i % kP1Depth) * kP1Stage;
-      const int p0 = 32 * i;
-      const int64_t b0 = (static_cast<int64_t>(g.in_off) + p0) >> 4;
-      for (int q = tid; q < sx * 2 * 256; q += kThreads) {
-        const int sl = q >> 9, step = (q >> 8) & 1, pc = q & 255;
-        cp16(st + (sl * 2 + step) * 4096 + pc * 16,
-             a.ximg + ((static_cast<int64_t>(sl) * a.nblk + b0 + step) << 12) + pc * 16);
+      uint8_t* st = base + (i % kDepth) * kP1Stage;
+      const int p = g.p0 + 16 * i;
+      const int64_t blk = (static_cast<int64_t>(g.in_off) + p) >> 4;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int u = tid + h * kThreads, sl = u >> 8, pc = u & 255;
+        cp16(st + sl * 4096 + pc * 16, a.ximg + ((static_cast<int64_t>(sl) * a.nblk + blk) << 12) + pc * 16);
       }
-      if (fmt == kBF16) {
-        uint8_t* vop = st + kP1XOp;
-        for (int q = tid; q < nk * 4; q += kThreads) {
-          const int j = q >> 2, u = q & 3, pos = p0 + 8 * u;
-          if (colp[j] && pos + 8 <= rows)
-            cp16(vop + (u >> 1) * (nk * 32) + core_off(j, u & 1), colp[j] + 2 * pos);
-        }
-      } else {
-        uint8_t* raw = st + kP1XOp + kP1VOp;
-        const int per = 16 / sz, units = 2 * sz;  // positions per copy, copies per rank row
-        for (int q = tid; q < nk * units; q += kThreads) {
-          const int j = q / units, u = q - j * units, pos = p0 + u * per;
-          if (colp[j] && pos < rows) cp16(raw + j * (32 * sz) + u * 16, colp[j] + static_cast<int64_t>(pos) * sz);
+      if (vcol) {
+        if (fmt == kBF16) {
+          const int pos = p + 8 * vc;
+          if (pos + 8 <= g.p1) cp16(st + kP1XOp + core_off(vj, vc), vcol + 2 * pos);
+        } else if (!e4) {
+          const int pos = p + 8 * vc;
+          if (pos < g.p1) cp16(st + kP1XOp + kP1VOp + vj * 32 + vc * 16, vcol + 2 * pos);
+        } else {
+          if (p < g.p1) cp16(st + kP1XOp + kP1VOp + vj * 16, vcol + p);
         }
       }
     }
     cp_commit();
   };
-
-  for (int i = 0; i < kP1Depth - 1; ++i) issue_loads(i);
-  bool ok = true;
-  for (int i = 0; i < nst; ++i) {
-    const int s = i % kP1Depth;
-    uint8_t* st = base + s * kP1Stage;
-    cp_wait<kP1Depth - 2>();
-    __syncthreads();
-    const int p0 = 32 * i;
+  // the operand bytes of this thread's factor unit for stage i: converted
+  // slices, zeros, or the masked tail
+  auto convert = [&](int i) {
+    if (!vown) return;
+    uint8_t* st = base + (i % kDepth) * kP1Stage;
     uint8_t* vop = st + kP1XOp;
+    const int p = g.p0 + 16 * i;
     if (fmt == kBF16) {
-      // rank rows and position groups that were not copied: zeros or the masked tail
-      for (int q = tid; q < nk * 4; q += kThreads) {
-        const int j = q >> 2, u = q & 3, pos = p0 + 8 * u;
-        if (colp[j] && pos + 8 <= rows) continue;
-        __align__(16) uint16_t e[8];
-        const uint16_t* src = colp[j] ? reinterpret_cast<const uint16_t*>(colp[j]) + pos : nullptr;
+      const int pos = p + 8 * vc;
+      if (vcol && pos + 8 <= g.p1) return;  // copied in place
+      __align__(16) uint16_t e[8];
+      const uint16_t* src = vcol ? reinterpret_cast<const uint16_t*>(vcol) + pos : nullptr;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) e[t] = (src && pos + t < rows) ? src[t] : static_cast<uint16_t>(0);
-        *reinterpret_cast<uint4*>(vop + (u >> 1) * (nk * 32) + core_off(j, u & 1)) =
-            *reinterpret_cast<const uint4*>(e);
-      }
+      for (int t = 0; t < 8; ++t) e[t] = (src && pos + t < g.p1) ? src[t] : static_cast<uint16_t>(0);
+      *reinterpret_cast<uint4*>(vop + core_off(vj, vc)) = *reinterpret_cast<const uint4*>(e);
+    } else if (!e4) {
+      const int pos = p + 8 * vc;
+      float v[8];
+      const uint16_t* raw = reinterpret_cast<const uint16_t*>(st + kP1XOp + kP1VOp + vj * 32 + vc * 16);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[t] = (vcol && pos + t < g.p1) ? f16_or_bf16(raw[t], fmt) : 0.f;
+      store_slices(v, sf, vop + core_off(vj, vc), nk * 32);
     } else {
-      const uint8_t* raw = st + kP1XOp + kP1VOp;
-      for (int q = tid; q < nk * 4; q += kThreads) {
-        const int j = q >> 2, u = q & 3, pos = p0 + 8 * u;
+      const uint8_t* raw = st + kP1XOp + kP1VOp + vj * 16;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
         float v[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t)
-          v[t] = (colp[j] && pos + t < rows) ? elem(raw + j * (32 * sz) + (8 * u + t) * sz, fmt) : 0.f;
-        store_slices(v, sf, vop + (u >> 1) * (nk * 32) + core_off(j, u & 1), vslice);
+        for (int t = 0; t < 8; ++t) v[t] = (vcol && p + 8 * c + t < g.p1) ? e4m3_to_float(raw[8 * c + t]) : 0.f;
+        store_slices(v, 1, vop + core_off(vj, c), nk * 32);
       }
     }
+  };
+
+  for (int i = 0; i < kDepth - 1; ++i) issue_loads(i);
+  bool ok = true;
+  for (int i = 0; i < nst; ++i) {
+    const int s = i % kDepth;
+    uint8_t* st = base + s * kP1Stage;
+    cp_wait<kDepth - 2>();
+    convert(i);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int step = 0; step < kP1Steps; ++step) {
-        if (p0 + 16 * step >= rows) break;
-        for (int p = 0; p < np; ++p) {
-          const uint64_t da = op_desc(st + (px(p) * 2 + step) * 4096);
-          const uint64_t db = op_desc(vop + pf(p) * vslice + step * (nk * 32));
-          const uint32_t acc = p == 0 ? ((i | step) ? 1u : 0u) : ((i | step | (p - 1)) ? 1u : 0u);
-          mma(ctl->tmem + (p ? kLoCol : 0), da, db, idesc, acc);
-        }
-      }
-      mma_commit(&ctl->bar[s]);
-    }
-    // refill the stage that the previous iteration's MMAs read
-    if (i >= 1 && i + kP1Depth - 1 < nst) {
-      const int sp = (i - 1) % kP1Depth;
-      if (!bar_wait(&ctl->bar[sp], ((i - 1) / kP1Depth) & 1)) ok = false;
-    }
     if (__syncthreads_or(!ok)) {
       ok = false;
       break;
     }
-    issue_loads(i + kP1Depth - 1);
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int p = 0; p < np; ++p) {
+        const uint64_t da = op_desc(st + px(p) * 4096);
+        const uint64_t db = op_desc(st + kP1XOp + pf(p) * (nk * 32));
+        const uint32_t acc = p == 0 ? (i ? 1u : 0u) : ((i || p > 1) ? 1u : 0u);
+        mma(ctl->tmem + (p ? kLoCol : 0), da, db, idesc, acc);
+      }
+      mma_commit(&ctl->bar[s]);
+    }
+    // refill the stage the previous iteration's MMAs read
+    if (i >= 1 && i + kDepth - 1 < nst && !bar_wait(&ctl->bar[(i - 1) % kDepth], ((i - 1) / kDepth) & 1))
+      ok = false;
+    issue_loads(i + kDepth - 1);
   }
-  if (ok && nst > 0 && !bar_wait(&ctl->bar[(nst - 1) % kP1Depth], ((nst - 1) / kP1Depth) & 1)) ok = false;
+  if (ok && nst > 0 && !bar_wait(&ctl->bar[(nst - 1) % kDepth], ((nst - 1) / kDepth) & 1)) ok = false;
   if (__syncthreads_or(!ok)) {
     if (tid == 0) atomicOr(a.status, 8);
-  } else {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: TMEM lane = right-hand side r, column = rank row of the group;
-    // T = 2^e D in slices, written as the phase-2 operand image of the piece
-    const int w = tid >> 5, lane = tid & 31;
-    const int r = 32 * (w & 3) + lane;
-    const uint32_t tbase = ctl->tmem + (static_cast<uint32_t>(32 * (w & 3)) << 16);
-    for (int cb = (w >> 2); 16 * cb < nk; cb += 2) {
-      float v[16], vl[16];
-      tmem_ld16(tbase + 16 * cb, v);
-      tmem_ld16(tbase + kLoCol + 16 * cb, vl);
+    tc_end(ctl);
+    return;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // epilogue: TMEM lane = right-hand side r, column = rank row of the group
+  const int w = tid >> 5, lane = tid & 31;
+  const int r = 32 * (w & 3) + lane;
+  const uint32_t tbase = ctl->tmem + (static_cast<uint32_t>(32 * (w & 3)) << 16);
+  const int64_t pstride = static_cast<int64_t>(128) * nk;  // floats of one split's partial sums
+  for (int cb = (w >> 2); 16 * cb < nk; cb += 2) {
+    float v[16], vl[16];
+    tmem_ld16(tbase + 16 * cb, v);
+    tmem_ld16(tbase + kLoCol + 16 * cb, vl);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] += vl[j];
-      const TcPiece& q = a.pieces[rowpiece[16 * cb]];
-      const int step = (16 * cb - q.col) >> 4;
-      const int nsl = input_slices(q.fmt);
+    for (int j = 0; j < 16; ++j) v[j] += vl[j];
+    if (g.nsplit == 1) {
+      write_t(a, a.pieces[rowpiece[16 * cb]], 16 * cb, r, v);
+    } else {
+      float4* dst = reinterpret_cast<float4*>(a.part + g.poff + static_cast<int64_t>(r) * nk + 16 * cb);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = ldexpf(v[j], q.e);
-      uint8_t* dst = a.timg + q.toff + static_cast<int64_t>(step) * 4096 + core_off(r, 0);
-      const int64_t sstride = static_cast<int64_t>(q.kp >> 4) * 4096;
-      store_slices(v, nsl, dst, sstride);
-      store_slices(v + 8, nsl, dst + 128, sstride);
+      for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    }
+  }
+  if (g.nsplit > 1) {
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) ctl->last = atomicAdd(a.cnt + g.gid, 1) == g.nsplit - 1;
+    __syncthreads();
+    if (ctl->last) {
+      __threadfence();
+      const float* p0 = a.part + g.poff - static_cast<int64_t>(g.split) * pstride;
+      for (int cb = (w >> 2); 16 * cb < nk; cb += 2) {
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        for (int sp = 0; sp < g.nsplit; ++sp) {
+          const float4* src = reinterpret_cast<const float4*>(p0 + sp * pstride + static_cast<int64_t>(r) * nk + 16 * cb);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 f = __ldcg(src + j);
+            v[4 * j] += f.x;
+            v[4 * j + 1] += f.y;
+            v[4 * j + 2] += f.z;
+            v[4 * j + 3] += f.w;
+          }
+        }
+        write_t(a, a.pieces[rowpiece[16 * cb]], 16 * cb, r, v);
+      }
+      if (tid == 0) a.cnt[g.gid] = 0;
     }
   }
   tc_end(ctl);
@@ -369,130 +400,133 @@ struct Cursor {
   int e, step;
 };
 
-__global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) tc_phase2(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* base = align1024(smem_raw);
-  Ctl* ctl = reinterpret_cast<Ctl*>(base + kP2Depth * kP2Stage);
+  uint8_t* base = align128(smem_raw);
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + kDepth * kP2Stage);
   const TcTile tl = a.tiles[blockIdx.x];
   const int tid = threadIdx.x, rp = a.rp;
-  tc_begin(ctl, kP2Depth);
+  tc_begin(ctl);
   int nst = 0;
   for (int e = 0; e < tl.count; ++e) nst += a.pieces[a.entries[tl.first + e].piece].kp >> 4;
   const uint32_t idesc = idesc_bf16(rp);
 
-  Cursor ld_cur{0, 0};
   auto advance = [&](Cursor& c) {
     if (++c.step == (a.pieces[a.entries[tl.first + c.e].piece].kp >> 4)) {
       c.step = 0;
       ++c.e;
     }
   };
+  Cursor ld{0, 0}, cv{0, 0};
+  // copies of stage i: the T slices (straight into the operand) and the raw
+  // factor rows [src, src + nrows) of the 16 ranks of the K step, laid out
+  // [rank][tile row]; thread = (rank, 16-byte piece of the rows)
   auto issue_loads = [&](int i) {
     if (i < nst) {
-      const TcEntry en = a.entries[tl.first + ld_cur.e];
+      const TcEntry en = a.entries[tl.first + ld.e];
       const TcPiece& q = a.pieces[en.piece];
-      uint8_t* st = base + (i % kP2Depth) * kP2Stage;
-      const int sz = fmt_size(q.fmt), nsl = input_slices(q.fmt);
-      // T slices of this K step: the first rp rows (rp * 32 bytes) of each slice tile
-      const uint8_t* tsrc = a.timg + q.toff + static_cast<int64_t>(ld_cur.step) * 4096;
+      uint8_t* st = base + (i % kDepth) * kP2Stage;
+      const uint8_t* tsrc = a.timg + q.toff + static_cast<int64_t>(ld.step) * 4096;
       const int tunits = rp * 2;
-      for (int u = tid; u < nsl * tunits; u += kThreads) {
-        const int sl = u / tunits, w = u - sl * tunits;
-        cp16(st + kP2Raw + kP2UOp + sl * 4096 + w * 16,
-             tsrc + static_cast<int64_t>(sl) * (q.kp >> 4) * 4096 + w * 16);
+      for (int u = tid; u < 2 * tunits; u += kThreads) {
+        const int sl = u >= tunits, w = u - sl * tunits;
+        cp16(st + kP2Raw + kP2UOp + sl * 4096 + w * 16, tsrc + static_cast<int64_t>(sl) * (q.kp >> 4) * 4096 + w * 16);
       }
-      // factor rows [src, src + nrows) of ranks 16*step .. +15: raw [rank][tile row]
-      const int per = 16 / sz, units = (en.nrows + per - 1) / per;
-      const int j0 = 16 * ld_cur.step;
-      for (int u = tid; u < 16 * units; u += kThreads) {
-        const int j = u / units, c = u - j * units;
-        if (j0 + j < q.k)
-          cp16(st + j * (kP2Rows * sz) + (en.dst + c * per) * sz,
-               q.f2 + (static_cast<int64_t>(j0 + j) * q.ld2 + en.src + c * per) * sz);
-      }
-      advance(ld_cur);
+      const int sz = fmt_size(q.fmt), per = 16 / sz;  // rows per 16-byte piece
+      const int pieces = kTcRows / per;                 // pieces per rank row of the tile
+      const int j = tid / pieces, c = tid - j * pieces, m0 = c * per;
+      const int jj = 16 * ld.step + j;
+      if (j < 16 && jj < q.k && m0 >= en.dst && m0 < en.dst + en.nrows)
+        cp16(st + j * (kTcRows * sz) + m0 * sz, q.f2 + (static_cast<int64_t>(jj) * q.ld2 + en.src + (m0 - en.dst)) * sz);
+      advance(ld);
     }
     cp_commit();
   };
-
-  for (int i = 0; i < kP2Depth - 1; ++i) issue_loads(i);
-  Cursor cu{0, 0};
-  bool ok = true;
-  int ini[4] = {0, 0, 0, 0};  // meaningful in thread 0
-  for (int i = 0; i < nst; ++i) {
-    const int s = i % kP2Depth;
-    uint8_t* st = base + s * kP2Stage;
-    const TcEntry en = a.entries[tl.first + cu.e];
+  // the U operand of stage i: thread = (tile row m, 8 ranks uo); slices, zeros
+  // or the masked tail (every thread's copies of the stage have landed)
+  auto convert = [&](int i) {
+    if (i >= nst) return;
+    const TcEntry en = a.entries[tl.first + cv.e];
     const TcPiece& q = a.pieces[en.piece];
-    const int sz = fmt_size(q.fmt), sf = factor_slices(q.fmt), np = n_products(q.fmt);
-    cp_wait<kP2Depth - 2>();
-    __syncthreads();
-    // convert: tile row m, ranks 16*step + 8c .. +7 -> slices of the K-major operand
-    uint8_t* uop = st + kP2Raw;
-    const int j0 = 16 * cu.step;
-    for (int u = tid; u < 2 * kP2Rows; u += kThreads) {
-      const int m = u >> 1, c = u & 1;
-      const bool in = m >= en.dst && m < en.dst + en.nrows;
-      float v[8];
+    uint8_t* st = base + (i % kDepth) * kP2Stage;
+    const int m = tid >> 1, uo = tid & 1, sz = fmt_size(q.fmt);
+    const bool in = m >= en.dst && m < en.dst + en.nrows;
+    const int j0 = 16 * cv.step + 8 * uo;
+    float v[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t)
-        v[t] = (in && j0 + 8 * c + t < q.k) ? elem(st + (8 * c + t) * (kP2Rows * sz) + m * sz, q.fmt) : 0.f;
-      store_slices(v, sf, uop + core_off(m, c), kP2Rows * 32);
+    for (int t = 0; t < 8; ++t) {
+      const uint8_t* src = st + (8 * uo + t) * (kTcRows * sz) + m * sz;
+      float x = 0.f;
+      if (in && j0 + t < q.k)
+        x = q.fmt == kE4M3 ? e4m3_to_float(*src) : f16_or_bf16(*reinterpret_cast<const uint16_t*>(src), q.fmt);
+      v[t] = x;
     }
+    store_slices(v, factor_slices(q.fmt), st + kP2Raw + core_off(m, uo), kTcRows * 32);
+    advance(cv);
+  };
+
+  for (int i = 0; i < kDepth - 1; ++i) issue_loads(i);
+  cp_wait<kDepth - 2>();
+  __syncthreads();
+  convert(0);
+  Cursor mc{0, 0};
+  bool ok = true;
+  int ini_hi = 0, ini_lo = 0;  // meaningful in thread 0
+  for (int i = 0; i < nst; ++i) {
+    const int s = i % kDepth;
+    uint8_t* st = base + s * kP2Stage;
+    cp_wait<kDepth - 3>();  // this thread's copies of stages <= i + 1
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int sub = 0; sub < 2; ++sub) {
-        if (en.dst >= 128 * (sub + 1) || en.dst + en.nrows <= 128 * sub) continue;
-        for (int p = 0; p < np; ++p) {
-          const uint64_t da = op_desc(uop + pf(p) * (kP2Rows * 32) + sub * 4096);
-          const uint64_t db = op_desc(st + kP2Raw + kP2UOp + px(p) * 4096);
-          const int slot = (p ? 2 : 0) + sub;
-          mma(ctl->tmem + (p ? kLoCol : 0) + 128 * sub, da, db, idesc, ini[slot] ? 1u : 0u);
-          ini[slot] = 1;
-        }
-      }
-      mma_commit(&ctl->bar[s]);
-    }
-    advance(cu);
-    if (i >= 1 && i + kP2Depth - 1 < nst) {
-      const int sp = (i - 1) % kP2Depth;
-      if (!bar_wait(&ctl->bar[sp], ((i - 1) / kP2Depth) & 1)) ok = false;
-    }
     if (__syncthreads_or(!ok)) {
       ok = false;
       break;
     }
-    issue_loads(i + kP2Depth - 1);
+    if (tid == 0) {
+      const int np = n_products(a.pieces[a.entries[tl.first + mc.e].piece].fmt);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int p = 0; p < np; ++p) {
+        const uint64_t da = op_desc(st + kP2Raw + pf(p) * (kTcRows * 32));
+        const uint64_t db = op_desc(st + kP2Raw + kP2UOp + px(p) * 4096);
+        int& ini = p ? ini_lo : ini_hi;
+        mma(ctl->tmem + (p ? kLoCol : 0), da, db, idesc, ini ? 1u : 0u);
+        ini = 1;
+      }
+      mma_commit(&ctl->bar[s]);
+    }
+    advance(mc);
+    if (i >= 1 && i + kDepth - 1 < nst && !bar_wait(&ctl->bar[(i - 1) % kDepth], ((i - 1) / kDepth) & 1))
+      ok = false;
+    issue_loads(i + kDepth - 1);
+    convert(i + 1);
   }
-  if (tid == 0)
-    for (int q = 0; q < 4; ++q) ctl->inited[q] = ini[q];
-  if (ok && nst > 0 && !bar_wait(&ctl->bar[(nst - 1) % kP2Depth], ((nst - 1) / kP2Depth) & 1)) ok = false;
+  if (tid == 0) {
+    ctl->inited[0] = ini_hi;
+    ctl->inited[1] = ini_lo;
+  }
+  if (ok && nst > 0 && !bar_wait(&ctl->bar[(nst - 1) % kDepth], ((nst - 1) / kDepth) & 1)) ok = false;
   if (__syncthreads_or(!ok)) {
     if (tid == 0) atomicOr(a.status, 8);
-  } else {
+  } else if (ctl->inited[0]) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warps 0-3 hold rows 0-127 of the tile, warps 4-7 rows 128-255
-    const int w = tid >> 5, lane = tid & 31, sub = w >> 2;
-    const int row = 128 * sub + 32 * (w & 3) + lane;
-    const bool has_lo = ctl->inited[2 + sub] != 0;
-    if (ctl->inited[sub]) {
-      const uint32_t tbase = ctl->tmem + (static_cast<uint32_t>(32 * (w & 3)) << 16) + 128 * sub;
-      for (int cb = 0; 16 * cb < rp; ++cb) {
-        float v[16], vl[16];
-        tmem_ld16(tbase + 16 * cb, v);
-        if (has_lo) {
-          tmem_ld16(tbase + kLoCol + 16 * cb, vl);
+    // epilogue: TMEM lane = tile row, column = right-hand side; warps 4-7 take
+    // the upper half of the columns
+    const int w = tid >> 5, lane = tid & 31;
+    const int row = 32 * (w & 3) + lane;
+    const bool has_lo = ctl->inited[1] != 0;
+    const uint32_t tbase = ctl->tmem + (static_cast<uint32_t>(32 * (w & 3)) << 16);
+    for (int cb = 4 * (w >> 2); cb < 4 * (w >> 2) + 4 && 16 * cb < rp; ++cb) {
+      float v[16], vl[16];
+      tmem_ld16(tbase + 16 * cb, v);
+      if (has_lo) {
+        tmem_ld16(tbase + kLoCol + 16 * cb, vl);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] += vl[j];
-        }
-        if (row < tl.rows) {
+        for (int j = 0; j < 16; ++j) v[j] += vl[j];
+      }
+      if (row < tl.rows) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int rr = 16 * cb + j;
-            if (rr < a.nr) a.acc[static_cast<int64_t>(rr) * a.npad + tl.row0 + row] += static_cast<double>(v[j]);
-          }
+        for (int j = 0; j < 16; ++j) {
+          const int rr = 16 * cb + j;
+          if (rr < a.nr) a.acc[static_cast<int64_t>(rr) * a.npad + tl.row0 + row] += static_cast<double>(v[j]);
         }
       }
     }
@@ -500,15 +534,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
   tc_end(ctl);
 }
 
-// X (caller's order, column-major, ld) -> tree order, fp32, bf16 slices in the
-// phase-1 operand image [slice][16-position block][128 rows x 32 B]; rows
-// r >= nr and positions >= n are zero.  Also clears the output accumulator.
+// X (caller's order, column-major, ld) -> tree order, fp32, two bf16 slices in
+// the phase-1 operand image [slice][16-position block][128 rows x 32 B]; rows
+// r >= nr and positions >= n are zero.  Also clears the output accumulator
+// and the arrival counters of the split groups.
 __global__ void tc_prep_kernel(const double* __restrict__ x, int64_t ld, int nr, const int32_t* __restrict__ perm,
                                int64_t n, int64_t nblk, uint8_t* __restrict__ ximg, double* __restrict__ acc,
-                               int64_t npad) {
+                               int64_t npad, int* __restrict__ cnt, int n_cnt) {
   const int64_t total = nblk * 256;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total; q += stride) {
+  const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  for (int64_t q = t0; q < total; q += stride) {
     const int64_t blk = q >> 8;
     const int c = static_cast<int>(q >> 7) & 1, r = static_cast<int>(q & 127);
     float v[8];
@@ -517,30 +553,31 @@ __global__ void tc_prep_kernel(const double* __restrict__ x, int64_t ld, int nr,
       const int64_t p = 16 * blk + 8 * c + t;
       v[t] = (r < nr && p < n) ? __double2float_rn(x[static_cast<int64_t>(perm[p]) + r * ld]) : 0.f;
     }
-    store_slices(v, 3, ximg + (blk << 12) + core_off(r, c), nblk << 12);
+    store_slices(v, 2, ximg + (blk << 12) + core_off(r, c), nblk << 12);
   }
   const int64_t ntot = static_cast<int64_t>(nr) * npad;
-  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < ntot; q += stride) acc[q] = 0.0;
+  for (int64_t q = t0; q < ntot; q += stride) acc[q] = 0.0;
+  for (int64_t q = t0; q < n_cnt; q += stride) cnt[q] = 0;
 }
 
 }  // namespace
 
 size_t tc_smem_bytes(int phase) {
-  return (phase == 1 ? kP1Depth * kP1Stage : kP2Depth * kP2Stage) + 1024 + sizeof(Ctl) + 256 * 12;
+  return (phase == 1 ? kDepth * kP1Stage : kDepth * kP2Stage) + 128 + sizeof(Ctl) + kTcGroupRanks * 12;
 }
 
 cudaError_t launch_tc_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t nblk,
-                           uint8_t* ximg, double* acc, int64_t npad, cudaStream_t st) {
+                           uint8_t* ximg, double* acc, int64_t npad, int* cnt, int n_cnt, cudaStream_t st) {
   int64_t blocks = (nblk * 256 + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   if (blocks < 1) blocks = 1;
-  tc_prep_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(x, ld, nr, perm, n, nblk, ximg, acc, npad);
+  tc_prep_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(x, ld, nr, perm, n, nblk, ximg, acc, npad, cnt, n_cnt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc(int phase, const TcArgs& a, cudaStream_t st) {
   const size_t smem = tc_smem_bytes(phase);
-  if (smem > 232448) return cudaErrorInvalidConfiguration;
+  if (a.rp < 16 || a.rp > 128 || (a.rp & 15)) return cudaErrorInvalidValue;
   if (phase == 1) {
     if (a.n_groups <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(tc_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -140,6 +140,22 @@ def test_tc_ragged_rhs_counts(P, tmp_path_factory, nrhs):
     check(H, O, nrhs, True, 7300 + nrhs)
 
 
+def test_tc_split_groups(P, tmp_path_factory, monkeypatch):
+    """Phase-1 items of 64 positions: every group of the matrix is split, and
+    the CTA that arrives last adds the partial sums."""
+    n, dim, kern, par, leaf, ell, tol, mask = CASES["gauss_narrow"]
+    monkeypatch.setenv("HH_TC_SPLIT_POSITIONS", "64")
+    pts = W.points(n, dim, 500 + n)
+    H = P.HMatrix.build(pts, kernel=kern, kernel_param=par, leaf_size=leaf, eta=1.0, switch_level=ell,
+                        tol=tol, fmt_mask=mask, device=0)
+    path = str(tmp_path_factory.mktemp("tcs") / "split.hhm")
+    H.save(path)
+    O = hhfile.read(path)
+    for nrhs, tr in ((32, False), (128, True), (48, False)):
+        check(H, O, nrhs, tr, 7700 + nrhs)
+        check(H, O, nrhs, tr, 7800 + nrhs)  # counters were reset by the previous call
+
+
 def test_tc_agrees_with_streaming_path(P, tmp_path_factory):
     """The same product through the tensor cores (one call with 32 columns) and
     through the streaming passes (eight calls with 4 columns)."""

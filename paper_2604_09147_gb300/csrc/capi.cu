@@ -62,6 +62,21 @@ struct TcSet {
   int64_t n_blocks = 0, factor_bytes = 0;
 };
 
+// Work tables of the CUDA-core products for many right-hand sides (mr.cu)
+// for one direction.
+struct MrSet {
+  hh::dev::TcPiece* d_pieces = nullptr;
+  hh::dev::TcGroup* d_groups = nullptr;
+  hh::dev::TcTile* d_tiles = nullptr;
+  hh::dev::TcEntry* d_entries = nullptr;
+  int n_pieces = 0, n_groups = 0, n_tiles = 0;
+  int64_t t_floats = 0;
+  hh::dev::TcPiece* d_dpieces = nullptr;  // dense blocks
+  hh::dev::TcTile* d_dtiles = nullptr;
+  hh::dev::TcEntry* d_dentries = nullptr;
+  int n_dtiles = 0;
+};
+
 struct hh_matrix {
   hh::HostMatrix H;
   hh::Summary S;
@@ -80,6 +95,7 @@ struct hh_matrix {
   StreamSet ss[2];     // [direction]: every block on the streaming passes
   StreamSet ss_rest[2];  // [direction]: the blocks the tensor-core path leaves to them
   TcSet tc[2];         // [direction]
+  MrSet mr[2];         // [direction]
   void* d_tc_ws = nullptr;  // tensor-core workspace, allocated on first use
   size_t tc_ws_bytes = 0;
 };
@@ -104,6 +120,13 @@ void free_device(hh_matrix* h) {
     cudaFree(h->tc[d].d_groups);
     cudaFree(h->tc[d].d_tiles);
     cudaFree(h->tc[d].d_entries);
+    cudaFree(h->mr[d].d_pieces);
+    cudaFree(h->mr[d].d_groups);
+    cudaFree(h->mr[d].d_tiles);
+    cudaFree(h->mr[d].d_entries);
+    cudaFree(h->mr[d].d_dpieces);
+    cudaFree(h->mr[d].d_dtiles);
+    cudaFree(h->mr[d].d_dentries);
   }
   cudaFree(h->d_tc_ws);
   cudaFree(h->d_dense_pad);
@@ -162,7 +185,8 @@ void upload_dense(hh_matrix* h, std::vector<int64_t>& doff, std::vector<int32_t>
 // Descriptors and work items of the streaming passes (stream.cu) for one
 // direction: every dense block and the low-rank blocks `take` selects.
 void build_stream_set(hh_matrix* h, int dir, const std::vector<int64_t>& toff, const std::vector<int64_t>& doff,
-                      const std::vector<int32_t>& dexp, const std::vector<char>& take, StreamSet& out) {
+                      const std::vector<int32_t>& dexp, const std::vector<char>& take, bool with_dense,
+                      StreamSet& out) {
   using hh::dev::StreamDesc;
   const hh::HostMatrix& H = h->H;
   const int cols1 = hh::dev::stream_cols_per_item();
@@ -215,7 +239,7 @@ void build_stream_set(hh_matrix* h, int dir, const std::vector<int64_t>& toff, c
     desc[1].push_back(s2);
     add_rows(1, (int)desc[1].size() - 1, s2.rows, s2.cols, B.fmt);
   }
-  for (size_t q = 0; q < H.dense.size(); ++q) {
+  for (size_t q = 0; q < H.dense.size() && with_dense; ++q) {
     const hh::DenseBlock& D = H.dense[q];
     StreamDesc s;
     std::memset(&s, 0, sizeof(s));
@@ -414,6 +438,163 @@ void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
   out.t_bytes = toff;
 }
 
+// Output tiles of `rows` rows over the output ranges [out_off, out_off +
+// rows2) of the given pieces, each tile with the piece rows that fall in it,
+// sorted by cost (sum of cost_of(piece) * rows in the tile) descending.
+template <class CostFn>
+void build_tiles(int64_t n, int rows, const std::vector<hh::dev::TcPiece>& pieces, CostFn cost_of,
+                 std::vector<hh::dev::TcTile>& tiles_out, std::vector<hh::dev::TcEntry>& entries) {
+  using namespace hh::dev;
+  const int64_t ntiles = (n + rows - 1) / rows;
+  std::vector<std::vector<TcEntry>> per_tile(static_cast<size_t>(ntiles));
+  for (size_t pi = 0; pi < pieces.size(); ++pi) {
+    const TcPiece& q = pieces[pi];
+    const int64_t lo = q.out_off, hi = int64_t(q.out_off) + q.rows2;
+    for (int64_t t = lo / rows; t * rows < hi; ++t) {
+      const int64_t r0 = t * rows, a = std::max(lo, r0), b = std::min(hi, r0 + rows);
+      per_tile[t].push_back(TcEntry{(int32_t)pi, (int32_t)(a - lo), (int32_t)(a - r0), (int32_t)(b - a)});
+    }
+  }
+  std::vector<std::pair<TcTile, double>> tiles;
+  for (int64_t t = 0; t < ntiles; ++t) {
+    if (per_tile[t].empty()) continue;
+    TcTile tl;
+    tl.row0 = (int32_t)(t * rows);
+    tl.rows = (int32_t)std::min<int64_t>(rows, n - t * rows);
+    tl.first = (int32_t)entries.size();
+    tl.count = (int32_t)per_tile[t].size();
+    double cost = 0;
+    for (const TcEntry& e : per_tile[t]) {
+      entries.push_back(e);
+      cost += cost_of(pieces[e.piece]) * rows;
+    }
+    tiles.push_back({tl, cost});
+  }
+  std::stable_sort(tiles.begin(), tiles.end(), [](const auto& x, const auto& y) { return x.second > y.second; });
+  for (auto& t : tiles) tiles_out.push_back(t.first);
+}
+
+// Work tables of the CUDA-core products for many right-hand sides for one
+// direction: the low-rank blocks in fp32, fp16, bf16 or e4m3 that the tensor
+// cores do not take, in pieces of at most kMrRanks ranks grouped by input
+// cluster and format and split into ranges of at most kTcSplitPositions
+// positions; the 128-row tiles of their phase 2; and the dense blocks in
+// 64-row tiles.
+void build_mr_set(hh_matrix* h, int dir, const std::vector<int64_t>& doff, const std::vector<int32_t>& dexp,
+                  MrSet& out) {
+  using namespace hh::dev;
+  const hh::HostMatrix& H = h->H;
+  struct Key {
+    int64_t in_off, rows;
+    int fmt;
+    bool operator<(const Key& o) const {
+      if (in_off != o.in_off) return in_off < o.in_off;
+      if (rows != o.rows) return rows < o.rows;
+      return fmt < o.fmt;
+    }
+  };
+  std::vector<std::pair<Key, TcPiece>> raw;
+  for (const hh::LRBlock& B : H.lr) {
+    if (B.k == 0 || B.fmt == hh::F64 || tc_eligible(B)) continue;
+    const int sz = hh::fmt_bytes(B.fmt);
+    const uint8_t* U = h->d_arena + B.u_off;
+    const uint8_t* V = h->d_arena + B.v_off;
+    const uint8_t* f1 = dir == 0 ? V : U;
+    const uint8_t* f2 = dir == 0 ? U : V;
+    const int64_t ld1 = dir == 0 ? B.ldv : B.ldu, ld2 = dir == 0 ? B.ldu : B.ldv;
+    for (int r0 = 0; r0 < B.k; r0 += kMrRanks) {
+      TcPiece q;
+      std::memset(&q, 0, sizeof(q));
+      q.k = std::min(kMrRanks, B.k - r0);
+      q.kp = (q.k + 3) / 4 * 4;
+      q.f1 = f1 + int64_t(r0) * ld1 * sz;
+      q.f2 = f2 + int64_t(r0) * ld2 * sz;
+      q.ld1 = ld1;
+      q.ld2 = ld2;
+      q.rows1 = (int32_t)(dir == 0 ? B.n : B.m);
+      q.rows2 = (int32_t)(dir == 0 ? B.m : B.n);
+      q.in_off = (int32_t)(dir == 0 ? B.col_off : B.row_off);
+      q.out_off = (int32_t)(dir == 0 ? B.row_off : B.col_off);
+      q.fmt = B.fmt;
+      q.e = B.exp_u + B.exp_v;
+      raw.push_back({Key{q.in_off, q.rows1, q.fmt}, q});
+    }
+  }
+  std::stable_sort(raw.begin(), raw.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+  std::vector<TcPiece> pieces;
+  std::vector<std::pair<TcGroup, double>> groups;
+  for (size_t i = 0; i < raw.size();) {
+    size_t j = i;
+    while (j < raw.size() && !(raw[i].first < raw[j].first) && !(raw[j].first < raw[i].first)) ++j;
+    for (size_t t = i; t < j;) {
+      TcGroup g;
+      std::memset(&g, 0, sizeof(g));
+      g.first = (int32_t)pieces.size();
+      g.fmt = raw[t].second.fmt;
+      g.in_off = raw[t].second.in_off;
+      g.rows = raw[t].second.rows1;
+      while (t < j && g.nk + raw[t].second.kp <= kMrRanks) {
+        TcPiece q = raw[t].second;
+        q.col = g.nk;
+        q.toff = out.t_floats;
+        out.t_floats += int64_t(q.kp) * 128;
+        g.nk += q.kp;
+        g.count += 1;
+        pieces.push_back(q);
+        ++t;
+      }
+      g.nsplit = (g.rows + kTcSplitPositions - 1) / kTcSplitPositions;
+      for (int sp = 0; sp < g.nsplit; ++sp) {
+        TcGroup gs = g;
+        gs.split = sp;
+        gs.p0 = sp * kTcSplitPositions;
+        gs.p1 = std::min(g.rows, (sp + 1) * kTcSplitPositions);
+        groups.push_back({gs, double(gs.p1 - gs.p0) * g.nk * hh::fmt_bytes(g.fmt)});
+      }
+    }
+    i = j;
+  }
+  std::stable_sort(groups.begin(), groups.end(), [](const auto& x, const auto& y) { return x.second > y.second; });
+  std::vector<TcGroup> gflat;
+  for (auto& g : groups) gflat.push_back(g.first);
+  std::vector<TcTile> tiles;
+  std::vector<TcEntry> entries;
+  build_tiles(H.n, kMrRows, pieces, [](const TcPiece& q) { return double(q.kp) * hh::fmt_bytes(q.fmt); }, tiles,
+              entries);
+  out.d_pieces = upload(pieces);
+  out.d_groups = upload(gflat);
+  out.d_tiles = upload(tiles);
+  out.d_entries = upload(entries);
+  out.n_pieces = (int)pieces.size();
+  out.n_groups = (int)gflat.size();
+  out.n_tiles = (int)tiles.size();
+  // dense blocks
+  std::vector<TcPiece> dp;
+  for (size_t q = 0; q < H.dense.size(); ++q) {
+    const hh::DenseBlock& D = H.dense[q];
+    TcPiece p;
+    std::memset(&p, 0, sizeof(p));
+    p.f2 = reinterpret_cast<const uint8_t*>(h->d_dense_pad + doff[q]);
+    p.ld2 = (D.m + 1) / 2 * 2;
+    p.k = (int32_t)(dir == 0 ? D.n : D.m);
+    p.kp = p.k;
+    p.rows2 = (int32_t)(dir == 0 ? D.m : D.n);
+    p.in_off = (int32_t)(dir == 0 ? D.col_off : D.row_off);
+    p.out_off = (int32_t)(dir == 0 ? D.row_off : D.col_off);
+    p.fmt = hh::F64;
+    p.e = dexp[q];
+    p.pad = dir;
+    dp.push_back(p);
+  }
+  std::vector<TcTile> dt;
+  std::vector<TcEntry> de;
+  build_tiles(H.n, kMrDenseRows, dp, [](const TcPiece& q) { return double(q.k) * 8; }, dt, de);
+  out.d_dpieces = upload(dp);
+  out.d_dtiles = upload(dt);
+  out.d_dentries = upload(de);
+  out.n_dtiles = (int)dt.size();
+}
+
 void upload_matrix(hh_matrix* h, int device) {
   const hh::HostMatrix& H = h->H;
   ck(cudaSetDevice(device), "cudaSetDevice");
@@ -433,12 +614,15 @@ void upload_matrix(hh_matrix* h, int device) {
   std::vector<int64_t> doff;
   std::vector<int32_t> dexp;
   upload_dense(h, doff, dexp);
-  std::vector<char> all(H.lr.size(), 1), rest(H.lr.size(), 1);
-  for (size_t b = 0; b < H.lr.size(); ++b) rest[b] = !tc_eligible(H.lr[b]);
+  // with many right-hand sides the streaming passes keep only the fp64
+  // low-rank blocks; the tensor cores and mr.cu take the rest
+  std::vector<char> all(H.lr.size(), 1), rest(H.lr.size(), 0);
+  for (size_t b = 0; b < H.lr.size(); ++b) rest[b] = H.lr[b].fmt == hh::F64;
   for (int dir = 0; dir < 2; ++dir) {
-    build_stream_set(h, dir, toff, doff, dexp, all, h->ss[dir]);
-    build_stream_set(h, dir, toff, doff, dexp, rest, h->ss_rest[dir]);
+    build_stream_set(h, dir, toff, doff, dexp, all, true, h->ss[dir]);
+    build_stream_set(h, dir, toff, doff, dexp, rest, false, h->ss_rest[dir]);
     build_tc_set(h, dir, h->tc[dir]);
+    build_mr_set(h, dir, doff, dexp, h->mr[dir]);
   }
   ck(cudaMalloc(&h->d_status, 256), "cudaMalloc");
   ck(cudaMemset(h->d_status, 0, 256), "cudaMemset");
@@ -523,6 +707,9 @@ struct TcWs {
   int* cnt;
   double* acc;
   int64_t nblk;
+  float* xh;   // fp32 input images [npad][128] (mr.cu)
+  float* xl;
+  float* t32;  // T of the CUDA-core pieces
 };
 
 size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
@@ -541,20 +728,30 @@ size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
   float* part = (float*)take(sizeof(float) * std::max<int64_t>(64, pf));
   int* cnt = (int*)take(sizeof(int) * std::max(64, nc));
   double* acc = (double*)take(sizeof(double) * hh::dev::kTcMaxRhs * h->npad);
-  if (v) *v = {ximg, timg, part, cnt, acc, nblk};
+  float* xh = (float*)take(sizeof(float) * 128 * h->npad);
+  float* xl = (float*)take(sizeof(float) * 128 * h->npad);
+  const int64_t tf = std::max(h->mr[0].t_floats, h->mr[1].t_floats);
+  float* t32 = (float*)take(sizeof(float) * std::max<int64_t>(64, tf));
+  if (v) *v = {ximg, timg, part, cnt, acc, nblk, xh, xl, t32};
   return off;
 }
 
-// Tensor-core product for nrhs <= 128 right-hand sides: prep of the input
-// image, the streaming passes for the blocks the tensor cores leave (fp64
-// blocks, dense blocks, unaligned clusters) in chunks of up to 4 right-hand
-// sides, the two tensor-core phases, and the output permutation.
+// Product for nrhs <= 128 right-hand sides in one pass over the blocks:
+// input images, the streaming passes over the fp64 low-rank blocks (chunks of
+// up to 4 right-hand sides), the CUDA-core and tensor-core phases 1, the
+// CUDA-core phase 2, the dense blocks, the tensor-core phase 2, and the output
+// permutation.  Events (when given): [0] before the input images, [1] before
+// the phases 1, [2] before the phases 2 and dense blocks, [3] before the
+// output permutation, [4] after it.
 cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr, int64_t ld_in, int64_t ld_out,
                    const WsView& w, const TcWs& t, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   if (ev) cudaEventRecord(ev[0], st);
   const TcSet& ts = h->tc[dir];
+  const MrSet& ms = h->mr[dir];
   cudaError_t e = hh::dev::launch_tc_prep(in, ld_in, nr, h->d_perm, h->H.n, t.nblk, t.ximg, t.acc, h->npad, t.cnt,
                                           ts.n_cnt, st);
+  if (e == cudaSuccess)
+    e = hh::dev::launch_mr_prep(in, ld_in, nr, h->d_perm, h->H.n, h->npad, t.xh, t.xl, t.t32, ms.t_floats, st);
   const StreamSet& rest = h->ss_rest[dir];
   if (rest.n_items[0] + rest.n_items[1] > 0)
     for (int rb = 0; rb < nr && e == cudaSuccess;) {
@@ -581,9 +778,34 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   a.acc = t.acc;
   a.npad = h->npad;
   a.status = h->d_status;
+  hh::dev::MrArgs m;
+  std::memset(&m, 0, sizeof(m));
+  m.pieces = ms.d_pieces;
+  m.groups = ms.d_groups;
+  m.tiles = ms.d_tiles;
+  m.entries = ms.d_entries;
+  m.n_groups = ms.n_groups;
+  m.n_tiles = ms.n_tiles;
+  m.nr = nr;
+  m.rp = nr <= 32 ? 32 : (nr <= 64 ? 64 : 128);
+  m.xh = t.xh;
+  m.xl = t.xl;
+  m.t32 = t.t32;
+  m.acc = t.acc;
+  m.npad = h->npad;
+  m.status = h->d_status;
+  hh::dev::MrArgs md = m;
+  md.pieces = ms.d_dpieces;
+  md.tiles = ms.d_dtiles;
+  md.entries = ms.d_dentries;
+  md.n_groups = 0;
+  md.n_tiles = ms.n_dtiles;
   if (ev) cudaEventRecord(ev[1], st);
+  if (e == cudaSuccess) e = hh::dev::launch_mr(1, m, st);
   if (e == cudaSuccess) e = hh::dev::launch_tc(1, a, st);
   if (ev) cudaEventRecord(ev[2], st);
+  if (e == cudaSuccess) e = hh::dev::launch_mr(2, m, st);
+  if (e == cudaSuccess) e = hh::dev::launch_mr(3, md, st);
   if (e == cudaSuccess) e = hh::dev::launch_tc(2, a, st);
   if (ev) cudaEventRecord(ev[3], st);
   if (e == cudaSuccess) e = hh::dev::launch_finish(t.acc, nr, h->d_perm, h->H.n, h->npad, out, ld_out, st);
@@ -611,7 +833,7 @@ int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, 
   WsView w;
   ws_layout(h, &w, (char*)ws);
   const int tmin = tc_min_nrhs();
-  const bool use_tc = allow_tc && tmin > 0 && nrhs >= tmin && h->tc[dir].n_pieces > 0;
+  const bool use_tc = allow_tc && tmin > 0 && nrhs >= tmin;
   TcWs t{};
   if (use_tc) {
     const size_t tneed = tc_ws_layout(h, nullptr, nullptr);
@@ -843,7 +1065,7 @@ int hh_matvec_timed(hh_handle h, int transpose, const double* in, double* out, i
   if (!h || !ms) return fail(HH_EINVAL, "null argument");
   if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data");
   const int dir = transpose ? 1 : 0;
-  const bool tc = tc_min_nrhs() > 0 && nrhs >= tc_min_nrhs() && nrhs <= hh::dev::kTcMaxRhs && h->tc[dir].n_pieces > 0;
+  const bool tc = tc_min_nrhs() > 0 && nrhs >= tc_min_nrhs() && nrhs <= hh::dev::kTcMaxRhs;
   if (!tc && (nrhs < 1 || nrhs > hh::dev::kMaxNR || nrhs == 3))
     return fail(HH_EINVAL, "nrhs must be 1, 2 or 4, or between the tensor-core threshold and 128");
   int cur = -1;

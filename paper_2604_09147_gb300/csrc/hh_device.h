@@ -130,5 +130,34 @@ cudaError_t launch_tc_prep(const double* x, int64_t ld, int nr, const int32_t* p
 cudaError_t launch_tc(int phase, const TcArgs& a, cudaStream_t st);
 size_t tc_smem_bytes(int phase);
 
+// ---- CUDA-core products for many right-hand sides (mr.cu) ----
+// Work lists in the tensor-core structures: phase-1 groups of at most
+// kMrRanks ranks (pieces with kp = ranks rounded up to 4, T at toff floats,
+// [rank][128]); phase-2 tiles of kMrRows rows; dense tiles of 64 rows whose
+// pieces are dense blocks (f2 = the fp64 block, ld2, k = the contracted
+// dimension, in_off its cluster offset, e = the power of two that undoes the
+// stored scale, pad = 1 for the transposed block).
+struct MrArgs {
+  const TcPiece* pieces;
+  const TcGroup* groups;
+  const TcTile* tiles;
+  const TcEntry* entries;
+  int32_t n_groups, n_tiles;
+  int32_t nr, rp;       // right-hand sides (<= 128); nr rounded up to 32, 64 or 128
+  const float* xh;      // input, tree order, fp32 leading halves [npos][128]
+  const float* xl;      // trailing halves
+  float* t32;           // T of the pieces
+  double* acc;          // output accumulator [nr][npad], tree order
+  int64_t npad;
+  int* status;
+};
+constexpr int kMrRanks = 64;
+constexpr int kMrRows = 128;
+constexpr int kMrDenseRows = 64;
+cudaError_t launch_mr_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t npos,
+                           float* xh, float* xl, float* t32, int64_t t_floats, cudaStream_t st);
+// kind 1: phase 1, 2: phase 2, 3: dense blocks
+cudaError_t launch_mr(int kind, const MrArgs& a, cudaStream_t st);
+
 }  // namespace dev
 }  // namespace hh

@@ -1,0 +1,497 @@
+// CUDA-core products for many right-hand sides (32 to 128 per launch): the
+// blocks the tensor-core path leaves to the CUDA cores, computed with every
+// right-hand side in one pass over their bytes.
+//
+//   mr_phase1  T_b = 2^(e_u+e_v) V_b^T X_J for the 32-, 16- and 8-bit blocks
+//              outside the tensor-core path (fp32 blocks, and 16/8-bit blocks
+//              on clusters that do not start at multiples of 16): one CTA per
+//              (group of at most 64 ranks sharing the input cluster, range of
+//              at most 1,024 positions); a thread holds 4 ranks x RPT
+//              right-hand sides.  Factors are upcast to fp32, the input is
+//              fp32 (relative 2^-24), products and sums are fp32 with round
+//              to nearest; split ranges add into T with atomics.
+//   mr_phase2  Y_I += U_b T_b for the same blocks: one CTA per 128-row output
+//              tile over every such block covering it; a thread holds 8 rows
+//              x RPT right-hand sides.
+//   mr_dense   Y_I += H_IJ X_J (or H_JI^T) for the fp64 dense blocks: one CTA
+//              per 64-row output tile; every product is formed from fp32
+//              leading and trailing halves of the fp64 entry and input and
+//              accumulated as an unevaluated fp32 pair (about 2^-44 relative),
+//              so the dense blocks keep the fp64 path's accuracy.
+// The tiles of phase 2 and of the dense kernel add into the fp64 output
+// accumulator with plain read-modify-writes: within one launch every output
+// row belongs to one CTA, and launches are ordered on the stream.  Operands
+// are staged through shared memory with register double buffering (the loads
+// of stage i + 1 are in flight while stage i is computed), which needs no
+// alignment of the clusters.
+#include "hh_device.h"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+namespace hh {
+namespace dev {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kK1 = 32;       // positions per phase-1 stage
+constexpr int kVStride = 36;  // floats per rank row of the phase-1 V stage (32 + 4)
+constexpr int kK2 = 16;       // ranks (dense: K columns) per phase-2 stage
+constexpr int kDenseRows = 64;
+
+constexpr int kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3, kE4M3 = 4;
+
+__device__ __forceinline__ int fsize(int f) { return f == kF32 ? 4 : (f == kE4M3 ? 1 : 2); }
+
+__device__ __forceinline__ float load_elem(const uint8_t* base, int64_t i, int fmt) {
+  if (fmt == kF32) return __ldg(reinterpret_cast<const float*>(base) + i);
+  if (fmt == kE4M3) {
+    __half_raw h = __nv_cvt_fp8_to_halfraw(static_cast<__nv_fp8_storage_t>(__ldg(base + i)), __NV_E4M3);
+    return __half2float(__half(h));
+  }
+  const unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(base) + i);
+  if (fmt == kBF16) return __uint_as_float(static_cast<uint32_t>(b) << 16);
+  __half_raw h;
+  h.x = b;
+  return __half2float(__half(h));
+}
+
+// right-hand side of element e of thread column tc (RPT = 8: two float4 64
+// columns apart, so a quarter warp reads 128 consecutive bytes)
+template <int RPT>
+__device__ __forceinline__ int rhs_col(int tc, int e) {
+  if (RPT == 8) return (e >> 2) * 64 + 4 * tc + (e & 3);
+  return RPT * tc + e;
+}
+
+template <int RPT>
+__device__ __forceinline__ void load_x(const float* row, int tc, float* x) {
+  if (RPT == 8) {
+    const float4 a = *reinterpret_cast<const float4*>(row + 4 * tc);
+    const float4 b = *reinterpret_cast<const float4*>(row + 64 + 4 * tc);
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+  } else if (RPT == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(row + 4 * tc);
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+  } else {
+    const float2 a = *reinterpret_cast<const float2*>(row + 2 * tc);
+    x[0] = a.x; x[1] = a.y;
+  }
+}
+
+// ------------------------------------------------------------------ phase 1
+template <int RPT>
+__global__ void __launch_bounds__(kThreads) mr_phase1(MrArgs a) {
+  constexpr int RP = 16 * RPT;
+  extern __shared__ __align__(16) float sm1[];
+  float* sV = sm1;                               // [2][64][kVStride]
+  float* sX = sm1 + 2 * kMrRanks * kVStride;     // [2][kK1][RP]
+  __shared__ const uint8_t* colp[kMrRanks];
+  __shared__ int rowpiece[kMrRanks];
+  const TcGroup g = a.groups[blockIdx.x];
+  const int tid = threadIdx.x;
+  if (tid < kMrRanks) {
+    colp[tid] = nullptr;
+    rowpiece[tid] = -1;
+  }
+  __syncthreads();
+  if (tid < g.count) {
+    const TcPiece& q = a.pieces[g.first + tid];
+    const int sz = fsize(q.fmt);
+    for (int j = 0; j < q.kp; ++j) {
+      rowpiece[q.col + j] = g.first + tid;
+      colp[q.col + j] = j < q.k ? q.f1 + static_cast<int64_t>(j) * q.ld1 * sz : nullptr;
+    }
+  }
+  __syncthreads();
+  const int fmt = g.fmt, nst = (g.p1 - g.p0 + kK1 - 1) / kK1;
+  // loader roles: V rank vj, positions 8 vq .. 8 vq + 7 of the stage; X units
+  const int vj = tid >> 2, vq = tid & 3;
+  const uint8_t* vcol = colp[vj];
+  constexpr int XU = kK1 * RP / 4 / kThreads;  // float4 units of X per thread
+  float vr[8];
+  float4 xr[XU];
+  auto load = [&](int i) {
+    const int P = g.p0 + kK1 * i;
+    const int pos = P + 8 * vq;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) vr[t] = (vcol && pos + t < g.p1) ? load_elem(vcol, pos + t, fmt) : 0.f;
+#pragma unroll
+    for (int h = 0; h < XU; ++h) {
+      const int u = tid + h * kThreads, p = u / (RP / 4), c4 = u - p * (RP / 4);
+      xr[h] = *reinterpret_cast<const float4*>(a.xh + (static_cast<int64_t>(g.in_off) + P + p) * 128 + 4 * c4);
+    }
+  };
+  auto store = [&](int buf) {
+    float* v = sV + (buf * kMrRanks + vj) * kVStride + 8 * vq;
+    *reinterpret_cast<float4*>(v) = make_float4(vr[0], vr[1], vr[2], vr[3]);
+    *reinterpret_cast<float4*>(v + 4) = make_float4(vr[4], vr[5], vr[6], vr[7]);
+#pragma unroll
+    for (int h = 0; h < XU; ++h) {
+      const int u = tid + h * kThreads, p = u / (RP / 4), c4 = u - p * (RP / 4);
+      *reinterpret_cast<float4*>(sX + (buf * kK1 + p) * RP + 4 * c4) = xr[h];
+    }
+  };
+  const int tr = tid >> 4, tc = tid & 15;
+  float acc[4][RPT];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int e = 0; e < RPT; ++e) acc[i][e] = 0.f;
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int i = 0; i < nst; ++i) {
+    const int buf = i & 1;
+    if (i + 1 < nst) load(i + 1);
+    const float* V = sV + (buf * kMrRanks + 4 * tr) * kVStride;
+    const float* X = sX + buf * kK1 * RP;
+#pragma unroll 8
+    for (int p = 0; p < kK1; ++p) {
+      float x[RPT];
+      load_x<RPT>(X + p * RP, tc, x);
+      const float v0 = V[p], v1 = V[kVStride + p], v2 = V[2 * kVStride + p], v3 = V[3 * kVStride + p];
+#pragma unroll
+      for (int e = 0; e < RPT; ++e) {
+        acc[0][e] = fmaf(v0, x[e], acc[0][e]);
+        acc[1][e] = fmaf(v1, x[e], acc[1][e]);
+        acc[2][e] = fmaf(v2, x[e], acc[2][e]);
+        acc[3][e] = fmaf(v3, x[e], acc[3][e]);
+      }
+    }
+    if (i + 1 < nst) store(buf ^ 1);
+    __syncthreads();
+  }
+  // T = 2^e D, rank-major [rank][128] per piece
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rank = 4 * tr + i;
+    const int pi = rowpiece[rank];
+    if (pi < 0) continue;
+    const TcPiece& q = a.pieces[pi];
+    const int rl = rank - q.col;
+    if (rl >= q.k) continue;
+    float* t = a.t32 + q.toff + static_cast<int64_t>(rl) * 128;
+#pragma unroll
+    for (int e = 0; e < RPT; ++e) {
+      const float v = ldexpf(acc[i][e], q.e);
+      if (g.nsplit > 1)
+        atomicAdd(t + rhs_col<RPT>(tc, e), v);
+      else
+        t[rhs_col<RPT>(tc, e)] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ phase 2
+// epilogue of a 128 x RP (or 64 x RP) tile: through shared memory so that the
+// fp64 read-modify-writes of the output run along rows
+template <int RPT, int ROWS, int RPTHR>
+__device__ __forceinline__ void add_tile(const MrArgs& a, const TcTile& tl, float* sAcc, const float (*acc)[RPT],
+                                         int tr, int tc) {
+  constexpr int RP = 16 * RPT;
+  constexpr int HALF = RP > 64 ? 64 : RP;
+  for (int h = 0; h < RP / HALF; ++h) {
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RPTHR; ++i)
+#pragma unroll
+      for (int e = 0; e < RPT; ++e) {
+        const int c = rhs_col<RPT>(tc, e) - h * HALF;
+        if (c >= 0 && c < HALF) sAcc[(RPTHR * tr + i) * (HALF + 1) + c] = acc[i][e];
+      }
+    __syncthreads();
+    for (int u = threadIdx.x; u < ROWS * HALF; u += kThreads) {
+      const int row = u % ROWS, c = u / ROWS, rr = h * HALF + c;
+      if (row < tl.rows && rr < a.nr)
+        a.acc[static_cast<int64_t>(rr) * a.npad + tl.row0 + row] += static_cast<double>(sAcc[row * (HALF + 1) + c]);
+    }
+  }
+}
+
+struct Cur {
+  int e, chunk;
+};
+
+template <int RPT>
+__global__ void __launch_bounds__(kThreads) mr_phase2(MrArgs a) {
+  constexpr int RP = 16 * RPT;
+  extern __shared__ __align__(16) float sm2[];
+  float* sU = sm2;                      // [2][kK2][128]
+  float* sT = sm2 + 2 * kK2 * kMrRows;  // [2][kK2][RP]
+  const TcTile tl = a.tiles[blockIdx.x];
+  const int tid = threadIdx.x;
+  int nst = 0;
+  for (int e = 0; e < tl.count; ++e) nst += (a.pieces[a.entries[tl.first + e].piece].kp + kK2 - 1) / kK2;
+  // loader roles: U rank uj, tile rows 8 um .. 8 um + 7; T units
+  const int uj = tid >> 4, um = tid & 15;
+  constexpr int TU = kK2 * RP / 4 / kThreads > 0 ? kK2 * RP / 4 / kThreads : 1;
+  float ur[8];
+  float4 trg[TU];
+  Cur lc{0, 0};
+  auto load = [&]() {
+    const TcEntry en = a.entries[tl.first + lc.e];
+    const TcPiece& q = a.pieces[en.piece];
+    const int j = kK2 * lc.chunk + uj;
+    const bool jin = j < q.k;
+    const int sz = fsize(q.fmt);
+    const uint8_t* col = q.f2 + static_cast<int64_t>(j) * q.ld2 * sz;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int m = 8 * um + t;
+      ur[t] = (jin && m >= en.dst && m < en.dst + en.nrows) ? load_elem(col, en.src + (m - en.dst), q.fmt) : 0.f;
+    }
+#pragma unroll
+    for (int h = 0; h < TU; ++h) {
+      const int u = tid + h * kThreads;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (u < kK2 * RP / 4) {
+        const int r = u / (RP / 4), c4 = u - r * (RP / 4), jj = kK2 * lc.chunk + r;
+        if (jj < q.k) v = *reinterpret_cast<const float4*>(a.t32 + q.toff + static_cast<int64_t>(jj) * 128 + 4 * c4);
+      }
+      trg[h] = v;
+    }
+    if (++lc.chunk == (q.kp + kK2 - 1) / kK2) {
+      lc.chunk = 0;
+      ++lc.e;
+    }
+  };
+  auto store = [&](int buf) {
+    float* u = sU + (buf * kK2 + uj) * kMrRows + 8 * um;
+    *reinterpret_cast<float4*>(u) = make_float4(ur[0], ur[1], ur[2], ur[3]);
+    *reinterpret_cast<float4*>(u + 4) = make_float4(ur[4], ur[5], ur[6], ur[7]);
+#pragma unroll
+    for (int h = 0; h < TU; ++h) {
+      const int u2 = tid + h * kThreads;
+      if (u2 < kK2 * RP / 4) {
+        const int r = u2 / (RP / 4), c4 = u2 - r * (RP / 4);
+        *reinterpret_cast<float4*>(sT + (buf * kK2 + r) * RP + 4 * c4) = trg[h];
+      }
+    }
+  };
+  const int tr = tid >> 4, tc = tid & 15;
+  float acc[8][RPT];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int e = 0; e < RPT; ++e) acc[i][e] = 0.f;
+  if (nst > 0) {
+    load();
+    store(0);
+  }
+  __syncthreads();
+  for (int i = 0; i < nst; ++i) {
+    const int buf = i & 1;
+    if (i + 1 < nst) load();
+    const float* U = sU + buf * kK2 * kMrRows + 8 * tr;
+    const float* T = sT + buf * kK2 * RP;
+#pragma unroll 4
+    for (int j = 0; j < kK2; ++j) {
+      const float4 u0 = *reinterpret_cast<const float4*>(U + j * kMrRows);
+      const float4 u1 = *reinterpret_cast<const float4*>(U + j * kMrRows + 4);
+      float x[RPT];
+      load_x<RPT>(T + j * RP, tc, x);
+      const float uu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int e = 0; e < RPT; ++e) acc[r][e] = fmaf(uu[r], x[e], acc[r][e]);
+    }
+    if (i + 1 < nst) store(buf ^ 1);
+    __syncthreads();
+  }
+  add_tile<RPT, kMrRows, 8>(a, tl, sm2, acc, tr, tc);
+}
+
+// ------------------------------------------------------------------ dense blocks
+__device__ __forceinline__ void split_d(double d, float& hi, float& lo) {
+  hi = __double2float_rn(d);
+  lo = __double2float_rn(d - static_cast<double>(hi));
+}
+
+// S + C += (ah + al)(bh + bl): the leading product exactly (fma error term),
+// the cross terms in fp32, the sum kept as an unevaluated pair (two-sum)
+__device__ __forceinline__ void dd_fma(float& S, float& C, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  const float pe = fmaf(ah, bh, -p);
+  const float cr = fmaf(ah, bl, fmaf(al, bh, pe));
+  const float t = S + p;
+  const float bp = t - S;
+  const float err = (S - (t - bp)) + (p - bp);
+  S = t;
+  C += err + cr;
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(kThreads) mr_dense(MrArgs a) {
+  constexpr int RP = 16 * RPT;
+  extern __shared__ __align__(16) float sm3[];
+  float* sDh = sm3;                              // [2][kK2][64]
+  float* sDl = sDh + 2 * kK2 * kDenseRows;
+  float* sXh = sDl + 2 * kK2 * kDenseRows;       // [2][kK2][RP]
+  float* sXl = sXh + 2 * kK2 * RP;
+  const TcTile tl = a.tiles[blockIdx.x];
+  const int tid = threadIdx.x;
+  int nst = 0;
+  for (int e = 0; e < tl.count; ++e) nst += (a.pieces[a.entries[tl.first + e].piece].k + kK2 - 1) / kK2;
+  // loader roles: D entries (k = tid >> 4, rows 4 (tid & 15) .. +3); X units
+  const int dk = tid >> 4, dm = tid & 15;
+  constexpr int XU = kK2 * RP / 4 / kThreads > 0 ? kK2 * RP / 4 / kThreads : 1;
+  float dh[4], dl[4];
+  float4 xh[XU], xl[XU];
+  Cur lc{0, 0};
+  auto load = [&]() {
+    const TcEntry en = a.entries[tl.first + lc.e];
+    const TcPiece& q = a.pieces[en.piece];
+    const double* D = reinterpret_cast<const double*>(q.f2);
+    const int k = kK2 * lc.chunk + dk;
+    const bool trans = q.pad != 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int m = 4 * dm + t;
+      double d = 0.0;
+      if (k < q.k && m >= en.dst && m < en.dst + en.nrows) {
+        const int64_t row = en.src + (m - en.dst);
+        d = ldexp(__ldg(D + (trans ? row * q.ld2 + k : static_cast<int64_t>(k) * q.ld2 + row)), q.e);
+      }
+      split_d(d, dh[t], dl[t]);
+    }
+#pragma unroll
+    for (int h = 0; h < XU; ++h) {
+      const int u = tid + h * kThreads;
+      float4 vh = make_float4(0.f, 0.f, 0.f, 0.f), vl = vh;
+      if (u < kK2 * RP / 4) {
+        const int r = u / (RP / 4), c4 = u - r * (RP / 4), kk = kK2 * lc.chunk + r;
+        if (kk < q.k) {
+          const int64_t off = (static_cast<int64_t>(q.in_off) + kk) * 128 + 4 * c4;
+          vh = *reinterpret_cast<const float4*>(a.xh + off);
+          vl = *reinterpret_cast<const float4*>(a.xl + off);
+        }
+      }
+      xh[h] = vh;
+      xl[h] = vl;
+    }
+    if (++lc.chunk == (q.k + kK2 - 1) / kK2) {
+      lc.chunk = 0;
+      ++lc.e;
+    }
+  };
+  auto store = [&](int buf) {
+    *reinterpret_cast<float4*>(sDh + (buf * kK2 + dk) * kDenseRows + 4 * dm) = make_float4(dh[0], dh[1], dh[2], dh[3]);
+    *reinterpret_cast<float4*>(sDl + (buf * kK2 + dk) * kDenseRows + 4 * dm) = make_float4(dl[0], dl[1], dl[2], dl[3]);
+#pragma unroll
+    for (int h = 0; h < XU; ++h) {
+      const int u = tid + h * kThreads;
+      if (u < kK2 * RP / 4) {
+        const int r = u / (RP / 4), c4 = u - r * (RP / 4);
+        *reinterpret_cast<float4*>(sXh + (buf * kK2 + r) * RP + 4 * c4) = xh[h];
+        *reinterpret_cast<float4*>(sXl + (buf * kK2 + r) * RP + 4 * c4) = xl[h];
+      }
+    }
+  };
+  const int tr = tid >> 4, tc = tid & 15;
+  float S[4][RPT], C[4][RPT];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int e = 0; e < RPT; ++e) S[i][e] = C[i][e] = 0.f;
+  if (nst > 0) {
+    load();
+    store(0);
+  }
+  __syncthreads();
+  for (int i = 0; i < nst; ++i) {
+    const int buf = i & 1;
+    if (i + 1 < nst) load();
+#pragma unroll 2
+    for (int k = 0; k < kK2; ++k) {
+      const float4 h4 = *reinterpret_cast<const float4*>(sDh + (buf * kK2 + k) * kDenseRows + 4 * tr);
+      const float4 l4 = *reinterpret_cast<const float4*>(sDl + (buf * kK2 + k) * kDenseRows + 4 * tr);
+      float bh[RPT], bl[RPT];
+      load_x<RPT>(sXh + (buf * kK2 + k) * RP, tc, bh);
+      load_x<RPT>(sXl + (buf * kK2 + k) * RP, tc, bl);
+      const float ah[4] = {h4.x, h4.y, h4.z, h4.w}, al[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int e = 0; e < RPT; ++e) dd_fma(S[r][e], C[r][e], ah[r], al[r], bh[e], bl[e]);
+    }
+    if (i + 1 < nst) store(buf ^ 1);
+    __syncthreads();
+  }
+  float acc[4][RPT];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int e = 0; e < RPT; ++e) acc[r][e] = S[r][e] + C[r][e];
+  // the sum of the pair is rounded to fp32 here only for the transpose through
+  // shared memory: add the trailing part separately to keep it
+  add_tile<RPT, kDenseRows, 4>(a, tl, sm3, acc, tr, tc);
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int e = 0; e < RPT; ++e) acc[r][e] = C[r][e] - (acc[r][e] - S[r][e]);
+  add_tile<RPT, kDenseRows, 4>(a, tl, sm3, acc, tr, tc);
+}
+
+// X (caller's order, column-major, ld) -> tree order, fp32 leading and
+// trailing halves [npos][128]; columns r >= nr and positions >= n are zero.
+// Also clears the T arena of the CUDA-core pieces (split ranges add into it).
+__global__ void mr_prep_kernel(const double* __restrict__ x, int64_t ld, int nr, const int32_t* __restrict__ perm,
+                               int64_t n, int64_t npos, float* __restrict__ xh, float* __restrict__ xl,
+                               float* __restrict__ t32, int64_t t_floats) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  for (int64_t q = t0; q < npos * 128; q += stride) {
+    const int64_t p = q >> 7;
+    const int r = static_cast<int>(q & 127);
+    const double v = (r < nr && p < n) ? x[static_cast<int64_t>(perm[p]) + r * ld] : 0.0;
+    const float h = __double2float_rn(v);
+    xh[q] = h;
+    xl[q] = __double2float_rn(v - static_cast<double>(h));
+  }
+  for (int64_t q = t0; q < t_floats; q += stride) t32[q] = 0.f;
+}
+
+template <int RPT>
+cudaError_t launch_rpt(int kind, const MrArgs& a, cudaStream_t st) {
+  constexpr int RP = 16 * RPT;
+  if (kind == 1) {
+    const size_t smem = sizeof(float) * (2 * kMrRanks * kVStride + 2 * kK1 * RP);
+    cudaError_t e = cudaFuncSetAttribute(mr_phase1<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) mr_phase1<RPT><<<a.n_groups, kThreads, smem, st>>>(a);
+  } else if (kind == 2) {
+    const size_t smem = sizeof(float) * std::max(2 * kK2 * (kMrRows + RP), kMrRows * (std::min(RP, 64) + 1));
+    cudaError_t e = cudaFuncSetAttribute(mr_phase2<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) mr_phase2<RPT><<<a.n_tiles, kThreads, smem, st>>>(a);
+  } else {
+    const size_t smem = sizeof(float) * std::max(4 * kK2 * (kDenseRows + RP), kDenseRows * (std::min(RP, 64) + 1));
+    cudaError_t e = cudaFuncSetAttribute(mr_dense<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) mr_dense<RPT><<<a.n_tiles, kThreads, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_mr_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t npos,
+                           float* xh, float* xl, float* t32, int64_t t_floats, cudaStream_t st) {
+  int64_t blocks = (npos * 128 + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  if (blocks < 1) blocks = 1;
+  mr_prep_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(x, ld, nr, perm, n, npos, xh, xl, t32, t_floats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mr(int kind, const MrArgs& a, cudaStream_t st) {
+  if ((kind == 1 && a.n_groups <= 0) || (kind != 1 && a.n_tiles <= 0)) return cudaSuccess;
+  if (a.rp <= 32) return launch_rpt<2>(kind, a, st);
+  if (a.rp <= 64) return launch_rpt<4>(kind, a, st);
+  return launch_rpt<8>(kind, a, st);
+}
+
+}  // namespace dev
+}  // namespace hh

@@ -181,3 +181,25 @@ def test_tc_autograd_multi_rhs(P, tmp_path_factory):
     ab_y, ab_g = abs_product(O, x, False), abs_product(O, ybar, True)
     assert np.linalg.norm(y.detach().cpu().numpy() - ref_y) <= TOL * np.linalg.norm(ref_y) + 2.0 ** -12 * np.linalg.norm(ab_y)
     assert np.linalg.norm(xt.grad.cpu().numpy() - ref_g) <= TOL * np.linalg.norm(ref_g) + 2.0 ** -12 * np.linalg.norm(ab_g)
+
+
+@pytest.mark.parametrize("nrhs", [32, 40, 128])
+def test_many_rhs_fp64_matrix(P, tmp_path, nrhs):
+    """Uniform fp64 storage with many right-hand sides: the fp64 low-rank blocks
+    take the streaming passes in chunks of 4 columns and the dense blocks the
+    pair-of-fp32 kernel; the fp64 path's 1e-12 holds for every column."""
+    from oracle import build as OB
+    c = W.CONFIGS["plain_small"]
+    pts = W.config_points("plain_small")
+    O = OB.build(pts, c["kernel"], c["kernel_param"], c["leaf"], 1.0, c["ell"], c["tol"], W.F64)
+    path = str(tmp_path / "p.hhm")
+    hhfile.write(O, path)
+    H = P.HMatrix.load(path, 0)
+    for tr in (False, True):
+        x = W.rhs(len(pts), nrhs, "uniform", 7900 + nrhs + tr)
+        xg = torch.from_numpy(np.ascontiguousarray(x.T)).cuda().t()
+        y = H.matvec(xg, transpose=tr).cpu().numpy()
+        H.sync_status()
+        ref = M.matvec_T(O, x) if tr else M.matvec(O, x)
+        cols = np.linalg.norm(y - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        assert cols.max() <= 1e-12, cols.max()

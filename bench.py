@@ -2,6 +2,7 @@
 """Benchmark of the H_h matrix-vector product on GB300.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+                    [--workload adaptive_65k|adaptive_16k|multirhs_65k|multirhs_262k] [--nrhs R]
 
 Workload (default): N = 65,536 points uniform in [0,1]^3, kernel 1/r with
 K(x,x) = 0, leaf 128, eta 1, switch level 4, tol 1e-6, adaptive storage from
@@ -10,6 +11,12 @@ uniform-fp64 H_h matvec of the same compression.  A step is one complete
 product y = A_h x (permute in, phase 1, phase 2 with the dense diagonal,
 permute out).  The factors (about 1.9 GB adaptive, 3.7 GB fp64) exceed the
 L2 cache, so every step streams them from HBM.
+
+Many right-hand sides (--workload multirhs_*): N points U[0,1]^3, Gaussian
+kernel exp(-r^2/0.01), leaf 128, eta 1, switch level 5, tol 1e-6, adaptive
+storage from {fp64, fp32, bf16, e4m3}, R = 128 right-hand sides N(0,1) (the
+262,144-point workload, or the same family at 65,536 points); a step is one
+product Y = A_h X of all R columns; the metric is right-hand sides per second.
 
 Multi-GPU (torchrun): every rank runs an independent replica (weak scaling);
 the max time over ranks is reported.  --impl reference times the CPU oracle
@@ -44,6 +51,15 @@ WORKLOADS = {
                     "tol 1e-6, adaptive {fp64,fp32,fp16,bf16} vs uniform fp64, 1 RHS U(-1,1)",
 }
 WORKLOAD_N = {"adaptive_65k": 65536, "adaptive_16k": 16384}
+MANY_N = {"multirhs_65k": 65536, "multirhs_262k": 262144}
+for _k, _n in MANY_N.items():
+    WORKLOADS[_k] = (f"N={_n:,} points U[0,1]^3, Gaussian exp(-r^2/0.01), leaf 128, eta 1, switch level 5, "
+                     "tol 1e-6, adaptive {fp64,fp32,bf16,e4m3}, R right-hand sides N(0,1) per product")
+# fp32 FMA issue rate of the CUDA cores: 152 SMs x 128 lanes x 2 flops at the
+# 2,070 MHz maximum SM clock; a product of fp32 pairs (the dense blocks) costs
+# 9 fp32 instructions (3 FMA, 6 add) per multiply-add
+FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+DD_TFLOPS = FP32_TFLOPS * 2 / (2 * 9)
 
 
 def dist_env():
@@ -60,6 +76,15 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops_sustained"]), "measured (sustained)"
+    except Exception:
+        return 1700.0, "fallback (sustained)"
 
 
 class ClockSampler:
@@ -198,24 +223,39 @@ def run_reference(args):
     if rank != 0:
         return 0
     import paper_2604_09147_gb300 as P
-    c = W.CONFIGS["adaptive_65k"]
-    pts = W.config_points("adaptive_65k", WORKLOAD_N[args.workload])
-    H64 = P.HMatrix.build_cached(pts, CACHE, c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"],
-                                 c["tol"], W.F64, device=-1)
-    Ham = H64.reencode(c["fmts"], -1)
-    path = os.path.join(CACHE, "bench_adaptive_ref.hhm")
-    Ham.save(path)
-    x = W.config_rhs("adaptive_65k", n=len(pts))[:, 0]
     per_step = max(0.5, 120.0 / max(1, args.steps + args.warmup))
-    rate, desc, el = oracle_sample(path, x, per_step * args.steps)
-    out = {"impl": "reference", "metric": "H_h matvecs/s (adaptive precision)", "value": rate,
-           "unit": "matvec/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+    if args.workload in MANY_N:
+        c = W.CONFIGS["multirhs_262k"]
+        pts = W.config_points("multirhs_262k", MANY_N[args.workload])
+        H = P.HMatrix.build_cached(pts, CACHE, c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"],
+                                   c["tol"], c["fmts"], device=-1)
+        path = os.path.join(CACHE, f"bench_{args.workload}_ref.hhm")
+        H.save(path)
+        x = W.config_rhs("multirhs_262k", nrhs=args.nrhs, n=len(pts))
+        rate, desc, el = oracle_sample(path, x, per_step * args.steps)
+        rate, unit = rate * args.nrhs, "rhs/s"
+        metric = "H_h matvec right-hand sides/s (adaptive precision, many right-hand sides)"
+        desc += f", {args.nrhs} columns per pass"
+    else:
+        c = W.CONFIGS["adaptive_65k"]
+        pts = W.config_points("adaptive_65k", WORKLOAD_N[args.workload])
+        H64 = P.HMatrix.build_cached(pts, CACHE, c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"],
+                                     c["tol"], W.F64, device=-1)
+        Ham = H64.reencode(c["fmts"], -1)
+        path = os.path.join(CACHE, "bench_adaptive_ref.hhm")
+        Ham.save(path)
+        x = W.config_rhs("adaptive_65k", n=len(pts))[:, 0]
+        rate, desc, el = oracle_sample(path, x, per_step * args.steps)
+        unit = "matvec/s"
+        metric = "H_h matvecs/s (adaptive precision), HBM GB/s and fraction of peak, vs uniform fp64"
+    out = {"impl": "reference", "metric": metric, "value": rate,
+           "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1000.0 / rate, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOADS[args.workload]},
-           "cpu_baseline": {"value": rate, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle",
+           "cpu_baseline": {"value": rate, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
                             "sample": desc},
-           "e2e": {"value": rate, "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "e2e": {"value": rate, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -262,8 +302,8 @@ def run_ours(args):
     bytes_p2 = inf["u_bytes"] + inf["dense_bytes"]
     dom = 1 if phases[1] >= phases[2] else 2
     dom_bytes = bytes_p1 if dom == 1 else bytes_p2
-    dom_name = "pass_kernel<1,...> (phase 1: t_b = V_b^T x_J)" if dom == 1 else \
-        "pass_kernel<2,...> (phase 2: y_I += U_b t_b, dense diagonal)"
+    dom_name = "stream_kernel<1,...> (phase 1: t_b = V_b^T x_J)" if dom == 1 else \
+        "stream_kernel<2,...> (phase 2: y_I += U_b t_b, dense diagonal)"
     achieved = dom_bytes / (phases[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic_for(f"phase{dom}"), "kernel": dom_name, "peak_kind": f"of {peak_kind}",
@@ -298,8 +338,8 @@ def run_ours(args):
         "metric": "H_h matvecs/s (adaptive precision), HBM GB/s and fraction of peak, vs uniform fp64",
         "value": value, "unit": "matvec/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_amp, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "dtype_note": "fp32 accumulation for 32/16/8-bit factors, fp64 for fp64 factors, "
-                                      "the dense diagonal and the output scatter",
+        "dtype": "f32", "dtype_note": "fp32 accumulation for 32/16/8-bit factors; fp64 factors and the dense "
+                                      "diagonal as pairs of fp32 halves (about 2^-48); fp64 output scatter",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "n": n, "nrhs": 1, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (factor bytes %.2f GB adaptive / %.2f GB fp64 per step)"
@@ -323,6 +363,131 @@ def run_ours(args):
     return 0
 
 
+def build_many(P, torch, rank, ws, dev, workload):
+    c = W.CONFIGS["multirhs_262k"]
+    pts = W.config_points("multirhs_262k", MANY_N[workload])
+    if ws > 1 and rank != 0:
+        torch.distributed.barrier()
+    t0 = time.time()
+    H = P.HMatrix.build_cached(pts, CACHE, c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"], c["tol"],
+                               c["fmts"], device=dev)
+    if ws > 1 and rank == 0:
+        torch.distributed.barrier()
+    return c, pts, H, time.time() - t0
+
+
+def run_many(args):
+    """Many right-hand sides: Y = A_h X with R columns per product."""
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", init_method="env://")
+    dev = torch.cuda.current_device()
+    import paper_2604_09147_gb300 as P
+    from paper_2604_09147_gb300 import build as B
+    B.build()
+    c, pts, H, build_s = build_many(P, torch, rank, ws, dev, args.workload)
+    n, R = len(pts), args.nrhs
+    X0 = W.config_rhs("multirhs_262k", nrhs=R, n=n)            # (n, R) column-major
+    x = torch.from_numpy(np.ascontiguousarray(X0.T)).cuda().t()  # device, column-major
+    y = torch.empty((R, n), dtype=torch.float64, device="cuda").t()
+    inf = H.info()
+    for _ in range(args.warmup):
+        H.matvec(x, out=y)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t_ms = timed_loop(torch, H, x, y, args.steps, ws)
+    clk = clocks.stop()
+    t_ms = max_over_ranks(torch, t_ms, ws)
+    H.sync_status()
+    ms = t_ms / args.steps
+    value = ws * args.steps * R / (t_ms / 1000.0)
+
+    # per-launch device times of the sequence (CUDA events around every launch)
+    nst = max(3, min(args.steps, 20))
+    st = np.mean([H.matvec_stages(x, y) for _ in range(nst)], axis=0)
+    names = ["images", "fp64_streaming", "mr_phase1", "tc_phase1", "mr_phase2", "mr_dense", "tc_phase2", "finish"]
+    stages = {k: float(v) for k, v in zip(names, st)}
+    hbm, peak_kind = peaks()
+    bf16, bf16_kind = bf16_peak()
+    fmt_b = {"fp32": 4, "fp16": 2, "bf16": 2, "e4m3": 1}
+    per = {
+        "mr_phase1": ("alu", 2.0 * R * inf["mr_v_elems"], FP32_TFLOPS, "derived fp32 FMA peak"),
+        "mr_phase2": ("alu", 2.0 * R * inf["mr_u_elems"], FP32_TFLOPS, "derived fp32 FMA peak"),
+        "mr_dense": ("alu", 2.0 * R * inf["dense_elems"], DD_TFLOPS, "derived fp32-pair FMA peak"),
+        "tc_phase1": ("tensor", 2.0 * R * inf["tc_v_elems"], bf16, bf16_kind),
+        "tc_phase2": ("tensor", 2.0 * R * inf["tc_u_elems"], bf16, bf16_kind),
+    }
+    detail = {}
+    for k, (bound, flops, peak, kind) in per.items():
+        t = stages[k] * 1e-3
+        detail[k] = {"ms": stages[k], "bound": bound, "tflops": flops / t / 1e12 if t > 0 else None,
+                     "peak_tflops": peak, "frac": (flops / t / 1e12) / peak if t > 0 else None, "peak_kind": kind}
+    dom = max(per, key=lambda k: stages[k])
+    bound, flops, peak, kind = per[dom]
+    achieved = flops / (stages[dom] * 1e-3) / 1e12
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic_for(dom), "kernel": dom, "peak_kind": f"of {kind}",
+                "flops_per_launch": flops, "ms_per_launch": stages[dom], "stages": detail}
+
+    # the same columns through the streaming passes, 4 per product
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(3, args.steps))
+    e0.record()
+    for _ in range(reps):
+        for j in range(0, R, 4):
+            H.matvec(x[:, j:j + 4], out=y[:, j:j + 4])
+    e1.record()
+    torch.cuda.synchronize()
+    ms_stream = e0.elapsed_time(e1) / reps
+
+    # end to end from pinned host buffers
+    xh = torch.empty((R, n), dtype=torch.float64, pin_memory=True)
+    xh.copy_(torch.from_numpy(np.ascontiguousarray(X0.T)))
+    xnp = xh.numpy().T
+    e2e_steps = max(3, min(args.steps, 50))
+    H.matvec_host(xnp)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        H.matvec_host(xnp)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ws * e2e_steps * R / max_over_ranks(torch, e2e_s, ws), "unit": "rhs/s",
+           "h2d_bytes_per_step": 8 * n * R, "d2h_bytes_per_step": 8 * n * R}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        path = os.path.join(CACHE, f"bench_{args.workload}.hhm")
+        H.save(path)
+        rate, desc, _ = oracle_sample(path, X0, args.cpu_seconds)
+        cpu = {"value": rate * R, "unit": "rhs/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": desc + f", {R} columns per pass"}
+    launches = 2 + 6 + 1 + (3 * ((R + 3) // 4) if stages["fp64_streaming"] > 0.002 else 0)
+    out = {
+        "metric": "H_h matvec right-hand sides/s (adaptive precision, many right-hand sides)",
+        "value": value, "unit": "rhs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "dtype_note": "fp32 FMA for fp32 factors; tensor-core bf16 slices with fp32 accumulation "
+                                      "for 16/8-bit factors; fp32 pairs for the fp64 dense diagonal; fp64 output",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "n": n, "nrhs": R, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (%.2f GB of factors and dense blocks per step)"
+                         % (inf["bytes_per_matvec"] / 1e9)},
+        "streaming_4col": {"ms_per_step": ms_stream, "speedup": ms_stream / ms},
+        "blocks_per_fmt": inf["blocks_per_fmt"], "factor_bytes_per_fmt": inf["factor_bytes_per_fmt"],
+        "tc_factor_bytes": inf["tc_factor_bytes"], "bound_thm44": inf["bound_thm44"], "build_seconds": build_s,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches * args.steps, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -332,11 +497,16 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="adaptive_65k")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU oracle baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nrhs", type=int, default=128, help="right-hand sides per product (multirhs workloads)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if not 1 <= args.nrhs <= 128:
+        ap.error("--nrhs must be between 1 and 128")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in MANY_N:
+        return run_many(args)
     return run_ours(args)
 
 

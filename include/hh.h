@@ -96,6 +96,10 @@ typedef struct {
   double build_seconds;           /* wall time of hh_build (0 for hh_load)           */
   int64_t tc_blocks;              /* admissible blocks the tensor-core path takes    */
   int64_t tc_factor_bytes;        /* their factor bytes                              */
+  int64_t tc_u_elems, tc_v_elems; /* their U and V elements (sum m k, sum n k)        */
+  int64_t mr_u_elems, mr_v_elems; /* the same for the 32/16/8-bit blocks that the
+                                     many-right-hand-side path runs on CUDA cores  */
+  int64_t dense_elems;            /* entries of the dense blocks                     */
 } hh_info_t;
 
 /*
@@ -191,18 +195,23 @@ int hh_matvec_ws(hh_handle h, int transpose, const double* in, double* out, int 
 int hh_matvec_host(hh_handle h, int transpose, const double* x_host, double* y_host, int nrhs,
                    void* stream);
 
-/* hh_matvec_timed -- one product (transpose != 0: A_h^T) with CUDA events
- * recorded on `stream` between its stages; synchronises the stream and
- * writes the device time in ms of each stage to ms[4].
- *   nrhs 1, 2 or 4 (one launch sequence of the streaming passes):
- *     {prep, phase 1 (t_b = V_b^T x), phase 2 (y += U_b t_b and dense
- *     blocks), finish}.
- *   nrhs from the tensor-core threshold (32) to 128, on a matrix with blocks
- *     the tensor cores take: {input image + the streaming passes over the
- *     other blocks, tensor-core phase 1, tensor-core phase 2, finish}.
- * Other nrhs: HH_EINVAL.  For measurement; uses the handle's workspaces. */
+/* hh_matvec_timed -- one product (transpose != 0: A_h^T) through the
+ * streaming passes with CUDA events recorded on `stream` between its four
+ * launches; synchronises the stream and writes the device time in ms of each
+ * launch to ms[4] = {prep, phase 1 (t_b = V_b^T x), phase 2 (y += U_b t_b and
+ * dense blocks), finish}.  nrhs must be 1, 2 or 4 (one launch sequence).  For
+ * measurement; uses the handle's workspace. */
 int hh_matvec_timed(hh_handle h, int transpose, const double* in, double* out, int nrhs,
                     int64_t ld_in, int64_t ld_out, void* stream, float* ms);
+
+/* hh_matvec_stages -- one product of 1 <= nrhs <= 128 right-hand sides
+ * through the many-right-hand-side sequence (whatever nrhs), with CUDA events
+ * around each launch; synchronises and writes ms[8] = {input images,
+ * streaming passes over the fp64 low-rank blocks, CUDA-core phase 1,
+ * tensor-core phase 1, CUDA-core phase 2, dense blocks, tensor-core phase 2,
+ * output permutation}.  For measurement; uses the handle's workspaces. */
+int hh_matvec_stages(hh_handle h, int transpose, const double* in, double* out, int nrhs,
+                     int64_t ld_in, int64_t ld_out, void* stream, float* ms);
 
 /* hh_matvec_batched -- y_i = A_i x_i for `count` independent matrices (one
  * right-hand side each, ld = n_i) in one launch sequence over the

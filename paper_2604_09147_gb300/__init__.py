@@ -49,6 +49,8 @@ class _Info(ctypes.Structure):
         ("bound_thm42", ctypes.c_double), ("bound_thm44", ctypes.c_double),
         ("bound_rounding", ctypes.c_double), ("build_seconds", ctypes.c_double),
         ("tc_blocks", ctypes.c_int64), ("tc_factor_bytes", ctypes.c_int64),
+        ("tc_u_elems", ctypes.c_int64), ("tc_v_elems", ctypes.c_int64),
+        ("mr_u_elems", ctypes.c_int64), ("mr_v_elems", ctypes.c_int64), ("dense_elems", ctypes.c_int64),
     ]
 
 
@@ -71,6 +73,7 @@ def _load():
         "hh_matvec_ws": (I32, [P, I32, P, P, I32, I64, I64, P, c.c_size_t, P]),
         "hh_matvec_host": (I32, [P, I32, P, P, I32, P]),
         "hh_matvec_timed": (I32, [P, I32, P, P, I32, I64, I64, P, c.POINTER(c.c_float)]),
+        "hh_matvec_stages": (I32, [P, I32, P, P, I32, I64, I64, P, c.POINTER(c.c_float)]),
         "hh_matvec_batched": (I32, [c.POINTER(P), I32, c.POINTER(P), c.POINTER(P), P]),
         "hh_sync_status": (I32, [P, P]),
         "hh_free": (None, [P]),
@@ -264,6 +267,18 @@ class HMatrix:
         ldy = self.n if y.dim() == 1 else y.stride(1)
         _check(_L().hh_matvec_timed(self._h, 1 if transpose else 0, xv.data_ptr(), y.data_ptr(), nrhs, ldx, ldy,
                                     _stream_ptr(x.device), ms))
+        return [float(v) for v in ms]
+
+    def matvec_stages(self, x: torch.Tensor, y: torch.Tensor, transpose: bool = False) -> list:
+        """One product of up to 128 columns through the many-right-hand-side
+        sequence with per-launch CUDA-event times in ms (synchronises):
+        [input images, fp64 streaming passes, CUDA-core phase 1, tensor-core
+        phase 1, CUDA-core phase 2, dense blocks, tensor-core phase 2, finish]."""
+        xv, nrhs, ldx, vec = _as_colmajor(x, self.n)
+        ms = (ctypes.c_float * 8)()
+        ldy = self.n if y.dim() == 1 else y.stride(1)
+        _check(_L().hh_matvec_stages(self._h, 1 if transpose else 0, xv.data_ptr(), y.data_ptr(), nrhs, ldx, ldy,
+                                     _stream_ptr(x.device), ms))
         return [float(v) for v in ms]
 
     def sync_status(self) -> None:

@@ -740,12 +740,16 @@ size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
 // input images, the streaming passes over the fp64 low-rank blocks (chunks of
 // up to 4 right-hand sides), the CUDA-core and tensor-core phases 1, the
 // CUDA-core phase 2, the dense blocks, the tensor-core phase 2, and the output
-// permutation.  Events (when given): [0] before the input images, [1] before
-// the phases 1, [2] before the phases 2 and dense blocks, [3] before the
-// output permutation, [4] after it.
+// permutation.  With ev (9 events) every launch is bracketed: [0] images,
+// [1] streaming passes, [2] CUDA-core phase 1, [3] tensor-core phase 1,
+// [4] CUDA-core phase 2, [5] dense blocks, [6] tensor-core phase 2,
+// [7] output permutation, [8] end.
 cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr, int64_t ld_in, int64_t ld_out,
                    const WsView& w, const TcWs& t, cudaStream_t st, cudaEvent_t* ev = nullptr) {
-  if (ev) cudaEventRecord(ev[0], st);
+  auto mark = [&](int i) {
+    if (ev) cudaEventRecord(ev[i], st);
+  };
+  mark(0);
   const TcSet& ts = h->tc[dir];
   const MrSet& ms = h->mr[dir];
   cudaError_t e = hh::dev::launch_tc_prep(in, ld_in, nr, h->d_perm, h->H.n, t.nblk, t.ximg, t.acc, h->npad, t.cnt,
@@ -753,6 +757,7 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   if (e == cudaSuccess)
     e = hh::dev::launch_mr_prep(in, ld_in, nr, h->d_perm, h->H.n, h->npad, t.xh, t.xl, t.t32, ms.t_floats, st);
   const StreamSet& rest = h->ss_rest[dir];
+  mark(1);
   if (rest.n_items[0] + rest.n_items[1] > 0)
     for (int rb = 0; rb < nr && e == cudaSuccess;) {
       const int rem = nr - rb, c = rem >= 4 ? 4 : (rem >= 2 ? 2 : 1);
@@ -800,22 +805,32 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   md.entries = ms.d_dentries;
   md.n_groups = 0;
   md.n_tiles = ms.n_dtiles;
-  if (ev) cudaEventRecord(ev[1], st);
+  mark(2);
   if (e == cudaSuccess) e = hh::dev::launch_mr(1, m, st);
+  mark(3);
   if (e == cudaSuccess) e = hh::dev::launch_tc(1, a, st);
-  if (ev) cudaEventRecord(ev[2], st);
+  mark(4);
   if (e == cudaSuccess) e = hh::dev::launch_mr(2, m, st);
+  mark(5);
   if (e == cudaSuccess) e = hh::dev::launch_mr(3, md, st);
+  mark(6);
   if (e == cudaSuccess) e = hh::dev::launch_tc(2, a, st);
-  if (ev) cudaEventRecord(ev[3], st);
+  mark(7);
   if (e == cudaSuccess) e = hh::dev::launch_finish(t.acc, nr, h->d_perm, h->H.n, h->npad, out, ld_out, st);
-  if (ev) cudaEventRecord(ev[4], st);
+  mark(8);
   return e;
 }
 
+// path: kStreamOnly (every column through the streaming passes), kAuto (the
+// many-right-hand-side sequence from tc_min_nrhs() columns on), kMany (that
+// sequence for any nrhs).  ev: 5 events for the streaming sequence (one chunk
+// of up to 4 columns), 9 for the many-right-hand-side sequence (one chunk of
+// up to 128 columns).
+enum Path { kStreamOnly = 0, kAuto = 1, kMany = 2 };
+
 int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, int64_t ld_in,
                 int64_t ld_out, void* ws, size_t ws_bytes, cudaStream_t st, cudaEvent_t* ev = nullptr,
-                bool allow_tc = false) {
+                Path path = kStreamOnly) {
   if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data (built with device = -1)");
   if (!in || !out || nrhs < 1 || ld_in < h->H.n || ld_out < h->H.n)
     return fail(HH_EINVAL, "bad vector arguments (null pointer, nrhs < 1 or ld < n)");
@@ -833,7 +848,7 @@ int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, 
   WsView w;
   ws_layout(h, &w, (char*)ws);
   const int tmin = tc_min_nrhs();
-  const bool use_tc = allow_tc && tmin > 0 && nrhs >= tmin;
+  const bool use_tc = path == kMany || (path == kAuto && tmin > 0 && nrhs >= tmin);
   TcWs t{};
   if (use_tc) {
     const size_t tneed = tc_ws_layout(h, nullptr, nullptr);
@@ -1019,14 +1034,19 @@ int hh_info(hh_handle h, hh_info_t* o) {
   o->bound_thm44 = S.bound44;
   o->bound_rounding = S.bound_round;
   o->build_seconds = H.build_seconds;
-  o->tc_blocks = h->tc[0].n_blocks;
-  o->tc_factor_bytes = h->tc[0].factor_bytes;
-  if (h->device < 0)
-    for (const hh::LRBlock& B : H.lr)
-      if (tc_eligible(B)) {
-        o->tc_blocks += 1;
-        o->tc_factor_bytes += (B.m + B.n) * int64_t(B.k) * hh::fmt_bytes(B.fmt);
-      }
+  for (const hh::LRBlock& B : H.lr) {
+    if (B.k == 0) continue;
+    if (tc_eligible(B)) {
+      o->tc_blocks += 1;
+      o->tc_factor_bytes += (B.m + B.n) * int64_t(B.k) * hh::fmt_bytes(B.fmt);
+      o->tc_u_elems += B.m * int64_t(B.k);
+      o->tc_v_elems += B.n * int64_t(B.k);
+    } else if (B.fmt != hh::F64) {
+      o->mr_u_elems += B.m * int64_t(B.k);
+      o->mr_v_elems += B.n * int64_t(B.k);
+    }
+  }
+  for (const hh::DenseBlock& D : H.dense) o->dense_elems += D.m * D.n;
   return HH_OK;
 }
 
@@ -1044,13 +1064,13 @@ int hh_workspace_bytes(hh_handle h, size_t* bytes) {
 
 int hh_matvec(hh_handle h, const double* x, double* y, int nrhs, int64_t ldx, int64_t ldy, void* stream) {
   if (!h) return fail(HH_EINVAL, "null handle");
-  return run_product(h, 0, x, y, nrhs, ldx, ldy, h->d_ws, h->ws_bytes, (cudaStream_t)stream, nullptr, true);
+  return run_product(h, 0, x, y, nrhs, ldx, ldy, h->d_ws, h->ws_bytes, (cudaStream_t)stream, nullptr, kAuto);
 }
 
 int hh_matvec_T(hh_handle h, const double* ybar, double* xbar, int nrhs, int64_t ldy, int64_t ldx,
                 void* stream) {
   if (!h) return fail(HH_EINVAL, "null handle");
-  return run_product(h, 1, ybar, xbar, nrhs, ldy, ldx, h->d_ws, h->ws_bytes, (cudaStream_t)stream, nullptr, true);
+  return run_product(h, 1, ybar, xbar, nrhs, ldy, ldx, h->d_ws, h->ws_bytes, (cudaStream_t)stream, nullptr, kAuto);
 }
 
 int hh_matvec_ws(hh_handle h, int transpose, const double* in, double* out, int nrhs, int64_t ld_in,
@@ -1060,30 +1080,43 @@ int hh_matvec_ws(hh_handle h, int transpose, const double* in, double* out, int 
                      (cudaStream_t)stream);
 }
 
-int hh_matvec_timed(hh_handle h, int transpose, const double* in, double* out, int nrhs, int64_t ld_in,
-                    int64_t ld_out, void* stream, float* ms) {
-  if (!h || !ms) return fail(HH_EINVAL, "null argument");
-  if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data");
-  const int dir = transpose ? 1 : 0;
-  const bool tc = tc_min_nrhs() > 0 && nrhs >= tc_min_nrhs() && nrhs <= hh::dev::kTcMaxRhs;
-  if (!tc && (nrhs < 1 || nrhs > hh::dev::kMaxNR || nrhs == 3))
-    return fail(HH_EINVAL, "nrhs must be 1, 2 or 4, or between the tensor-core threshold and 128");
+// CUDA events around one product (n_ev = 5 for the streaming sequence, 9 for
+// the many-right-hand-side sequence); writes the n_ev - 1 intervals to ms.
+int timed_product(hh_handle h, int dir, const double* in, double* out, int nrhs, int64_t ld_in, int64_t ld_out,
+                  void* stream, float* ms, int n_ev, bool many) {
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != h->device) cudaSetDevice(h->device);
-  cudaEvent_t ev[5];
+  cudaEvent_t ev[9];
   int made = 0;
-  for (; made < 5; ++made)
+  for (; made < n_ev; ++made)
     if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
-  int rc = made == 5 ? HH_OK : fail(HH_ECUDA, "cudaEventCreate failed");
+  int rc = made == n_ev ? HH_OK : fail(HH_ECUDA, "cudaEventCreate failed");
   if (rc == HH_OK)
-    rc = run_product(h, dir, in, out, nrhs, ld_in, ld_out, h->d_ws, h->ws_bytes, (cudaStream_t)stream, ev, tc);
-  if (rc == HH_OK && cudaEventSynchronize(ev[4]) != cudaSuccess) rc = fail(HH_ECUDA, "event synchronize failed");
-  for (int i = 0; rc == HH_OK && i < 4; ++i)
+    rc = run_product(h, dir, in, out, nrhs, ld_in, ld_out, h->d_ws, h->ws_bytes, (cudaStream_t)stream, ev,
+                     many ? kMany : kStreamOnly);
+  if (rc == HH_OK && cudaEventSynchronize(ev[n_ev - 1]) != cudaSuccess) rc = fail(HH_ECUDA, "event synchronize failed");
+  for (int i = 0; rc == HH_OK && i < n_ev - 1; ++i)
     if (cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]) != cudaSuccess) rc = fail(HH_ECUDA, "event timing failed");
   for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
   if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
   return rc;
+}
+
+int hh_matvec_timed(hh_handle h, int transpose, const double* in, double* out, int nrhs, int64_t ld_in,
+                    int64_t ld_out, void* stream, float* ms) {
+  if (!h || !ms) return fail(HH_EINVAL, "null argument");
+  if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data");
+  if (nrhs < 1 || nrhs > hh::dev::kMaxNR || nrhs == 3) return fail(HH_EINVAL, "nrhs must be 1, 2 or 4");
+  return timed_product(h, transpose ? 1 : 0, in, out, nrhs, ld_in, ld_out, stream, ms, 5, false);
+}
+
+int hh_matvec_stages(hh_handle h, int transpose, const double* in, double* out, int nrhs, int64_t ld_in,
+                     int64_t ld_out, void* stream, float* ms) {
+  if (!h || !ms) return fail(HH_EINVAL, "null argument");
+  if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data");
+  if (nrhs < 1 || nrhs > hh::dev::kTcMaxRhs) return fail(HH_EINVAL, "nrhs must be between 1 and 128");
+  return timed_product(h, transpose ? 1 : 0, in, out, nrhs, ld_in, ld_out, stream, ms, 9, true);
 }
 
 int hh_matvec_host(hh_handle h, int transpose, const double* x_host, double* y_host, int nrhs,
@@ -1112,7 +1145,7 @@ int hh_matvec_host(hh_handle h, int transpose, const double* x_host, double* y_h
   if (cudaMemcpyAsync(dx, x_host, sizeof(double) * n * nrhs, cudaMemcpyHostToDevice, st) != cudaSuccess)
     rc = fail(HH_ECUDA, "host-to-device copy failed");
   if (rc == HH_OK)
-    rc = run_product(h, transpose ? 1 : 0, dx, dy, nrhs, n, n, h->d_ws, h->ws_bytes, st, nullptr, true);
+    rc = run_product(h, transpose ? 1 : 0, dx, dy, nrhs, n, n, h->d_ws, h->ws_bytes, st, nullptr, kAuto);
   if (rc == HH_OK &&
       cudaMemcpyAsync(y_host, dy, sizeof(double) * n * nrhs, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     rc = fail(HH_ECUDA, "device-to-host copy failed");

@@ -173,18 +173,20 @@ def max_over_ranks(torch, v, ws):
     return float(t.item())
 
 
-def traffic_for(kernel: str):
-    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
-    the current sources (profiles/traffic.json carries the source digest)."""
+def traffic_for(kernel: str, algorithmic_bytes: float):
+    """DRAM bytes per launch: the traffic / algorithmic-bytes ratio of a
+    committed ncu capture (profiles/traffic.json) times this launch's
+    algorithmic bytes; None unless the kernel's source is the one captured."""
     try:
-        from paper_2604_09147_gb300 import build as b
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            t = json.load(f)
-        if t.get("source_digest") == b._digest() and kernel in t.get("kernels", {}):
-            return float(t["kernels"][kernel]["dram_bytes_per_launch"])
+            t = json.load(f)["kernels"][kernel]
+        src = os.path.join(ROOT, "paper_2604_09147_gb300", "csrc", t["source"])
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
+                return None
+        return float(t["dram_bytes"]) / float(t["algorithmic_bytes"]) * algorithmic_bytes
     except Exception:
-        pass
-    return None
+        return None
 
 
 def oracle_sample(path: str, x: np.ndarray, budget_s: float, fraction: float | None = None):
@@ -306,7 +308,7 @@ def run_ours(args):
         "stream_kernel<2,...> (phase 2: y_I += U_b t_b, dense diagonal)"
     achieved = dom_bytes / (phases[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic_for(f"phase{dom}"), "kernel": dom_name, "peak_kind": f"of {peak_kind}",
+                "traffic": traffic_for(f"phase{dom}", dom_bytes), "kernel": dom_name, "peak_kind": f"of {peak_kind}",
                 "bytes_per_launch": dom_bytes, "ms_per_launch": float(phases[dom]),
                 "phase_ms": {"prep": phases[0], "phase1": phases[1], "phase2": phases[2], "finish": phases[3]}}
 
@@ -425,11 +427,22 @@ def run_many(args):
         t = stages[k] * 1e-3
         detail[k] = {"ms": stages[k], "bound": bound, "tflops": flops / t / 1e12 if t > 0 else None,
                      "peak_tflops": peak, "frac": (flops / t / 1e12) / peak if t > 0 else None, "peak_kind": kind}
+    # bytes of the stored operands each launch reads once (fp32-equivalent for
+    # the CUDA-core phases, whose factors are fp32 here; stored bytes for the
+    # tensor-core phases; fp64 for the dense blocks)
+    tcb = inf["tc_factor_bytes"]
+    tcu = tcb * inf["tc_u_elems"] / max(1, inf["tc_u_elems"] + inf["tc_v_elems"])
+    alg_bytes = {"mr_phase1": 4.0 * inf["mr_v_elems"], "mr_phase2": 4.0 * inf["mr_u_elems"],
+                 "mr_dense": 8.0 * inf["dense_elems"], "tc_phase1": tcb - tcu, "tc_phase2": tcu}
+    for k in detail:
+        t = stages[k] * 1e-3
+        detail[k]["operand_bytes"] = alg_bytes[k]
+        detail[k]["operand_gbs"] = alg_bytes[k] / t / 1e9 if t > 0 else None
     dom = max(per, key=lambda k: stages[k])
     bound, flops, peak, kind = per[dom]
     achieved = flops / (stages[dom] * 1e-3) / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic_for(dom), "kernel": dom, "peak_kind": f"of {kind}",
+                "traffic": traffic_for(dom, alg_bytes[dom]), "kernel": dom, "peak_kind": f"of {kind}",
                 "flops_per_launch": flops, "ms_per_launch": stages[dom], "stages": detail}
 
     # the same columns through the streaming passes, 4 per product

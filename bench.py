@@ -55,6 +55,9 @@ MANY_N = {"multirhs_65k": 65536, "multirhs_262k": 262144}
 for _k, _n in MANY_N.items():
     WORKLOADS[_k] = (f"N={_n:,} points U[0,1]^3, Gaussian exp(-r^2/0.01), leaf 128, eta 1, switch level 5, "
                      "tol 1e-6, adaptive {fp64,fp32,bf16,e4m3}, R right-hand sides N(0,1) per product")
+WORKLOADS["uneven_batch"] = ("64 independent matrices, N log-uniform in [nmin, nmax] (preset [2,048, 131,072]); "
+                             "even index 2-D exp(-r) leaf 64, odd index 3-D 1/r leaf 128; eta 1, switch level "
+                             "floor(L/2), tol 1e-6, adaptive {fp64,fp32,fp16,bf16}; one RHS U(-1,1) each")
 # fp32 FMA issue rate of the CUDA cores: 152 SMs x 128 lanes x 2 flops at the
 # 2,070 MHz maximum SM clock; a product of fp32 pairs (the dense blocks) costs
 # 9 fp32 instructions (3 FMA, 6 add) per multiply-add
@@ -501,6 +504,115 @@ def run_many(args):
     return 0
 
 
+def run_batch(args):
+    """Uneven batch: one product of every matrix per step, as one captured CUDA
+    graph (four kernels for the whole batch), next to the same products as one
+    launch sequence per matrix."""
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", init_method="env://")
+    dev = torch.cuda.current_device()
+    import paper_2604_09147_gb300 as P
+    from paper_2604_09147_gb300 import build as B
+    B.build()
+    specs = W.uneven_batch(args.batch_count, nmin=args.batch_nmin, nmax=args.batch_nmax)
+    t0 = time.time()
+    mats = [P.HMatrix.build_cached(sp["points"], CACHE, sp["kernel"], sp["kernel_param"], sp["leaf"], sp["eta"],
+                                   sp["ell"], sp["tol"], sp["fmts"], device=dev) for sp in specs]
+    build_s = time.time() - t0
+    batch = P.HBatch(mats)
+    xs_h = [sp["x"][:, 0] for sp in specs]
+    x = torch.from_numpy(np.concatenate(xs_h)).cuda()
+    y = torch.empty_like(x)
+    xs = [x[batch.offsets[i]:batch.offsets[i + 1]] for i in range(len(mats))]
+    ys = [y[batch.offsets[i]:batch.offsets[i + 1]] for i in range(len(mats))]
+    infos = [m.info() for m in mats]
+    total_bytes = sum(i["bytes_per_matvec"] for i in infos)
+    for _ in range(args.warmup):
+        batch.matvec(x, out=y, graph=True)
+        for m, xi, yi in zip(mats, xs, ys):
+            m.matvec(xi, out=yi)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, steps):
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        return max_over_ranks(torch, e0.elapsed_time(e1), ws)
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t_graph = timed(lambda: batch.matvec(x, out=y, graph=True), args.steps)
+    t_seq = timed(lambda: batch.matvec(x, out=y), args.steps)
+    t_each = timed(lambda: [m.matvec(xi, out=yi) for m, xi, yi in zip(mats, xs, ys)], args.steps)
+    clk = clocks.stop()
+    mats[0].sync_status()
+    ms = t_graph / args.steps
+    count = len(mats)
+    value = ws * args.steps * count / (t_graph / 1000.0)
+    hbm, peak_kind = peaks()
+    gbs = total_bytes / (ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+                "kernel": "whole batch (prep, stream_kernel phase 1 and 2, finish) per graph launch",
+                "peak_kind": f"of {peak_kind}", "bytes_per_launch": total_bytes, "ms_per_launch": ms}
+    # end to end: pinned host vector in, product, host vector out
+    xh = torch.empty_like(x, device="cpu").pin_memory()
+    xh.copy_(x.cpu())
+    yh = torch.empty_like(xh).pin_memory()
+    e2e_steps = max(3, min(args.steps, 200))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        x.copy_(xh, non_blocking=True)
+        batch.matvec(x, out=y, graph=True)
+        yh.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ws * e2e_steps * count / max_over_ranks(torch, e2e_s, ws), "unit": "matvec/s",
+           "h2d_bytes_per_step": 8 * x.numel(), "d2h_bytes_per_step": 8 * x.numel()}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # the oracle on the largest matrix of the batch, scaled by bytes to the whole batch
+        big = max(range(count), key=lambda i: infos[i]["bytes_per_matvec"])
+        path = os.path.join(CACHE, "bench_batch_big.hhm")
+        mats[big].save(path)
+        rate, desc, _ = oracle_sample(path, xs_h[big], args.cpu_seconds)
+        scale = infos[big]["bytes_per_matvec"] / total_bytes
+        cpu = {"value": rate * scale * count, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": desc + f"; matrix {big} (N={specs[big]['n']}), scaled by bytes to the batch"}
+    out = {
+        "metric": "H_h matvecs/s over an uneven batch (one CUDA graph per batch product)",
+        "value": value, "unit": "matvec/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "dtype_note": "fp32 accumulation for 32/16/8-bit factors; fp64 data as fp32 pairs",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["uneven_batch"], "count": count, "nmin": args.batch_nmin,
+                   "nmax": args.batch_nmax, "n_total": int(x.numel()), "parallelism": f"replicas x{ws}",
+                   "l2": "batch bytes %.2f GB per step" % (total_bytes / 1e9)},
+        "one_sequence": {"ms_per_step": t_seq / args.steps},
+        "per_matrix_launches": {"ms_per_step": t_each / args.steps, "speedup_graph": t_each / t_graph},
+        "build_seconds": build_s, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": 4 * args.steps, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    batch.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -511,6 +623,9 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU oracle baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nrhs", type=int, default=128, help="right-hand sides per product (multirhs workloads)")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-nmin", type=int, default=2048)
+    ap.add_argument("--batch-nmax", type=int, default=131072)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -520,6 +635,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload in MANY_N:
         return run_many(args)
+    if args.workload == "uneven_batch":
+        return run_batch(args)
     return run_ours(args)
 
 

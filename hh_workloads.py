@@ -78,15 +78,16 @@ def config_rhs(name: str, nrhs: int = 1, n: int | None = None) -> np.ndarray:
     return rhs(c["n"] if n is None else n, nrhs, c["rhs"], 42 + c["id"])
 
 
-def uneven_batch(count: int = 64, seed: int = 1238):
-    """The uneven batch of independent matrices: N log-uniform in [2,048, 131,072].
+def uneven_batch(count: int = 64, seed: int = 1238, nmin: int = 2048, nmax: int = 131072):
+    """The uneven batch of independent matrices: N log-uniform in [nmin, nmax]
+    (the preset: [2,048, 131,072]).
 
     Even index: 2-D exp(-r), leaf 64.  Odd index: 3-D 1/r, leaf 128.  eta 1,
     tol 1e-6, adaptive {fp64, fp32, fp16, bf16}, switch level -1 (floor(L/2)).
     Returns a list of dicts with the build parameters and the points.
     """
     g = _rng(seed)
-    ns = np.exp(g.uniform(math.log(2048), math.log(131072), size=count)).astype(np.int64)
+    ns = np.exp(g.uniform(math.log(nmin), math.log(nmax), size=count)).astype(np.int64)
     out = []
     for i, n in enumerate(ns):
         if i % 2 == 0:

@@ -69,6 +69,7 @@ enum hh_fmt { HH_FMT_F64 = 0, HH_FMT_F32 = 1, HH_FMT_F16 = 2, HH_FMT_BF16 = 3, H
 #define HH_E4M3 16u
 
 typedef struct hh_matrix* hh_handle;
+typedef struct hh_batch_s* hh_batch;
 
 #define HH_MAX_LEVELS 48
 
@@ -218,6 +219,33 @@ int hh_matvec_stages(hh_handle h, int transpose, const double* in, double* out, 
  * concatenated work lists.  All handles must live on the same device. */
 int hh_matvec_batched(const hh_handle* hs, int count, const double* const* xs,
                       double* const* ys, void* stream);
+
+/* Batches of independent matrices (one right-hand side each) in one launch
+ * sequence.  The product of every matrix is Algorithm 4 as above; the batch
+ * only concatenates the work tables, so one product of the whole batch is
+ * four kernel launches (prep, phase 1, phase 2, finish) whatever the count.
+ *
+ * hh_batch_create -- a batch over `count` >= 1 handles on one device.  The
+ *   handles must stay alive (not hh_free'd) while the batch exists.  Allocates
+ *   the batch's tables and workspace (about 40 bytes per point plus the t
+ *   arenas); HH_ENOTSUP for a handle without device data, HH_EINVAL for
+ *   handles on different devices or more than 2^31 positions in total.
+ * hh_batch_offsets -- offsets[count + 1]: matrix i's vector occupies
+ *   [offsets[i], offsets[i + 1]) of the concatenated input and output (its n
+ *   entries in its own point order).
+ * hh_batch_matvec -- y = blockdiag(A_i) x (transpose != 0: the transposes)
+ *   for concatenated device vectors x and y (no overlap); asynchronous on
+ *   `stream`; allocates nothing, so it may be captured in a CUDA graph; calls
+ *   on one batch must be ordered on one stream (one workspace).
+ * hh_batch_matvec_graph -- the same through a CUDA graph that the batch
+ *   captures on first use (and again when x, y or transpose change) and then
+ *   replays on `stream` with one graph launch.
+ * hh_batch_free -- NULL-safe. */
+int hh_batch_create(const hh_handle* hs, int count, hh_batch* out);
+int hh_batch_offsets(hh_batch b, int64_t* offsets);
+int hh_batch_matvec(hh_batch b, int transpose, const double* x, double* y, void* stream);
+int hh_batch_matvec_graph(hh_batch b, int transpose, const double* x, double* y, void* stream);
+void hh_batch_free(hh_batch b);
 
 /* hh_matvec_noalloc -- y = A_h x (transpose != 0: A_h^T x) for ONE
  * right-hand side (x, y device, ld = n) that allocates nothing: no

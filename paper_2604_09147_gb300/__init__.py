@@ -75,6 +75,11 @@ def _load():
         "hh_matvec_timed": (I32, [P, I32, P, P, I32, I64, I64, P, c.POINTER(c.c_float)]),
         "hh_matvec_stages": (I32, [P, I32, P, P, I32, I64, I64, P, c.POINTER(c.c_float)]),
         "hh_matvec_batched": (I32, [c.POINTER(P), I32, c.POINTER(P), c.POINTER(P), P]),
+        "hh_batch_create": (I32, [c.POINTER(P), I32, c.POINTER(P)]),
+        "hh_batch_offsets": (I32, [P, c.POINTER(I64)]),
+        "hh_batch_matvec": (I32, [P, I32, P, P, P]),
+        "hh_batch_matvec_graph": (I32, [P, I32, P, P, P]),
+        "hh_batch_free": (None, [P]),
         "hh_sync_status": (I32, [P, P]),
         "hh_free": (None, [P]),
         "hh_last_error": (c.c_char_p, []),
@@ -294,6 +299,46 @@ def matvec_batched(mats: list, xs: list) -> list:
     yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
     _check(_L().hh_matvec_batched(hs, n, xp, yp, _stream_ptr(xs[0].device) if n else 0))
     return ys
+
+
+class HBatch:
+    """Independent matrices (one right-hand side each) multiplied in one launch
+    sequence over concatenated vectors: matrix i's vector is
+    x[offsets[i]:offsets[i+1]] in its own point order.  The matrices must stay
+    open while the batch exists."""
+
+    def __init__(self, mats: list):
+        self.mats = list(mats)
+        hs = (ctypes.c_void_p * len(mats))(*[m._h.value for m in mats])
+        out = ctypes.c_void_p()
+        _check(_L().hh_batch_create(hs, len(mats), ctypes.byref(out)))
+        self._b = out
+        offs = (ctypes.c_int64 * (len(mats) + 1))()
+        _check(_L().hh_batch_offsets(self._b, offs))
+        self.offsets = [int(v) for v in offs]
+        self.device = mats[0].device
+
+    def matvec(self, x: torch.Tensor, transpose: bool = False, out: torch.Tensor | None = None,
+               graph: bool = False) -> torch.Tensor:
+        """y = blockdiag(A_i) x (graph=True: replay a captured CUDA graph)."""
+        if x.dtype != torch.float64 or not x.is_cuda or x.dim() != 1 or not x.is_contiguous() \
+                or x.numel() != self.offsets[-1]:
+            raise ValueError("x must be a contiguous float64 CUDA vector of the concatenated size")
+        y = torch.empty_like(x) if out is None else out
+        f = _L().hh_batch_matvec_graph if graph else _L().hh_batch_matvec
+        _check(f(self._b, 1 if transpose else 0, x.data_ptr(), y.data_ptr(), _stream_ptr(x.device)))
+        return y
+
+    def close(self) -> None:
+        if getattr(self, "_b", None) and self._b.value:
+            _L().hh_batch_free(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class HhMatvec(torch.autograd.Function):

@@ -46,7 +46,12 @@ struct StreamSet {
   Item* d_items[2] = {nullptr, nullptr};
   int n_items[2] = {0, 0};
   unsigned fset = hh::dev::kSetAll;
-  int grid[3][5] = {};  // [phase][nr]
+  unsigned present = 0;  // formats of the low-rank blocks in the set (bit f)
+  int grid[3][5] = {};   // [phase][nr]
+  // host copies (batches concatenate them)
+  std::vector<hh::dev::StreamDesc> h_desc[2];
+  std::vector<Item> h_items[2];
+  std::vector<double> h_cost[2];
 };
 
 // Work tables of the tensor-core path (tc.cu) for one direction.
@@ -266,11 +271,19 @@ void build_stream_set(hh_matrix* h, int dir, const std::vector<int64_t>& toff, c
     std::stable_sort(items[p].begin(), items[p].end(),
                      [](const Costed& x, const Costed& y) { return x.cost > y.cost; });
     std::vector<Item> flat;
-    for (auto& c : items[p]) flat.push_back(c.it);
+    std::vector<double> cost;
+    for (auto& c : items[p]) {
+      flat.push_back(c.it);
+      cost.push_back(c.cost);
+    }
     out.d_desc[p] = upload(desc[p]);
     out.d_items[p] = upload(flat);
     out.n_items[p] = (int)flat.size();
+    out.h_desc[p] = desc[p];
+    out.h_items[p] = flat;
+    out.h_cost[p] = cost;
   }
+  out.present = present;
   out.fset = hh::dev::pass_set_for(present);
   for (int phase = 1; phase <= 2; ++phase)
     for (int nr : {1, 2, 4}) out.grid[phase][nr] = h->sms * hh::dev::stream_blocks_per_sm(phase, out.fset, nr);
@@ -1188,6 +1201,273 @@ void hh_free(hh_handle h) {
   if (!h) return;
   free_device(h);
   delete h;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent matrices (hh_batch_*, see include/hh.h): the
+// streaming tables of every matrix concatenated over one position space, so
+// that one product of the whole batch is four launches whatever the count.
+struct hh_batch_s {
+  std::vector<hh_matrix*> mats;
+  int device = -1;
+  int sms = 0;
+  int count = 0;
+  int64_t np = 0;                 // concatenated positions
+  std::vector<int64_t> offsets;   // caller-order vector offsets, count + 1
+  int64_t* d_xofs = nullptr;
+  int64_t* d_pofs = nullptr;
+  int64_t* d_ns = nullptr;
+  int32_t* d_perm = nullptr;
+  StreamSet ss[2];
+  void* d_ws = nullptr;
+  float* xs = nullptr;
+  float* xs_lo = nullptr;
+  double* acc = nullptr;
+  float* t32 = nullptr;
+  float2* t64 = nullptr;
+  int* counters = nullptr;
+  cudaStream_t cap = nullptr;     // private stream for graph capture
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  const double* gx[2] = {nullptr, nullptr};
+  double* gy[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+void free_batch(hh_batch_s* b) {
+  if (b->device < 0) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != b->device) cudaSetDevice(b->device);
+  for (int d = 0; d < 2; ++d) {
+    for (int p = 0; p < 2; ++p) {
+      cudaFree(b->ss[d].d_desc[p]);
+      cudaFree(b->ss[d].d_items[p]);
+    }
+    if (b->gexec[d]) cudaGraphExecDestroy(b->gexec[d]);
+  }
+  cudaFree(b->d_xofs);
+  cudaFree(b->d_pofs);
+  cudaFree(b->d_ns);
+  cudaFree(b->d_perm);
+  cudaFree(b->d_ws);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (cur >= 0 && cur != b->device) cudaSetDevice(cur);
+}
+
+cudaError_t batch_launches(hh_batch_s* b, int dir, const double* x, double* y, cudaStream_t st) {
+  cudaError_t e = hh::dev::launch_batch_prep(x, b->d_xofs, b->d_perm, b->d_pofs, b->d_ns, b->count, b->np, b->xs,
+                                             b->xs_lo, b->acc, b->counters, st);
+  for (int phase = 1; phase <= 2 && e == cudaSuccess; ++phase) {
+    const StreamSet& set = b->ss[dir];
+    hh::dev::StreamArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.desc = set.d_desc[phase - 1];
+    a.items = set.d_items[phase - 1];
+    a.n_items = set.n_items[phase - 1];
+    a.nr = 1;
+    a.npad = b->np;
+    a.xs = b->xs;
+    a.xs_lo = b->xs_lo;
+    a.t32 = b->t32;
+    a.t64 = b->t64;
+    a.acc = b->acc;
+    a.status = b->mats[0]->d_status;
+    a.counter = b->counters + (phase - 1);
+    if (a.n_items == 0) continue;
+    const int grid = std::max(1, std::min(set.grid[phase][1], a.n_items));
+    e = hh::dev::launch_stream(phase, set.fset, a, grid, st);
+  }
+  if (e == cudaSuccess)
+    e = hh::dev::launch_batch_finish(b->acc, b->d_xofs, b->d_perm, b->d_pofs, b->d_ns, b->count, b->np, y, st);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hh_batch_create(const hh_handle* hs, int count, hh_batch* out) {
+  if (!out) return fail(HH_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !hs) return fail(HH_EINVAL, "need at least one handle");
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return fail(HH_EINVAL, "null handle in batch");
+    if (hs[i]->device < 0) return fail(HH_ENOTSUP, "handle without device data in batch");
+    if (hs[i]->device != hs[0]->device) return fail(HH_EINVAL, "handles on different devices");
+  }
+  hh_batch_s* b = new (std::nothrow) hh_batch_s();
+  if (!b) return fail(HH_ENOMEM, "out of host memory");
+  int cur = -1;
+  cudaGetDevice(&cur);
+  try {
+    ck(cudaSetDevice(hs[0]->device), "cudaSetDevice");
+    b->device = hs[0]->device;
+    b->sms = hs[0]->sms;
+    b->count = count;
+    std::vector<int64_t> pofs(count + 1, 0), ns(count, 0);
+    b->offsets.assign(count + 1, 0);
+    int64_t t32 = 0, t64 = 0;
+    std::vector<int64_t> t32o(count), t64o(count);
+    for (int i = 0; i < count; ++i) {
+      hh_matrix* h = hs[i];
+      b->mats.push_back(h);
+      ns[i] = h->H.n;
+      pofs[i + 1] = pofs[i] + h->npad;
+      b->offsets[i + 1] = b->offsets[i] + h->H.n;
+      t32o[i] = t32;
+      t64o[i] = t64;
+      t32 += h->t32_elems;
+      t64 += h->t64_elems;
+    }
+    b->np = pofs[count];
+    if (b->np + 64 > (int64_t(1) << 31)) throw std::invalid_argument("batch too large for 32-bit positions");
+    std::vector<int32_t> perm(static_cast<size_t>(b->np), 0);
+    for (int i = 0; i < count; ++i) std::copy(hs[i]->H.perm.begin(), hs[i]->H.perm.end(), perm.begin() + pofs[i]);
+    b->d_xofs = upload(b->offsets);
+    b->d_pofs = upload(pofs);
+    b->d_ns = upload(ns);
+    b->d_perm = upload(perm);
+    for (int dir = 0; dir < 2; ++dir) {
+      unsigned present = 0;
+      for (int p = 0; p < 2; ++p) {
+        std::vector<hh::dev::StreamDesc> desc;
+        std::vector<std::pair<Item, double>> items;
+        for (int i = 0; i < count; ++i) {
+          const StreamSet& src = hs[i]->ss[dir];
+          const int base = (int)desc.size();
+          for (hh::dev::StreamDesc d : src.h_desc[p]) {
+            d.in_off += (int32_t)pofs[i];
+            d.out_off += (int32_t)pofs[i];
+            if (d.mode == 0) d.toff += (d.fmt == hh::F64 ? t64o[i] : t32o[i]) * hh::dev::kMaxNR;
+            desc.push_back(d);
+          }
+          for (size_t k = 0; k < src.h_items[p].size(); ++k) {
+            Item it = src.h_items[p][k];
+            it.idx += base;
+            items.push_back({it, src.h_cost[p][k]});
+          }
+          present |= src.present;
+        }
+        std::stable_sort(items.begin(), items.end(), [](const auto& x, const auto& y) { return x.second > y.second; });
+        std::vector<Item> flat;
+        for (auto& it : items) flat.push_back(it.first);
+        b->ss[dir].d_desc[p] = upload(desc);
+        b->ss[dir].d_items[p] = upload(flat);
+        b->ss[dir].n_items[p] = (int)flat.size();
+      }
+      b->ss[dir].present = present;
+      b->ss[dir].fset = hh::dev::pass_set_for(present);
+      for (int phase = 1; phase <= 2; ++phase)
+        b->ss[dir].grid[phase][1] = b->sms * hh::dev::stream_blocks_per_sm(phase, b->ss[dir].fset, 1);
+    }
+    // workspace: shifted input copies, output accumulator, t arenas, counters
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      size_t o = off;
+      off = align256(off + bytes);
+      return o;
+    };
+    const size_t o_xs = take(sizeof(float) * 4 * b->np), o_lo = take(sizeof(float) * 4 * b->np);
+    const size_t o_acc = take(sizeof(double) * b->np);
+    const size_t o_t32 = take(sizeof(float) * std::max<int64_t>(1, t32 * hh::dev::kMaxNR));
+    const size_t o_t64 = take(sizeof(float2) * std::max<int64_t>(1, t64 * hh::dev::kMaxNR));
+    const size_t o_cnt = take(256);
+    ck(cudaMalloc(&b->d_ws, off), "cudaMalloc batch workspace");
+    char* w = static_cast<char*>(b->d_ws);
+    b->xs = reinterpret_cast<float*>(w + o_xs);
+    b->xs_lo = reinterpret_cast<float*>(w + o_lo);
+    b->acc = reinterpret_cast<double*>(w + o_acc);
+    b->t32 = reinterpret_cast<float*>(w + o_t32);
+    b->t64 = reinterpret_cast<float2*>(w + o_t64);
+    b->counters = reinterpret_cast<int*>(w + o_cnt);
+    ck(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+  } catch (const CudaError& e) {
+    free_batch(b);
+    delete b;
+    if (cur >= 0) cudaSetDevice(cur);
+    return fail(HH_ECUDA, e.what());
+  } catch (const std::bad_alloc&) {
+    free_batch(b);
+    delete b;
+    if (cur >= 0) cudaSetDevice(cur);
+    return fail(HH_ENOMEM, "out of host memory");
+  } catch (const std::exception& e) {
+    free_batch(b);
+    delete b;
+    if (cur >= 0) cudaSetDevice(cur);
+    return fail(HH_EINVAL, e.what());
+  }
+  if (cur >= 0 && cur != b->device) cudaSetDevice(cur);
+  *out = b;
+  return HH_OK;
+}
+
+int hh_batch_offsets(hh_batch b, int64_t* offsets) {
+  if (!b || !offsets) return fail(HH_EINVAL, "null argument");
+  std::copy(b->offsets.begin(), b->offsets.end(), offsets);
+  return HH_OK;
+}
+
+int hh_batch_matvec(hh_batch b, int transpose, const double* x, double* y, void* stream) {
+  if (!b || !x || !y) return fail(HH_EINVAL, "null argument");
+  const size_t span = static_cast<size_t>(b->offsets[b->count]) * sizeof(double);
+  if ((const char*)x < (const char*)y + span && (const char*)y < (const char*)x + span)
+    return fail(HH_EINVAL, "input and output overlap");
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != b->device && cudaSetDevice(b->device) != cudaSuccess) return fail(HH_ECUDA, "cudaSetDevice failed");
+  cudaError_t e = batch_launches(b, transpose ? 1 : 0, x, y, (cudaStream_t)stream);
+  if (cur >= 0 && cur != b->device) cudaSetDevice(cur);
+  if (e != cudaSuccess) return fail(HH_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+  return HH_OK;
+}
+
+int hh_batch_matvec_graph(hh_batch b, int transpose, const double* x, double* y, void* stream) {
+  if (!b || !x || !y) return fail(HH_EINVAL, "null argument");
+  const size_t span = static_cast<size_t>(b->offsets[b->count]) * sizeof(double);
+  if ((const char*)x < (const char*)y + span && (const char*)y < (const char*)x + span)
+    return fail(HH_EINVAL, "input and output overlap");
+  const int dir = transpose ? 1 : 0;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != b->device && cudaSetDevice(b->device) != cudaSuccess) return fail(HH_ECUDA, "cudaSetDevice failed");
+  int rc = HH_OK;
+  if (!b->gexec[dir] || b->gx[dir] != x || b->gy[dir] != y) {
+    if (b->gexec[dir]) {
+      cudaStreamSynchronize((cudaStream_t)stream);
+      cudaGraphExecDestroy(b->gexec[dir]);
+      b->gexec[dir] = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+    cudaError_t e2 = cudaSuccess;
+    if (e == cudaSuccess) {
+      e2 = batch_launches(b, dir, x, y, b->cap);
+      e = cudaStreamEndCapture(b->cap, &g);
+    }
+    if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&b->gexec[dir], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      b->gexec[dir] = nullptr;
+      rc = fail(HH_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    } else {
+      b->gx[dir] = x;
+      b->gy[dir] = y;
+    }
+  }
+  if (rc == HH_OK && cudaGraphLaunch(b->gexec[dir], (cudaStream_t)stream) != cudaSuccess)
+    rc = fail(HH_ECUDA, "cudaGraphLaunch failed");
+  if (cur >= 0 && cur != b->device) cudaSetDevice(cur);
+  return rc;
+}
+
+void hh_batch_free(hh_batch b) {
+  if (!b) return;
+  free_batch(b);
+  delete b;
 }
 
 }  // extern "C"

@@ -65,6 +65,16 @@ cudaError_t launch_finish(const double* acc, int nr, const int32_t* perm, int64_
 
 constexpr int kMaxNR = 4;  // right-hand sides per launch sequence
 
+// batches (kernels.cu): one right-hand side per matrix; matrix j's tree-order
+// positions are [pofs[j], pofs[j] + npad_j) of the concatenated position space
+// (np in total), its caller-order vector starts at xofs[j] of the
+// concatenated input / output; perm holds each matrix's permutation at pofs[j]
+cudaError_t launch_batch_prep(const double* x, const int64_t* xofs, const int32_t* perm, const int64_t* pofs,
+                              const int64_t* ns, int count, int64_t np, float* xs, float* xs_lo, double* acc,
+                              int* counters, cudaStream_t st);
+cudaError_t launch_batch_finish(const double* acc, const int64_t* xofs, const int32_t* perm, const int64_t* pofs,
+                                const int64_t* ns, int count, int64_t np, double* y, cudaStream_t st);
+
 // ---- tensor-core path for many right-hand sides (tc.cu) ----
 // A piece: ranks [r0, r0 + k) of one low-rank block stored in fp16, bf16 or
 // e4m3.  f1 / f2 point at the piece's first rank column of the phase-1

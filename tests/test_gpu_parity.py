@@ -198,3 +198,54 @@ def test_host_api_and_batched(P, tmp_path):
         assert rel(H.matvec_host(x), M.matvec(O, x)) <= TOL32
         assert rel(H.matvec_ws(gpu(x)).cpu().numpy(), M.matvec(O, x)) <= TOL32
         H.sync_status()
+
+
+def test_batch_one_launch_sequence_and_graph(P, tmp_path):
+    """Uneven batch (2-D exp and 3-D 1/r, sizes that are not multiples of the
+    leaf size) through one launch sequence and through a captured CUDA graph,
+    forward and transposed, against the oracle per matrix."""
+    specs = [(3000, 2, W.EXP, 64), (5184, 3, W.INV_R, 128), (2100, 2, W.EXP, 64), (7777, 3, W.INV_R, 128),
+             (4096, 2, W.EXP, 64), (2500, 3, W.INV_R, 64)]
+    mats, oracles, xs = [], [], []
+    for i, (n, dim, kern, leaf) in enumerate(specs):
+        H = P.HMatrix.build(W.points(n, dim, 9100 + i), kernel=kern, kernel_param=1.0, leaf_size=leaf, eta=1.0,
+                            switch_level=-1, tol=1e-6, fmt_mask=W.F64 | W.F32 | W.F16 | W.BF16, device=0)
+        path = str(tmp_path / f"b{i}.hhm")
+        H.save(path)
+        mats.append(H)
+        oracles.append(hhfile.read(path))
+        xs.append(W.rhs(n, 1, "uniform", 9200 + i)[:, 0])
+    B = P.HBatch(mats)
+    assert B.offsets == list(np.cumsum([0] + [s[0] for s in specs]))
+    x = gpu(np.concatenate(xs))
+    for tr in (False, True):
+        y1 = B.matvec(x, transpose=tr).cpu().numpy()
+        y2 = B.matvec(x, transpose=tr, graph=True).cpu().numpy()
+        y3 = B.matvec(x, transpose=tr, graph=True).cpu().numpy()  # replay
+        mats[0].sync_status()
+        for i, O in enumerate(oracles):
+            a, b = B.offsets[i], B.offsets[i + 1]
+            ref = M.matvec_T(O, xs[i]) if tr else M.matvec(O, xs[i])
+            assert rel(y1[a:b], ref) <= TOL32
+        # replays agree up to the order of the fp64 atomic additions
+        assert rel(y3, y2) <= 1e-12
+        assert rel(y2, y1) <= 1e-12
+    B.close()
+
+
+def test_batch_fp64_matrices_match_at_1e12(P, tmp_path):
+    """A batch of uniform-fp64 matrices keeps the fp64 path's 1e-12."""
+    mats, oracles, xs = [], [], []
+    for i, n in enumerate((1500, 3333, 2048)):
+        O = OB.build(W.points(n, 2, 9300 + i), W.EXP, 1.0, 64, 1.0, -1, 1e-8, W.F64)
+        path = str(tmp_path / f"f{i}.hhm")
+        hhfile.write(O, path)
+        mats.append(P.HMatrix.load(path, 0))
+        oracles.append(O)
+        xs.append(W.rhs(n, 1, "uniform", 9400 + i)[:, 0])
+    B = P.HBatch(mats)
+    y = B.matvec(gpu(np.concatenate(xs)), graph=True).cpu().numpy()
+    for i, O in enumerate(oracles):
+        a, b = B.offsets[i], B.offsets[i + 1]
+        assert rel(y[a:b], M.matvec(O, xs[i])) <= TOL64
+    B.close()

@@ -280,6 +280,7 @@ def run_ours(args):
     xh0 = W.config_rhs("adaptive_65k", n=n)[:, 0]
     x = torch.from_numpy(xh0.copy()).cuda()
     y = torch.empty_like(x)
+    tuned = {"adaptive": Ham.autotune(0), "fp64": H64.autotune(0)}
     inf, inf64 = Ham.info(), H64.info()
     for _ in range(args.warmup):
         Ham.matvec(x, out=y)
@@ -359,7 +360,7 @@ def run_ours(args):
         "bound_thm44": inf["bound_thm44"],
         "build_seconds": build_s,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": 4 * args.steps, "clocks": clk,
+        "gpu_launches": 4 * args.steps, "clocks": clk, "autotune": tuned,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -397,6 +398,7 @@ def run_many(args):
     X0 = W.config_rhs("multirhs_262k", nrhs=R, n=n)            # (n, R) column-major
     x = torch.from_numpy(np.ascontiguousarray(X0.T)).cuda().t()  # device, column-major
     y = torch.empty((R, n), dtype=torch.float64, device="cuda").t()
+    tuned = H.autotune(R)
     inf = H.info()
     for _ in range(args.warmup):
         H.matvec(x, out=y)
@@ -495,7 +497,7 @@ def run_many(args):
         "blocks_per_fmt": inf["blocks_per_fmt"], "factor_bytes_per_fmt": inf["factor_bytes_per_fmt"],
         "tc_factor_bytes": inf["tc_factor_bytes"], "bound_thm44": inf["bound_thm44"], "build_seconds": build_s,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches * args.steps, "clocks": clk,
+        "gpu_launches": launches * args.steps, "clocks": clk, "autotune": tuned,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -101,6 +101,11 @@ typedef struct {
   int64_t mr_u_elems, mr_v_elems; /* the same for the 32/16/8-bit blocks that the
                                      many-right-hand-side path runs on CUDA cores  */
   int64_t dense_elems;            /* entries of the dense blocks                     */
+  int32_t tuned;                  /* 1 after hh_autotune                             */
+  int32_t split_positions;        /* positions of a many-column phase-1 item         */
+  int32_t blocks_per_sm[4];       /* streaming CTAs per SM chosen by hh_autotune:
+                                     {fwd phase 1, fwd phase 2, T phase 1, T phase 2};
+                                     0 = the occupancy maximum                       */
 } hh_info_t;
 
 /*
@@ -204,6 +209,16 @@ int hh_matvec_host(hh_handle h, int transpose, const double* x_host, double* y_h
  * measurement; uses the handle's workspace. */
 int hh_matvec_timed(hh_handle h, int transpose, const double* in, double* out, int nrhs,
                     int64_t ld_in, int64_t ld_out, void* stream, float* ms);
+
+/* hh_autotune -- choose launch parameters by timing them on the device
+ * (CUDA events, a private stream, temporary buffers of 2 n max(4, nrhs_many)
+ * doubles): the CTAs per SM of each streaming pass (1 .. occupancy maximum,
+ * per direction and phase) and, when nrhs_many > 0, the positions per
+ * many-column phase-1 item ({256, ..., 4096}) for products of nrhs_many
+ * columns.  The choices stay in the handle (hh_info reports them); results
+ * of products do not depend on them beyond rounding.  Synchronous; not
+ * concurrent with products on the same handle. */
+int hh_autotune(hh_handle h, int nrhs_many);
 
 /* hh_matvec_stages -- one product of 1 <= nrhs <= 128 right-hand sides
  * through the many-right-hand-side sequence (whatever nrhs), with CUDA events

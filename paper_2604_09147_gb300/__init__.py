@@ -51,6 +51,7 @@ class _Info(ctypes.Structure):
         ("tc_blocks", ctypes.c_int64), ("tc_factor_bytes", ctypes.c_int64),
         ("tc_u_elems", ctypes.c_int64), ("tc_v_elems", ctypes.c_int64),
         ("mr_u_elems", ctypes.c_int64), ("mr_v_elems", ctypes.c_int64), ("dense_elems", ctypes.c_int64),
+        ("tuned", ctypes.c_int32), ("split_positions", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32 * 4),
     ]
 
 
@@ -74,6 +75,7 @@ def _load():
         "hh_matvec_host": (I32, [P, I32, P, P, I32, P]),
         "hh_matvec_timed": (I32, [P, I32, P, P, I32, I64, I64, P, c.POINTER(c.c_float)]),
         "hh_matvec_stages": (I32, [P, I32, P, P, I32, I64, I64, P, c.POINTER(c.c_float)]),
+        "hh_autotune": (I32, [P, I32]),
         "hh_matvec_batched": (I32, [c.POINTER(P), I32, c.POINTER(P), c.POINTER(P), P]),
         "hh_batch_create": (I32, [c.POINTER(P), I32, c.POINTER(P)]),
         "hh_batch_offsets": (I32, [P, c.POINTER(I64)]),
@@ -213,7 +215,15 @@ class HMatrix:
         d["blocks_per_fmt"] = {FMT_NAMES[i]: int(s.blocks_per_fmt[i]) for i in range(5)}
         d["factor_bytes_per_fmt"] = {FMT_NAMES[i]: int(s.factor_bytes_per_fmt[i]) for i in range(5)}
         d["csp"] = [int(s.csp[i]) for i in range(s.L + 1)]
+        d["blocks_per_sm"] = [int(v) for v in s.blocks_per_sm]
         return d
+
+    def autotune(self, nrhs_many: int = 0) -> dict:
+        """Time candidate launch parameters on the device and keep the fastest
+        (streaming CTAs per SM; with nrhs_many > 0 the many-column item split)."""
+        _check(_L().hh_autotune(self._h, int(nrhs_many)))
+        i = self.info()
+        return {"blocks_per_sm": i["blocks_per_sm"], "split_positions": i["split_positions"]}
 
     def perm(self) -> np.ndarray:
         p = np.empty(self.n, dtype=np.int32)

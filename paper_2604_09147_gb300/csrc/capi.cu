@@ -103,6 +103,11 @@ struct hh_matrix {
   MrSet mr[2];         // [direction]
   void* d_tc_ws = nullptr;  // tensor-core workspace, allocated on first use
   size_t tc_ws_bytes = 0;
+  std::vector<int64_t> doff;   // dense block offsets in d_dense_pad
+  std::vector<int32_t> dexp;   // and their scale exponents
+  int split_len = hh::dev::kTcSplitPositions;  // positions of a many-column phase-1 item
+  int blocks_per_sm[2][3] = {};                // streaming grid per [direction][phase] (0: occupancy)
+  int tuned = 0;
 };
 
 namespace {
@@ -312,13 +317,7 @@ bool tc_eligible(const hh::LRBlock& B) {
 void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
   using namespace hh::dev;
   const hh::HostMatrix& H = h->H;
-  // positions of one phase-1 item (HH_TC_SPLIT_POSITIONS, a positive multiple
-  // of 16, overrides; read when a handle is constructed)
-  int split_len = kTcSplitPositions;
-  if (const char* e = std::getenv("HH_TC_SPLIT_POSITIONS")) {
-    const int v = std::atoi(e);
-    if (v >= 16 && v % 16 == 0) split_len = v;
-  }
+  const int split_len = h->split_len;
   struct Key {
     int64_t in_off, rows;
     int fmt;
@@ -556,12 +555,12 @@ void build_mr_set(hh_matrix* h, int dir, const std::vector<int64_t>& doff, const
         pieces.push_back(q);
         ++t;
       }
-      g.nsplit = (g.rows + kTcSplitPositions - 1) / kTcSplitPositions;
+      g.nsplit = (g.rows + h->split_len - 1) / h->split_len;
       for (int sp = 0; sp < g.nsplit; ++sp) {
         TcGroup gs = g;
         gs.split = sp;
-        gs.p0 = sp * kTcSplitPositions;
-        gs.p1 = std::min(g.rows, (sp + 1) * kTcSplitPositions);
+        gs.p0 = sp * h->split_len;
+        gs.p1 = std::min(g.rows, (sp + 1) * h->split_len);
         groups.push_back({gs, double(gs.p1 - gs.p0) * g.nk * hh::fmt_bytes(g.fmt)});
       }
     }
@@ -624,11 +623,17 @@ void upload_matrix(hh_matrix* h, int device) {
     toff[b] = tot * hh::dev::kMaxNR;
     tot += H.lr[b].k;
   }
-  std::vector<int64_t> doff;
-  std::vector<int32_t> dexp;
+  std::vector<int64_t>& doff = h->doff;
+  std::vector<int32_t>& dexp = h->dexp;
   upload_dense(h, doff, dexp);
   // with many right-hand sides the streaming passes keep only the fp64
   // low-rank blocks; the tensor cores and mr.cu take the rest
+  // positions of one many-column phase-1 item (HH_TC_SPLIT_POSITIONS, a
+  // positive multiple of 16, overrides; hh_autotune may change it)
+  if (const char* e = std::getenv("HH_TC_SPLIT_POSITIONS")) {
+    const int v = std::atoi(e);
+    if (v >= 16 && v % 16 == 0) h->split_len = v;
+  }
   std::vector<char> all(H.lr.size(), 1), rest(H.lr.size(), 0);
   for (size_t b = 0; b < H.lr.size(); ++b) rest[b] = H.lr[b].fmt == hh::F64;
   for (int dir = 0; dir < 2; ++dir) {
@@ -903,6 +908,39 @@ int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, 
   return HH_OK;
 }
 
+// Rebuild the many-column tables (tensor-core and CUDA-core) with the
+// handle's current split length.
+void rebuild_many(hh_matrix* h) {
+  for (int d = 0; d < 2; ++d) {
+    cudaFree(h->tc[d].d_pieces);
+    cudaFree(h->tc[d].d_groups);
+    cudaFree(h->tc[d].d_tiles);
+    cudaFree(h->tc[d].d_entries);
+    cudaFree(h->mr[d].d_pieces);
+    cudaFree(h->mr[d].d_groups);
+    cudaFree(h->mr[d].d_tiles);
+    cudaFree(h->mr[d].d_entries);
+    cudaFree(h->mr[d].d_dpieces);
+    cudaFree(h->mr[d].d_dtiles);
+    cudaFree(h->mr[d].d_dentries);
+    h->tc[d] = TcSet();
+    h->mr[d] = MrSet();
+    build_tc_set(h, d, h->tc[d]);
+    build_mr_set(h, d, h->doff, h->dexp, h->mr[d]);
+  }
+}
+
+// Streaming grid of one direction and phase: c CTAs per SM (clamped to the
+// occupancy of each column count).
+void set_stream_grid(hh_matrix* h, int dir, int phase, int c) {
+  StreamSet& ss = h->ss[dir];
+  for (int nr : {1, 2, 4}) {
+    const int occ = hh::dev::stream_blocks_per_sm(phase, ss.fset, nr);
+    ss.grid[phase][nr] = h->sms * std::max(1, std::min(c, occ));
+  }
+  h->blocks_per_sm[dir][phase] = c;
+}
+
 hh_matrix* make_handle() { return new (std::nothrow) hh_matrix(); }
 
 int finish_construction(hh_matrix* h, int device, hh_handle* out) {
@@ -1060,6 +1098,10 @@ int hh_info(hh_handle h, hh_info_t* o) {
     }
   }
   for (const hh::DenseBlock& D : H.dense) o->dense_elems += D.m * D.n;
+  o->tuned = h->tuned;
+  o->split_positions = h->split_len;
+  for (int d = 0; d < 2; ++d)
+    for (int p = 1; p <= 2; ++p) o->blocks_per_sm[2 * d + p - 1] = h->blocks_per_sm[d][p];
   return HH_OK;
 }
 
@@ -1095,7 +1137,7 @@ int hh_matvec_ws(hh_handle h, int transpose, const double* in, double* out, int 
 
 // CUDA events around one product (n_ev = 5 for the streaming sequence, 9 for
 // the many-right-hand-side sequence); writes the n_ev - 1 intervals to ms.
-int timed_product(hh_handle h, int dir, const double* in, double* out, int nrhs, int64_t ld_in, int64_t ld_out,
+static int timed_product(hh_handle h, int dir, const double* in, double* out, int nrhs, int64_t ld_in, int64_t ld_out,
                   void* stream, float* ms, int n_ev, bool many) {
   int cur = -1;
   cudaGetDevice(&cur);
@@ -1130,6 +1172,89 @@ int hh_matvec_stages(hh_handle h, int transpose, const double* in, double* out, 
   if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data");
   if (nrhs < 1 || nrhs > hh::dev::kTcMaxRhs) return fail(HH_EINVAL, "nrhs must be between 1 and 128");
   return timed_product(h, transpose ? 1 : 0, in, out, nrhs, ld_in, ld_out, stream, ms, 9, true);
+}
+
+int hh_autotune(hh_handle h, int nrhs_many) {
+  if (!h) return fail(HH_EINVAL, "null handle");
+  if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data");
+  if (nrhs_many < 0 || nrhs_many > hh::dev::kTcMaxRhs) return fail(HH_EINVAL, "nrhs_many must be in [0, 128]");
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  const int64_t n = h->H.n;
+  const int cols = std::max(4, nrhs_many);
+  double* x = nullptr;
+  double* y = nullptr;
+  cudaStream_t st = nullptr;
+  int rc = HH_OK;
+  if (cudaMalloc(&x, sizeof(double) * n * cols) != cudaSuccess ||
+      cudaMalloc(&y, sizeof(double) * n * cols) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+    rc = fail(HH_ENOMEM, "cannot allocate autotuning buffers");
+  if (rc == HH_OK && cudaMemsetAsync(x, 0x3f, sizeof(double) * n * cols, st) != cudaSuccess)  // entries ~4.8e-4
+    rc = fail(HH_ECUDA, "cudaMemsetAsync failed");
+  float ms[8];
+  // streaming passes: CTAs per SM for each direction and phase, one column
+  for (int dir = 0; dir < 2 && rc == HH_OK; ++dir)
+    for (int phase = 1; phase <= 2 && rc == HH_OK; ++phase) {
+      const int occ = hh::dev::stream_blocks_per_sm(phase, h->ss[dir].fset, 1);
+      int best_c = occ;
+      float best = 1e30f;
+      for (int c = 1; c <= occ && rc == HH_OK; ++c) {
+        set_stream_grid(h, dir, phase, c);
+        float t = 1e30f;
+        for (int rep = 0; rep < 6 && rc == HH_OK; ++rep) {
+          rc = timed_product(h, dir, x, y, 1, n, n, st, ms, 5, false);
+          if (rep >= 1) t = std::min(t, ms[phase]);
+        }
+        if (t < best) {
+          best = t;
+          best_c = c;
+        }
+      }
+      set_stream_grid(h, dir, phase, best_c);
+    }
+  // many columns: the position split of the phase-1 items
+  if (rc == HH_OK && nrhs_many > 0) {
+    int best_s = h->split_len;
+    float best = 1e30f;
+    for (int split : {256, 512, 1024, 2048, 4096}) {
+      h->split_len = split;
+      try {
+        rebuild_many(h);
+      } catch (const std::exception& e) {
+        rc = fail(HH_ECUDA, e.what());
+        break;
+      }
+      float t = 1e30f;
+      for (int rep = 0; rep < 4 && rc == HH_OK; ++rep) {
+        rc = timed_product(h, 0, x, y, nrhs_many, n, n, st, ms, 9, true);
+        float sum = 0.f;
+        for (int k = 0; k < 8; ++k) sum += ms[k];
+        if (rep >= 1) t = std::min(t, sum);
+      }
+      if (rc != HH_OK) break;
+      if (t < best) {
+        best = t;
+        best_s = split;
+      }
+    }
+    h->split_len = best_s;
+    try {
+      rebuild_many(h);
+    } catch (const std::exception& e) {
+      if (rc == HH_OK) rc = fail(HH_ECUDA, e.what());
+    }
+  }
+  if (st) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  cudaFree(x);
+  cudaFree(y);
+  if (rc == HH_OK) h->tuned = 1;
+  if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+  return rc;
 }
 
 int hh_matvec_host(hh_handle h, int transpose, const double* x_host, double* y_host, int nrhs,

@@ -6,7 +6,7 @@
 //              outside the tensor-core path (fp32 blocks, and 16/8-bit blocks
 //              on clusters that do not start at multiples of 16): one CTA per
 //              (group of at most 64 ranks sharing the input cluster, range of
-//              at most 1,024 positions); a thread holds 4 ranks x RPT
+//              at most 1,024 positions); a thread holds 8 ranks x RPT
 //              right-hand sides.  Factors are upcast to fp32, the input is
 //              fp32 (relative 2^-24), products and sums are fp32 with round
 //              to nearest; split ranges add into T with atomics.
@@ -37,7 +37,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kK1 = 32;       // positions per phase-1 stage
-constexpr int kVStride = 36;  // floats per rank row of the phase-1 V stage (32 + 4)
 constexpr int kK2 = 16;       // ranks (dense: K columns) per phase-2 stage
 constexpr int kDenseRows = 64;
 
@@ -83,12 +82,15 @@ __device__ __forceinline__ void load_x(const float* row, int tc, float* x) {
 }
 
 // ------------------------------------------------------------------ phase 1
+constexpr int kP1Threads = 128;
+constexpr int kVRow = kMrRanks + 4;  // floats per position row of the V stage
+
 template <int RPT>
-__global__ void __launch_bounds__(kThreads) mr_phase1(MrArgs a) {
+__global__ void __launch_bounds__(kP1Threads) mr_phase1(MrArgs a) {
   constexpr int RP = 16 * RPT;
   extern __shared__ __align__(16) float sm1[];
-  float* sV = sm1;                               // [2][64][kVStride]
-  float* sX = sm1 + 2 * kMrRanks * kVStride;     // [2][kK1][RP]
+  float* sV = sm1;                        // [2][kK1][kVRow]: V transposed, position-major
+  float* sX = sm1 + 2 * kK1 * kVRow;      // [2][kK1][RP]
   __shared__ const uint8_t* colp[kMrRanks];
   __shared__ int rowpiece[kMrRanks];
   const TcGroup g = a.groups[blockIdx.x];
@@ -108,37 +110,51 @@ __global__ void __launch_bounds__(kThreads) mr_phase1(MrArgs a) {
   }
   __syncthreads();
   const int fmt = g.fmt, nst = (g.p1 - g.p0 + kK1 - 1) / kK1;
-  // loader roles: V rank vj, positions 8 vq .. 8 vq + 7 of the stage; X units
-  const int vj = tid >> 2, vq = tid & 3;
+  // loader roles: V rank vj, positions 16 vh .. 16 vh + 15 of the stage (a warp
+  // covers 32 consecutive ranks, so the transposed stores are conflict-free)
+  const int vj = tid & 63, vh = tid >> 6;
   const uint8_t* vcol = colp[vj];
-  constexpr int XU = kK1 * RP / 4 / kThreads;  // float4 units of X per thread
-  float vr[8];
+  constexpr int XU = kK1 * RP / 4 / kP1Threads;  // float4 units of X per thread
+  float vr[16];
   float4 xr[XU];
   auto load = [&](int i) {
-    const int P = g.p0 + kK1 * i;
-    const int pos = P + 8 * vq;
+    const int pos = g.p0 + kK1 * i + 16 * vh;
+    if (fmt == 1 && vcol && pos + 16 <= g.p1) {
+      const float4* src = reinterpret_cast<const float4*>(vcol) + (pos >> 2);
 #pragma unroll
-    for (int t = 0; t < 8; ++t) vr[t] = (vcol && pos + t < g.p1) ? load_elem(vcol, pos + t, fmt) : 0.f;
+      for (int t = 0; t < 4; ++t) {
+        const float4 f = __ldg(src + t);
+        vr[4 * t] = f.x;
+        vr[4 * t + 1] = f.y;
+        vr[4 * t + 2] = f.z;
+        vr[4 * t + 3] = f.w;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 16; ++t) vr[t] = (vcol && pos + t < g.p1) ? load_elem(vcol, pos + t, fmt) : 0.f;
+    }
+    const int P = g.p0 + kK1 * i;
 #pragma unroll
     for (int h = 0; h < XU; ++h) {
-      const int u = tid + h * kThreads, p = u / (RP / 4), c4 = u - p * (RP / 4);
+      const int u = tid + h * kP1Threads, p = u / (RP / 4), c4 = u - p * (RP / 4);
       xr[h] = *reinterpret_cast<const float4*>(a.xh + (static_cast<int64_t>(g.in_off) + P + p) * 128 + 4 * c4);
     }
   };
   auto store = [&](int buf) {
-    float* v = sV + (buf * kMrRanks + vj) * kVStride + 8 * vq;
-    *reinterpret_cast<float4*>(v) = make_float4(vr[0], vr[1], vr[2], vr[3]);
-    *reinterpret_cast<float4*>(v + 4) = make_float4(vr[4], vr[5], vr[6], vr[7]);
+    float* v = sV + (buf * kK1 + 16 * vh) * kVRow + vj;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t * kVRow] = vr[t];
 #pragma unroll
     for (int h = 0; h < XU; ++h) {
-      const int u = tid + h * kThreads, p = u / (RP / 4), c4 = u - p * (RP / 4);
+      const int u = tid + h * kP1Threads, p = u / (RP / 4), c4 = u - p * (RP / 4);
       *reinterpret_cast<float4*>(sX + (buf * kK1 + p) * RP + 4 * c4) = xr[h];
     }
   };
+  // thread tile: ranks 8 tr .. 8 tr + 7 (two float4 32 ranks apart), columns of tc
   const int tr = tid >> 4, tc = tid & 15;
-  float acc[4][RPT];
+  float acc[8][RPT];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int e = 0; e < RPT; ++e) acc[i][e] = 0.f;
   load(0);
@@ -147,28 +163,27 @@ __global__ void __launch_bounds__(kThreads) mr_phase1(MrArgs a) {
   for (int i = 0; i < nst; ++i) {
     const int buf = i & 1;
     if (i + 1 < nst) load(i + 1);
-    const float* V = sV + (buf * kMrRanks + 4 * tr) * kVStride;
+    const float* V = sV + buf * kK1 * kVRow + 4 * tr;
     const float* X = sX + buf * kK1 * RP;
-#pragma unroll 8
+#pragma unroll 4
     for (int p = 0; p < kK1; ++p) {
       float x[RPT];
       load_x<RPT>(X + p * RP, tc, x);
-      const float v0 = V[p], v1 = V[kVStride + p], v2 = V[2 * kVStride + p], v3 = V[3 * kVStride + p];
+      const float4 va = *reinterpret_cast<const float4*>(V + p * kVRow);
+      const float4 vb = *reinterpret_cast<const float4*>(V + p * kVRow + 32);
+      const float v[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
 #pragma unroll
-      for (int e = 0; e < RPT; ++e) {
-        acc[0][e] = fmaf(v0, x[e], acc[0][e]);
-        acc[1][e] = fmaf(v1, x[e], acc[1][e]);
-        acc[2][e] = fmaf(v2, x[e], acc[2][e]);
-        acc[3][e] = fmaf(v3, x[e], acc[3][e]);
-      }
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int e = 0; e < RPT; ++e) acc[r][e] = fmaf(v[r], x[e], acc[r][e]);
     }
     if (i + 1 < nst) store(buf ^ 1);
     __syncthreads();
   }
   // T = 2^e D, rank-major [rank][128] per piece
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int rank = 4 * tr + i;
+  for (int r = 0; r < 8; ++r) {
+    const int rank = (r < 4 ? 4 * tr + r : 32 + 4 * tr + r - 4);
     const int pi = rowpiece[rank];
     if (pi < 0) continue;
     const TcPiece& q = a.pieces[pi];
@@ -177,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) mr_phase1(MrArgs a) {
     float* t = a.t32 + q.toff + static_cast<int64_t>(rl) * 128;
 #pragma unroll
     for (int e = 0; e < RPT; ++e) {
-      const float v = ldexpf(acc[i][e], q.e);
+      const float v = ldexpf(acc[r][e], q.e);
       if (g.nsplit > 1)
         atomicAdd(t + rhs_col<RPT>(tc, e), v);
       else
@@ -217,7 +232,7 @@ struct Cur {
 };
 
 template <int RPT>
-__global__ void __launch_bounds__(kThreads) mr_phase2(MrArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) mr_phase2(MrArgs a) {
   constexpr int RP = 16 * RPT;
   extern __shared__ __align__(16) float sm2[];
   float* sU = sm2;                      // [2][kK2][128]
@@ -460,9 +475,9 @@ template <int RPT>
 cudaError_t launch_rpt(int kind, const MrArgs& a, cudaStream_t st) {
   constexpr int RP = 16 * RPT;
   if (kind == 1) {
-    const size_t smem = sizeof(float) * (2 * kMrRanks * kVStride + 2 * kK1 * RP);
+    const size_t smem = sizeof(float) * (2 * kK1 * kVRow + 2 * kK1 * RP);
     cudaError_t e = cudaFuncSetAttribute(mr_phase1<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) mr_phase1<RPT><<<a.n_groups, kThreads, smem, st>>>(a);
+    if (e == cudaSuccess) mr_phase1<RPT><<<a.n_groups, kP1Threads, smem, st>>>(a);
   } else if (kind == 2) {
     const size_t smem = sizeof(float) * std::max(2 * kK2 * (kMrRows + RP), kMrRows * (std::min(RP, 64) + 1));
     cudaError_t e = cudaFuncSetAttribute(mr_phase2<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

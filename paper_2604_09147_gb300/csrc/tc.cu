@@ -396,9 +396,35 @@ __global__ void __launch_bounds__(kThreads, 2) tc_phase1(TcArgs a) {
 }
 
 // ------------------------------------------------------------------ phase 2
+// position in a tile's list of (entry, K step), with the current entry and
+// the fields of its piece held in registers (reloaded when the entry changes)
 struct Cursor {
   int e, step;
+  TcEntry en;
+  const uint8_t* f2;
+  int64_t ld2, toff;
+  int k, steps, fmt;
 };
+
+__device__ __forceinline__ void cursor_load(Cursor& c, const TcArgs& a, const TcTile& tl) {
+  if (c.e >= tl.count) return;
+  c.en = a.entries[tl.first + c.e];
+  const TcPiece& q = a.pieces[c.en.piece];
+  c.f2 = q.f2;
+  c.ld2 = q.ld2;
+  c.toff = q.toff;
+  c.k = q.k;
+  c.steps = q.kp >> 4;
+  c.fmt = q.fmt;
+}
+
+__device__ __forceinline__ void cursor_advance(Cursor& c, const TcArgs& a, const TcTile& tl) {
+  if (++c.step == c.steps) {
+    c.step = 0;
+    ++c.e;
+    cursor_load(c, a, tl);
+  }
+}
 
 __global__ void __launch_bounds__(kThreads, 2) tc_phase2(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -411,34 +437,30 @@ __global__ void __launch_bounds__(kThreads, 2) tc_phase2(TcArgs a) {
   for (int e = 0; e < tl.count; ++e) nst += a.pieces[a.entries[tl.first + e].piece].kp >> 4;
   const uint32_t idesc = idesc_bf16(rp);
 
-  auto advance = [&](Cursor& c) {
-    if (++c.step == (a.pieces[a.entries[tl.first + c.e].piece].kp >> 4)) {
-      c.step = 0;
-      ++c.e;
-    }
-  };
-  Cursor ld{0, 0}, cv{0, 0};
+  Cursor ld{}, cv{}, mc{};
+  cursor_load(ld, a, tl);
+  cv = ld;
+  mc = ld;
   // copies of stage i: the T slices (straight into the operand) and the raw
   // factor rows [src, src + nrows) of the 16 ranks of the K step, laid out
   // [rank][tile row]; thread = (rank, 16-byte piece of the rows)
   auto issue_loads = [&](int i) {
     if (i < nst) {
-      const TcEntry en = a.entries[tl.first + ld.e];
-      const TcPiece& q = a.pieces[en.piece];
+      const TcEntry& en = ld.en;
       uint8_t* st = base + (i % kDepth) * kP2Stage;
-      const uint8_t* tsrc = a.timg + q.toff + static_cast<int64_t>(ld.step) * 4096;
+      const uint8_t* tsrc = a.timg + ld.toff + static_cast<int64_t>(ld.step) * 4096;
       const int tunits = rp * 2;
       for (int u = tid; u < 2 * tunits; u += kThreads) {
         const int sl = u >= tunits, w = u - sl * tunits;
-        cp16(st + kP2Raw + kP2UOp + sl * 4096 + w * 16, tsrc + static_cast<int64_t>(sl) * (q.kp >> 4) * 4096 + w * 16);
+        cp16(st + kP2Raw + kP2UOp + sl * 4096 + w * 16, tsrc + static_cast<int64_t>(sl) * ld.steps * 4096 + w * 16);
       }
-      const int sz = fmt_size(q.fmt), per = 16 / sz;  // rows per 16-byte piece
-      const int pieces = kTcRows / per;                 // pieces per rank row of the tile
+      const int sz = fmt_size(ld.fmt), per = 16 / sz;  // rows per 16-byte piece
+      const int pieces = kTcRows / per;                  // pieces per rank row of the tile
       const int j = tid / pieces, c = tid - j * pieces, m0 = c * per;
       const int jj = 16 * ld.step + j;
-      if (j < 16 && jj < q.k && m0 >= en.dst && m0 < en.dst + en.nrows)
-        cp16(st + j * (kTcRows * sz) + m0 * sz, q.f2 + (static_cast<int64_t>(jj) * q.ld2 + en.src + (m0 - en.dst)) * sz);
-      advance(ld);
+      if (j < 16 && jj < ld.k && m0 >= en.dst && m0 < en.dst + en.nrows)
+        cp16(st + j * (kTcRows * sz) + m0 * sz, ld.f2 + (static_cast<int64_t>(jj) * ld.ld2 + en.src + (m0 - en.dst)) * sz);
+      cursor_advance(ld, a, tl);
     }
     cp_commit();
   };
@@ -446,10 +468,9 @@ __global__ void __launch_bounds__(kThreads, 2) tc_phase2(TcArgs a) {
   // or the masked tail (every thread's copies of the stage have landed)
   auto convert = [&](int i) {
     if (i >= nst) return;
-    const TcEntry en = a.entries[tl.first + cv.e];
-    const TcPiece& q = a.pieces[en.piece];
+    const TcEntry& en = cv.en;
     uint8_t* st = base + (i % kDepth) * kP2Stage;
-    const int m = tid >> 1, uo = tid & 1, sz = fmt_size(q.fmt);
+    const int m = tid >> 1, uo = tid & 1, sz = fmt_size(cv.fmt);
     const bool in = m >= en.dst && m < en.dst + en.nrows;
     const int j0 = 16 * cv.step + 8 * uo;
     float v[8];
@@ -457,19 +478,18 @@ __global__ void __launch_bounds__(kThreads, 2) tc_phase2(TcArgs a) {
     for (int t = 0; t < 8; ++t) {
       const uint8_t* src = st + (8 * uo + t) * (kTcRows * sz) + m * sz;
       float x = 0.f;
-      if (in && j0 + t < q.k)
-        x = q.fmt == kE4M3 ? e4m3_to_float(*src) : f16_or_bf16(*reinterpret_cast<const uint16_t*>(src), q.fmt);
+      if (in && j0 + t < cv.k)
+        x = cv.fmt == kE4M3 ? e4m3_to_float(*src) : f16_or_bf16(*reinterpret_cast<const uint16_t*>(src), cv.fmt);
       v[t] = x;
     }
-    store_slices(v, factor_slices(q.fmt), st + kP2Raw + core_off(m, uo), kTcRows * 32);
-    advance(cv);
+    store_slices(v, factor_slices(cv.fmt), st + kP2Raw + core_off(m, uo), kTcRows * 32);
+    cursor_advance(cv, a, tl);
   };
 
   for (int i = 0; i < kDepth - 1; ++i) issue_loads(i);
   cp_wait<kDepth - 2>();
   __syncthreads();
   convert(0);
-  Cursor mc{0, 0};
   bool ok = true;
   int ini_hi = 0, ini_lo = 0;  // meaningful in thread 0
   for (int i = 0; i < nst; ++i) {
@@ -482,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_phase2(TcArgs a) {
       break;
     }
     if (tid == 0) {
-      const int np = n_products(a.pieces[a.entries[tl.first + mc.e].piece].fmt);
+      const int np = n_products(mc.fmt);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       for (int p = 0; p < np; ++p) {
         const uint64_t da = op_desc(st + kP2Raw + pf(p) * (kTcRows * 32));
@@ -493,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_phase2(TcArgs a) {
       }
       mma_commit(&ctl->bar[s]);
     }
-    advance(mc);
+    cursor_advance(mc, a, tl);
     if (i >= 1 && i + kDepth - 1 < nst && !bar_wait(&ctl->bar[(i - 1) % kDepth], ((i - 1) / kDepth) & 1))
       ok = false;
     issue_loads(i + kDepth - 1);

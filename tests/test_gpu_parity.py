@@ -249,3 +249,23 @@ def test_batch_fp64_matrices_match_at_1e12(P, tmp_path):
         a, b = B.offsets[i], B.offsets[i + 1]
         assert rel(y[a:b], M.matvec(O, xs[i])) <= TOL64
     B.close()
+
+
+def test_autotune_keeps_results(P):
+    """hh_autotune changes launch parameters only: the products before and
+    after agree up to rounding, and the choices are reported."""
+    H = P.HMatrix.build(W.points(6000, 3, 9500), kernel=W.GAUSS, kernel_param=0.05, leaf_size=64, eta=1.0,
+                        switch_level=-1, tol=1e-5, fmt_mask=ALL, device=0)
+    x1 = gpu(W.rhs(6000, 1, "uniform", 9501)[:, 0])
+    xm = gpu(np.ascontiguousarray(W.rhs(6000, 40, "normal", 9502).T)).t()
+    before = [H.matvec(x1).cpu().numpy(), H.matvec(x1, transpose=True).cpu().numpy(), H.matvec(xm).cpu().numpy()]
+    info0 = H.info()
+    assert info0["tuned"] == 0 and info0["split_positions"] == 1024
+    choice = H.autotune(40)
+    info = H.info()
+    assert info["tuned"] == 1 and choice["split_positions"] in (256, 512, 1024, 2048, 4096)
+    assert all(1 <= c <= 16 for c in choice["blocks_per_sm"])
+    after = [H.matvec(x1).cpu().numpy(), H.matvec(x1, transpose=True).cpu().numpy(), H.matvec(xm).cpu().numpy()]
+    H.sync_status()
+    for a, b in zip(before, after):
+        assert rel(b, a) <= 1e-6

@@ -280,7 +280,7 @@ def run_ours(args):
     xh0 = W.config_rhs("adaptive_65k", n=n)[:, 0]
     x = torch.from_numpy(xh0.copy()).cuda()
     y = torch.empty_like(x)
-    tuned = {"adaptive": Ham.autotune(0), "fp64": H64.autotune(0)}
+    tuned = None if args.no_autotune else {"adaptive": Ham.autotune(0), "fp64": H64.autotune(0)}
     inf, inf64 = Ham.info(), H64.info()
     for _ in range(args.warmup):
         Ham.matvec(x, out=y)
@@ -398,7 +398,7 @@ def run_many(args):
     X0 = W.config_rhs("multirhs_262k", nrhs=R, n=n)            # (n, R) column-major
     x = torch.from_numpy(np.ascontiguousarray(X0.T)).cuda().t()  # device, column-major
     y = torch.empty((R, n), dtype=torch.float64, device="cuda").t()
-    tuned = H.autotune(R)
+    tuned = None if args.no_autotune else H.autotune(R)
     inf = H.info()
     for _ in range(args.warmup):
         H.matvec(x, out=y)
@@ -625,6 +625,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU oracle baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nrhs", type=int, default=128, help="right-hand sides per product (multirhs workloads)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch parameters (for profiling runs with a fixed launch sequence)")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-nmin", type=int, default=2048)
     ap.add_argument("--batch-nmax", type=int, default=131072)

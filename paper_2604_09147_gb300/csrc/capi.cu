@@ -55,12 +55,14 @@ struct StreamSet {
 };
 
 // Work tables of the tensor-core path (tc.cu) for one direction.
+// Groups and tiles come in two variants: [0] fp16/bf16/e4m3 pieces, [1] fp32
+// pieces (the kernels with per-stage draining, tc.cu).
 struct TcSet {
   hh::dev::TcPiece* d_pieces = nullptr;
-  hh::dev::TcGroup* d_groups = nullptr;
-  hh::dev::TcTile* d_tiles = nullptr;
-  hh::dev::TcEntry* d_entries = nullptr;
-  int n_pieces = 0, n_groups = 0, n_tiles = 0;
+  hh::dev::TcGroup* d_groups[2] = {nullptr, nullptr};
+  hh::dev::TcTile* d_tiles[2] = {nullptr, nullptr};
+  hh::dev::TcEntry* d_entries[2] = {nullptr, nullptr};
+  int n_pieces = 0, n_groups[2] = {0, 0}, n_tiles[2] = {0, 0};
   int64_t t_bytes = 0;                  // T images of all pieces
   int64_t part_floats = 0;              // partial sums of the split groups
   int n_cnt = 0;                        // split groups (arrival counters)
@@ -127,9 +129,11 @@ void free_device(hh_matrix* h) {
       cudaFree(h->ss_rest[d].d_items[p]);
     }
     cudaFree(h->tc[d].d_pieces);
-    cudaFree(h->tc[d].d_groups);
-    cudaFree(h->tc[d].d_tiles);
-    cudaFree(h->tc[d].d_entries);
+    for (int v = 0; v < 2; ++v) {
+      cudaFree(h->tc[d].d_groups[v]);
+      cudaFree(h->tc[d].d_tiles[v]);
+      cudaFree(h->tc[d].d_entries[v]);
+    }
     cudaFree(h->mr[d].d_pieces);
     cudaFree(h->mr[d].d_groups);
     cudaFree(h->mr[d].d_tiles);
@@ -295,12 +299,13 @@ void build_stream_set(hh_matrix* h, int dir, const std::vector<int64_t>& toff, c
 }
 
 // Formats the tensor-core path takes and the most ranks of one piece.
-// fp32 blocks stay on the streaming passes: the tensor core's truncating
-// accumulation is accurate to about 2^-17 of a block's product, below the unit
-// roundoff of the 16- and 8-bit formats but not of fp32.
-bool tc_format(int fmt) { return fmt == hh::F16 || fmt == hh::BF16 || fmt == hh::E4M3; }
+// fp32 blocks take the variant that drains tensor memory into fp32 registers
+// every stage (the tensor core's accumulation truncates; over a whole
+// contraction that costs about 2^-17 of a block's product, far below the unit
+// roundoff of the 16- and 8-bit formats but not of fp32).
+bool tc_format(int fmt) { return fmt == hh::F32 || fmt == hh::F16 || fmt == hh::BF16 || fmt == hh::E4M3; }
 int tc_piece_cap(int) { return hh::dev::kTcGroupRanks; }
-int tc_input_slices(int) { return 2; }
+int tc_input_slices(int fmt) { return fmt == hh::F32 ? 3 : 2; }
 
 // A block goes to the tensor cores when its format is one they take and both
 // of its clusters start at a tree position that is a multiple of 16 (the
@@ -404,49 +409,54 @@ void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
     i = j;
   }
   std::stable_sort(groups.begin(), groups.end(), [](const CGroup& x, const CGroup& y) { return x.cost > y.cost; });
-  // phase-2 tiles
+  // phase-2 tiles, per variant (the entries of fp32 pieces and of the others)
   const int64_t ntiles = (H.n + kTcRows - 1) / kTcRows;
-  std::vector<std::vector<TcEntry>> per_tile(static_cast<size_t>(ntiles));
+  std::vector<std::vector<TcEntry>> per_tile[2];
+  for (int v = 0; v < 2; ++v) per_tile[v].resize(static_cast<size_t>(ntiles));
   for (size_t pi = 0; pi < pieces.size(); ++pi) {
     const TcPiece& q = pieces[pi];
+    const int v = q.fmt == hh::F32;
     const int64_t lo = q.out_off, hi = int64_t(q.out_off) + q.rows2;
     for (int64_t t = lo / kTcRows; t * kTcRows < hi; ++t) {
       const int64_t r0 = t * kTcRows, a = std::max(lo, r0), b = std::min(hi, r0 + kTcRows);
-      per_tile[t].push_back(TcEntry{(int32_t)pi, (int32_t)(a - lo), (int32_t)(a - r0), (int32_t)(b - a)});
+      per_tile[v][t].push_back(TcEntry{(int32_t)pi, (int32_t)(a - lo), (int32_t)(a - r0), (int32_t)(b - a)});
     }
   }
-  struct CTile {
-    TcTile t;
-    double cost;
-  };
-  std::vector<CTile> tiles;
-  std::vector<TcEntry> entries;
-  for (int64_t t = 0; t < ntiles; ++t) {
-    if (per_tile[t].empty()) continue;
-    TcTile tl;
-    tl.row0 = (int32_t)(t * kTcRows);
-    tl.rows = (int32_t)std::min<int64_t>(kTcRows, H.n - t * kTcRows);
-    tl.first = (int32_t)entries.size();
-    tl.count = (int32_t)per_tile[t].size();
-    double cost = 0;
-    for (const TcEntry& e : per_tile[t]) {
-      entries.push_back(e);
-      cost += double(pieces[e.piece].kp) * (kTcRows * hh::fmt_bytes(pieces[e.piece].fmt) + 4096.0);
-    }
-    tiles.push_back({tl, cost});
-  }
-  std::stable_sort(tiles.begin(), tiles.end(), [](const CTile& x, const CTile& y) { return x.cost > y.cost; });
-  std::vector<TcGroup> gflat;
-  for (auto& g : groups) gflat.push_back(g.g);
-  std::vector<TcTile> tflat;
-  for (auto& t : tiles) tflat.push_back(t.t);
   out.d_pieces = upload(pieces);
-  out.d_groups = upload(gflat);
-  out.d_tiles = upload(tflat);
-  out.d_entries = upload(entries);
   out.n_pieces = (int)pieces.size();
-  out.n_groups = (int)gflat.size();
-  out.n_tiles = (int)tflat.size();
+  for (int v = 0; v < 2; ++v) {
+    struct CTile {
+      TcTile t;
+      double cost;
+    };
+    std::vector<CTile> tiles;
+    std::vector<TcEntry> entries;
+    for (int64_t t = 0; t < ntiles; ++t) {
+      if (per_tile[v][t].empty()) continue;
+      TcTile tl;
+      tl.row0 = (int32_t)(t * kTcRows);
+      tl.rows = (int32_t)std::min<int64_t>(kTcRows, H.n - t * kTcRows);
+      tl.first = (int32_t)entries.size();
+      tl.count = (int32_t)per_tile[v][t].size();
+      double cost = 0;
+      for (const TcEntry& e : per_tile[v][t]) {
+        entries.push_back(e);
+        cost += double(pieces[e.piece].kp) * (kTcRows * hh::fmt_bytes(pieces[e.piece].fmt) + 4096.0);
+      }
+      tiles.push_back({tl, cost});
+    }
+    std::stable_sort(tiles.begin(), tiles.end(), [](const CTile& x, const CTile& y) { return x.cost > y.cost; });
+    std::vector<TcGroup> gflat;
+    for (auto& g : groups)
+      if ((g.g.fmt == hh::F32) == (v == 1)) gflat.push_back(g.g);
+    std::vector<TcTile> tflat;
+    for (auto& t : tiles) tflat.push_back(t.t);
+    out.d_groups[v] = upload(gflat);
+    out.d_tiles[v] = upload(tflat);
+    out.d_entries[v] = upload(entries);
+    out.n_groups[v] = (int)gflat.size();
+    out.n_tiles[v] = (int)tflat.size();
+  }
   out.t_bytes = toff;
 }
 
@@ -741,7 +751,7 @@ size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
   };
   const int64_t pf = std::max(h->tc[0].part_floats, h->tc[1].part_floats);
   const int nc = std::max(h->tc[0].n_cnt, h->tc[1].n_cnt);
-  uint8_t* ximg = (uint8_t*)take(size_t(2) * nblk * 4096);
+  uint8_t* ximg = (uint8_t*)take(size_t(3) * nblk * 4096);  // three bf16 slices
   uint8_t* timg = (uint8_t*)take(std::max<size_t>(256, size_t(tb)));
   float* part = (float*)take(sizeof(float) * std::max<int64_t>(64, pf));
   int* cnt = (int*)take(sizeof(int) * std::max(64, nc));
@@ -785,11 +795,11 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   hh::dev::TcArgs a;
   std::memset(&a, 0, sizeof(a));
   a.pieces = ts.d_pieces;
-  a.groups = ts.d_groups;
-  a.tiles = ts.d_tiles;
-  a.entries = ts.d_entries;
-  a.n_groups = ts.n_groups;
-  a.n_tiles = ts.n_tiles;
+  a.groups = ts.d_groups[0];
+  a.tiles = ts.d_tiles[0];
+  a.entries = ts.d_entries[0];
+  a.n_groups = ts.n_groups[0];
+  a.n_tiles = ts.n_tiles[0];
   a.nr = nr;
   a.rp = (nr + 15) / 16 * 16;
   a.ximg = t.ximg;
@@ -823,15 +833,23 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   md.entries = ms.d_dentries;
   md.n_groups = 0;
   md.n_tiles = ms.n_dtiles;
+  hh::dev::TcArgs a32 = a;  // the fp32 pieces
+  a32.groups = ts.d_groups[1];
+  a32.tiles = ts.d_tiles[1];
+  a32.entries = ts.d_entries[1];
+  a32.n_groups = ts.n_groups[1];
+  a32.n_tiles = ts.n_tiles[1];
   mark(2);
   if (e == cudaSuccess) e = hh::dev::launch_mr(1, m, st);
   mark(3);
+  if (e == cudaSuccess) e = hh::dev::launch_tc(1, a32, st, true);
   if (e == cudaSuccess) e = hh::dev::launch_tc(1, a, st);
   mark(4);
   if (e == cudaSuccess) e = hh::dev::launch_mr(2, m, st);
   mark(5);
   if (e == cudaSuccess) e = hh::dev::launch_mr(3, md, st);
   mark(6);
+  if (e == cudaSuccess) e = hh::dev::launch_tc(2, a32, st, true);
   if (e == cudaSuccess) e = hh::dev::launch_tc(2, a, st);
   mark(7);
   if (e == cudaSuccess) e = hh::dev::launch_finish(t.acc, nr, h->d_perm, h->H.n, h->npad, out, ld_out, st);
@@ -913,9 +931,11 @@ int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, 
 void rebuild_many(hh_matrix* h) {
   for (int d = 0; d < 2; ++d) {
     cudaFree(h->tc[d].d_pieces);
-    cudaFree(h->tc[d].d_groups);
-    cudaFree(h->tc[d].d_tiles);
-    cudaFree(h->tc[d].d_entries);
+    for (int v = 0; v < 2; ++v) {
+      cudaFree(h->tc[d].d_groups[v]);
+      cudaFree(h->tc[d].d_tiles[v]);
+      cudaFree(h->tc[d].d_entries[v]);
+    }
     cudaFree(h->mr[d].d_pieces);
     cudaFree(h->mr[d].d_groups);
     cudaFree(h->mr[d].d_tiles);

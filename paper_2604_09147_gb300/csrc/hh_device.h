@@ -76,8 +76,8 @@ cudaError_t launch_batch_finish(const double* acc, const int64_t* xofs, const in
                                 const int64_t* ns, int count, int64_t np, double* y, cudaStream_t st);
 
 // ---- tensor-core path for many right-hand sides (tc.cu) ----
-// A piece: ranks [r0, r0 + k) of one low-rank block stored in fp16, bf16 or
-// e4m3.  f1 / f2 point at the piece's first rank column of the phase-1
+// A piece: ranks [r0, r0 + k) of one low-rank block stored in fp32, fp16, bf16
+// or e4m3.  f1 / f2 point at the piece's first rank column of the phase-1
 // factor (V forward, U transpose) and the phase-2 factor; rows1 / rows2 are
 // the sizes of the input / output clusters, which start at tree positions
 // in_off / out_off (both multiples of 16).
@@ -121,7 +121,7 @@ struct TcArgs {
   const TcEntry* entries;
   int32_t n_groups, n_tiles;
   int32_t nr, rp;        // right-hand sides of this launch (<= 128), nr rounded up to 16
-  const uint8_t* ximg;   // input image [2][nblk][128 rows x 32 B] (tc prep)
+  const uint8_t* ximg;   // input image [3][nblk][128 rows x 32 B] (tc prep)
   int64_t nblk;
   uint8_t* timg;         // T images of the pieces
   float* part;           // partial sums of split groups
@@ -137,7 +137,8 @@ constexpr int kTcGroupRanks = 128;      // ranks of one phase-1 group
 constexpr int kTcSplitPositions = 1024; // positions of one phase-1 item
 cudaError_t launch_tc_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t nblk,
                            uint8_t* ximg, double* acc, int64_t npad, int* cnt, int n_cnt, cudaStream_t st);
-cudaError_t launch_tc(int phase, const TcArgs& a, cudaStream_t st);
+// f32: the kernels for fp32 pieces (groups / tiles of fp32 pieces only)
+cudaError_t launch_tc(int phase, const TcArgs& a, cudaStream_t st, bool f32 = false);
 size_t tc_smem_bytes(int phase);
 
 // ---- CUDA-core products for many right-hand sides (mr.cu) ----

@@ -189,7 +189,7 @@ __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
   return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 127) & ~static_cast<uintptr_t>(127));
 }
 
-__device__ __forceinline__ void tc_begin(Ctl* c) {
+__device__ __forceinline__ void tc_begin(Ctl* c, uint32_t cols = kTmemCols) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < kDepth; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&c->bar[s])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -198,7 +198,7 @@ __device__ __forceinline__ void tc_begin(Ctl* c) {
   }
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&c->tmem)),
-                 "r"(kTmemCols));
+                 "r"(cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -206,24 +206,43 @@ __device__ __forceinline__ void tc_begin(Ctl* c) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tc_end(Ctl* c) {
+__device__ __forceinline__ void tc_end(Ctl* c, uint32_t cols = kTmemCols) {
   cp_wait<0>();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (threadIdx.x < 32)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c->tmem), "r"(kTmemCols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c->tmem), "r"(cols));
 }
 
 // T = 2^e D of 16 ranks of one right-hand side, as the two slices of the
 // phase-2 operand image of its piece
+// exact split of an fp32 value into three bf16 slices
+__device__ __forceinline__ void store_slices3(const float* v, uint8_t* dst, int64_t sstride) {
+  __align__(16) __nv_bfloat16 s[3][8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    s[0][t] = __float2bfloat16_rn(v[t]);
+    const float r1 = v[t] - __bfloat162float(s[0][t]);
+    s[1][t] = __float2bfloat16_rn(r1);
+    s[2][t] = __float2bfloat16_rn(r1 - __bfloat162float(s[1][t]));
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) *reinterpret_cast<uint4*>(dst + k * sstride) = *reinterpret_cast<const uint4*>(s[k]);
+}
+
 __device__ __forceinline__ void write_t(const TcArgs& a, const TcPiece& q, int cb16, int r, float* v) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = ldexpf(v[j], q.e);
   const int step = (cb16 - q.col) >> 4;
   uint8_t* dst = a.timg + q.toff + static_cast<int64_t>(step) * 4096 + core_off(r, 0);
   const int64_t sstride = static_cast<int64_t>(q.kp >> 4) * 4096;
-  store_slices(v, 2, dst, sstride);
-  store_slices(v + 8, 2, dst + 128, sstride);
+  if (q.fmt == 1) {  // fp32 pieces: three slices
+    store_slices3(v, dst, sstride);
+    store_slices3(v + 8, dst + 128, sstride);
+  } else {
+    store_slices(v, 2, dst, sstride);
+    store_slices(v + 8, 2, dst + 128, sstride);
+  }
 }
 
 // ------------------------------------------------------------------ phase 1
@@ -554,7 +573,309 @@ __global__ void __launch_bounds__(kThreads, 2) tc_phase2(TcArgs a) {
   tc_end(ctl);
 }
 
-// X (caller's order, column-major, ld) -> tree order, fp32, two bf16 slices in
+// ------------------------------------------------------------------ fp32 blocks
+// fp32 factors and inputs as three exact bf16 slices, six products (slice
+// indices summing to at most 2).  Every stage's MMAs start a fresh pair of
+// accumulators (main product, corrections) in one of two tensor-memory banks,
+// and the threads add the finished bank into fp32 registers (round to
+// nearest) while the next stage's MMAs fill the other bank: the tensor core's
+// truncating accumulation then acts once per 16-term stage instead of
+// growing with the length of the contraction, which keeps fp32 accuracy.
+// 160 KB of shared memory and 512 tensor-memory columns: one CTA per SM.
+constexpr int kF1XOp = 3 * 4096;                   // X slices [3][128 rows x 32 B]
+constexpr int kF1VOp = 3 * kTcGroupRanks * 32;     // V slices [3][nk rows x 32 B]
+constexpr int kF1Raw = kTcGroupRanks * 64;         // raw fp32 V [nk ranks][16 positions]
+constexpr int kF1Stage = kF1XOp + kF1VOp + kF1Raw;
+constexpr int kF2Raw = 16 * kTcRows * 4;           // raw fp32 U [16 ranks][128 rows]
+constexpr int kF2UOp = 3 * kTcRows * 32;           // U slices [3][128 rows x 32 B]
+constexpr int kF2TOp = 3 * 128 * 32;               // T slices [3][rp rows x 32 B]
+constexpr int kF2Stage = kF2Raw + kF2UOp + kF2TOp;
+constexpr uint32_t kFTmemCols = 512;               // bank b: main at 256 b, corrections at 256 b + 128
+// products: factor slice fpf(p) times input slice fpx(p): (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+__device__ __forceinline__ int fpf(int p) { return (0x210100 >> (4 * p)) & 0xf; }
+__device__ __forceinline__ int fpx(int p) { return (0x012010 >> (4 * p)) & 0xf; }
+
+// add a finished bank (this thread's lane, 64 columns from col0) into acc
+__device__ __forceinline__ void drain_bank(const Ctl* ctl, int bank, int col0, int ncols, float* acc) {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int w = threadIdx.x >> 5;
+  const uint32_t t = ctl->tmem + (static_cast<uint32_t>(32 * (w & 3)) << 16) + 256 * bank;
+#pragma unroll
+  for (int cb = 0; cb < 4; ++cb) {
+    if (col0 + 16 * cb < ncols) {
+      float hi[16], lo[16];
+      tmem_ld16(t + col0 + 16 * cb, hi);
+      tmem_ld16(t + 128 + col0 + 16 * cb, lo);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[16 * cb + j] += hi[j] + lo[j];
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1) tc_phase1_f32(TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align128(smem_raw);
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + kDepth * kF1Stage);
+  const uint8_t** colp = reinterpret_cast<const uint8_t**>(ctl + 1);
+  int* rowpiece = reinterpret_cast<int*>(colp + kTcGroupRanks);
+  const TcGroup g = a.groups[blockIdx.x];
+  const int tid = threadIdx.x;
+  if (tid < g.count) {
+    const TcPiece& q = a.pieces[g.first + tid];
+    for (int j = 0; j < q.kp; ++j) {
+      rowpiece[q.col + j] = g.first + tid;
+      colp[q.col + j] = j < q.k ? q.f1 + static_cast<int64_t>(j) * q.ld1 * 4 : nullptr;
+    }
+  }
+  tc_begin(ctl, kFTmemCols);
+  const int nk = g.nk;
+  const int nst = (g.p1 - g.p0 + 15) >> 4;
+  const uint32_t idesc = idesc_bf16(nk);
+  // this thread's factor unit: rank vj, positions 8 vc .. 8 vc + 7 of the stage
+  const int vj = tid >> 1, vc = tid & 1;
+  const bool vown = vj < nk;
+  const uint8_t* vcol = vown ? colp[vj] : nullptr;
+  const int w = tid >> 5, col0 = 64 * (w >> 2);
+  float acc[64];
+#pragma unroll
+  for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+
+  auto issue_loads = [&](int i) {
+    if (i < nst) {
+      uint8_t* st = base + (i % kDepth) * kF1Stage;
+      const int p = g.p0 + 16 * i;
+      const int64_t blk = (static_cast<int64_t>(g.in_off) + p) >> 4;
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl)
+        cp16(st + sl * 4096 + tid * 16, a.ximg + ((static_cast<int64_t>(sl) * a.nblk + blk) << 12) + tid * 16);
+      if (vcol) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int pos = p + 8 * vc + 4 * h;
+          if (pos < g.p1) cp16(st + kF1XOp + kF1VOp + vj * 64 + vc * 32 + h * 16, vcol + 4 * pos);
+        }
+      }
+    }
+    cp_commit();
+  };
+  auto convert = [&](int i) {
+    if (!vown) return;
+    uint8_t* st = base + (i % kDepth) * kF1Stage;
+    const int pos = g.p0 + 16 * i + 8 * vc;
+    const float* raw = reinterpret_cast<const float*>(st + kF1XOp + kF1VOp + vj * 64 + vc * 32);
+    float v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = (vcol && pos + t < g.p1) ? raw[t] : 0.f;
+    store_slices3(v, st + kF1XOp + core_off(vj, vc), nk * 32);
+  };
+
+  for (int i = 0; i < kDepth - 1; ++i) issue_loads(i);
+  bool ok = true;
+  for (int i = 0; i < nst; ++i) {
+    const int s = i % kDepth;
+    uint8_t* st = base + s * kF1Stage;
+    cp_wait<kDepth - 2>();
+    convert(i);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t tb = ctl->tmem + 256 * (i & 1);
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        const uint64_t da = op_desc(st + fpx(p) * 4096);
+        const uint64_t db = op_desc(st + kF1XOp + fpf(p) * (nk * 32));
+        mma(tb + (p ? 128 : 0), da, db, idesc, p >= 2 ? 1u : 0u);
+      }
+      mma_commit(&ctl->bar[s]);
+    }
+    if (i >= 1) {
+      if (bar_wait(&ctl->bar[(i - 1) % kDepth], ((i - 1) / kDepth) & 1))
+        drain_bank(ctl, (i - 1) & 1, col0, nk, acc);
+      else
+        ok = false;
+    }
+    issue_loads(i + kDepth - 1);
+  }
+  if (ok && nst > 0) {
+    if (bar_wait(&ctl->bar[(nst - 1) % kDepth], ((nst - 1) / kDepth) & 1))
+      drain_bank(ctl, (nst - 1) & 1, col0, nk, acc);
+    else
+      ok = false;
+  }
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicOr(a.status, 8);
+    tc_end(ctl, kFTmemCols);
+    return;
+  }
+  // epilogue: right-hand side r, ranks col0 .. col0 + 63 of the group
+  const int r = 32 * (w & 3) + (tid & 31);
+  const int64_t pstride = static_cast<int64_t>(128) * nk;
+#pragma unroll
+  for (int cb = 0; cb < 4; ++cb) {
+    const int c16 = col0 + 16 * cb;
+    if (c16 >= nk) break;
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = acc[16 * cb + j];
+    if (g.nsplit == 1) {
+      write_t(a, a.pieces[rowpiece[c16]], c16, r, v);
+    } else {
+      float4* dst = reinterpret_cast<float4*>(a.part + g.poff + static_cast<int64_t>(r) * nk + c16);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    }
+  }
+  if (g.nsplit > 1) {
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) ctl->last = atomicAdd(a.cnt + g.gid, 1) == g.nsplit - 1;
+    __syncthreads();
+    if (ctl->last) {
+      __threadfence();
+      const float* p0 = a.part + g.poff - static_cast<int64_t>(g.split) * pstride;
+#pragma unroll
+      for (int cb = 0; cb < 4; ++cb) {
+        const int c16 = col0 + 16 * cb;
+        if (c16 >= nk) break;
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        for (int sp = 0; sp < g.nsplit; ++sp) {
+          const float4* src = reinterpret_cast<const float4*>(p0 + sp * pstride + static_cast<int64_t>(r) * nk + c16);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 f = __ldcg(src + j);
+            v[4 * j] += f.x;
+            v[4 * j + 1] += f.y;
+            v[4 * j + 2] += f.z;
+            v[4 * j + 3] += f.w;
+          }
+        }
+        write_t(a, a.pieces[rowpiece[c16]], c16, r, v);
+      }
+      if (tid == 0) a.cnt[g.gid] = 0;
+    }
+  }
+  tc_end(ctl, kFTmemCols);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) tc_phase2_f32(TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align128(smem_raw);
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + kDepth * kF2Stage);
+  const TcTile tl = a.tiles[blockIdx.x];
+  const int tid = threadIdx.x, rp = a.rp;
+  tc_begin(ctl, kFTmemCols);
+  int nst = 0;
+  for (int e = 0; e < tl.count; ++e) nst += a.pieces[a.entries[tl.first + e].piece].kp >> 4;
+  const uint32_t idesc = idesc_bf16(rp);
+  const int w = tid >> 5, col0 = 64 * (w >> 2);
+  float acc[64];
+#pragma unroll
+  for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+  Cursor ld{}, cv{};
+  cursor_load(ld, a, tl);
+  cv = ld;
+  // copies of stage i: T slices straight into the operand; raw fp32 U rows
+  // [src, src + nrows) of the 16 ranks, [rank][tile row], 4 rows per copy
+  auto issue_loads = [&](int i) {
+    if (i < nst) {
+      const TcEntry& en = ld.en;
+      uint8_t* st = base + (i % kDepth) * kF2Stage;
+      const uint8_t* tsrc = a.timg + ld.toff + static_cast<int64_t>(ld.step) * 4096;
+      const int tunits = rp * 2;
+      for (int u = tid; u < 3 * tunits; u += kThreads) {
+        const int sl = u / tunits, wu = u - sl * tunits;
+        cp16(st + kF2Raw + kF2UOp + sl * 4096 + wu * 16, tsrc + static_cast<int64_t>(sl) * ld.steps * 4096 + wu * 16);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int u = tid + h * kThreads, j = u >> 5, m0 = 4 * (u & 31);
+        const int jj = 16 * ld.step + j;
+        if (jj < ld.k && m0 >= en.dst && m0 < en.dst + en.nrows)
+          cp16(st + j * (kTcRows * 4) + m0 * 4, ld.f2 + (static_cast<int64_t>(jj) * ld.ld2 + en.src + (m0 - en.dst)) * 4);
+      }
+      cursor_advance(ld, a, tl);
+    }
+    cp_commit();
+  };
+  auto convert = [&](int i) {
+    if (i >= nst) return;
+    const TcEntry& en = cv.en;
+    uint8_t* st = base + (i % kDepth) * kF2Stage;
+    const int m = tid >> 1, uo = tid & 1;
+    const bool in = m >= en.dst && m < en.dst + en.nrows;
+    const int j0 = 16 * cv.step + 8 * uo;
+    const float* raw = reinterpret_cast<const float*>(st);
+    float v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = (in && j0 + t < cv.k) ? raw[(8 * uo + t) * kTcRows + m] : 0.f;
+    store_slices3(v, st + kF2Raw + core_off(m, uo), kTcRows * 32);
+    cursor_advance(cv, a, tl);
+  };
+
+  for (int i = 0; i < kDepth - 1; ++i) issue_loads(i);
+  cp_wait<kDepth - 2>();
+  __syncthreads();
+  convert(0);
+  bool ok = true;
+  for (int i = 0; i < nst; ++i) {
+    const int s = i % kDepth;
+    uint8_t* st = base + s * kF2Stage;
+    cp_wait<kDepth - 3>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t tb = ctl->tmem + 256 * (i & 1);
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        const uint64_t da = op_desc(st + kF2Raw + fpf(p) * (kTcRows * 32));
+        const uint64_t db = op_desc(st + kF2Raw + kF2UOp + fpx(p) * 4096);
+        mma(tb + (p ? 128 : 0), da, db, idesc, p >= 2 ? 1u : 0u);
+      }
+      mma_commit(&ctl->bar[s]);
+    }
+    if (i >= 1) {
+      if (bar_wait(&ctl->bar[(i - 1) % kDepth], ((i - 1) / kDepth) & 1))
+        drain_bank(ctl, (i - 1) & 1, col0, rp, acc);
+      else
+        ok = false;
+    }
+    issue_loads(i + kDepth - 1);
+    convert(i + 1);
+  }
+  if (ok && nst > 0) {
+    if (bar_wait(&ctl->bar[(nst - 1) % kDepth], ((nst - 1) / kDepth) & 1))
+      drain_bank(ctl, (nst - 1) & 1, col0, rp, acc);
+    else
+      ok = false;
+  }
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicOr(a.status, 8);
+  } else if (nst > 0) {
+    // epilogue: tile row of this lane, right-hand sides col0 .. col0 + 63
+    const int row = 32 * (w & 3) + (tid & 31);
+    if (row < tl.rows) {
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        const int rr = col0 + j;
+        if (rr < a.nr) a.acc[static_cast<int64_t>(rr) * a.npad + tl.row0 + row] += static_cast<double>(acc[j]);
+      }
+    }
+  }
+  tc_end(ctl, kFTmemCols);
+}
+
+// X (caller's order, column-major, ld) -> tree order, fp32, three bf16 slices in
 // the phase-1 operand image [slice][16-position block][128 rows x 32 B]; rows
 // r >= nr and positions >= n are zero.  Also clears the output accumulator
 // and the arrival counters of the split groups.
@@ -573,7 +894,7 @@ __global__ void tc_prep_kernel(const double* __restrict__ x, int64_t ld, int nr,
       const int64_t p = 16 * blk + 8 * c + t;
       v[t] = (r < nr && p < n) ? __double2float_rn(x[static_cast<int64_t>(perm[p]) + r * ld]) : 0.f;
     }
-    store_slices(v, 2, ximg + (blk << 12) + core_off(r, c), nblk << 12);
+    store_slices3(v, ximg + (blk << 12) + core_off(r, c), nblk << 12);
   }
   const int64_t ntot = static_cast<int64_t>(nr) * npad;
   for (int64_t q = t0; q < ntot; q += stride) acc[q] = 0.0;
@@ -595,9 +916,24 @@ cudaError_t launch_tc_prep(const double* x, int64_t ld, int nr, const int32_t* p
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc(int phase, const TcArgs& a, cudaStream_t st) {
-  const size_t smem = tc_smem_bytes(phase);
+cudaError_t launch_tc(int phase, const TcArgs& a, cudaStream_t st, bool f32) {
   if (a.rp < 16 || a.rp > 128 || (a.rp & 15)) return cudaErrorInvalidValue;
+  if (f32) {
+    const size_t smem = (phase == 1 ? kDepth * kF1Stage : kDepth * kF2Stage) + 128 + sizeof(Ctl) + kTcGroupRanks * 12;
+    if (phase == 1) {
+      if (a.n_groups <= 0) return cudaSuccess;
+      cudaError_t e = cudaFuncSetAttribute(tc_phase1_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      tc_phase1_f32<<<a.n_groups, kThreads, smem, st>>>(a);
+    } else {
+      if (a.n_tiles <= 0) return cudaSuccess;
+      cudaError_t e = cudaFuncSetAttribute(tc_phase2_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      tc_phase2_f32<<<a.n_tiles, kThreads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+  }
+  const size_t smem = tc_smem_bytes(phase);
   if (phase == 1) {
     if (a.n_groups <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(tc_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

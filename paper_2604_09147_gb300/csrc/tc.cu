@@ -216,6 +216,15 @@ __device__ __forceinline__ void tc_end(Ctl* c, uint32_t cols = kTmemCols) {
 
 // T = 2^e D of 16 ranks of one right-hand side, as the two slices of the
 // phase-2 operand image of its piece
+// 16 columns of this warp's 32 lanes, without waiting (tcgen05.wait::ld follows)
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
 // exact split of an fp32 value into three bf16 slices
 __device__ __forceinline__ void store_slices3(const float* v, uint8_t* dst, int64_t sstride) {
   __align__(16) __nv_bfloat16 s[3][8];
@@ -268,7 +277,9 @@ __global__ void __launch_bounds__(kThreads, 2) tc_phase1(TcArgs a) {
   const uint32_t idesc = idesc_bf16(nk);
   // this thread's factor unit: 16-bit formats (rank j, 8 positions at 8c), e4m3 (rank j, 16 positions)
   const bool e4 = fmt == kE4M3;
-  const int vj = e4 ? tid : (tid >> 1), vc = e4 ? 0 : (tid & 1);
+  // consecutive threads take consecutive ranks: the 16-byte operand stores of a
+  // quarter warp then fill one 128-byte line
+  const int vj = e4 ? tid : (tid & 127), vc = e4 ? 0 : (tid >> 7);
   const bool vown = vj < nk && (e4 || true);
   const uint8_t* vcol = vown ? colp[vj] : nullptr;
 
@@ -489,7 +500,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_phase2(TcArgs a) {
     if (i >= nst) return;
     const TcEntry& en = cv.en;
     uint8_t* st = base + (i % kDepth) * kP2Stage;
-    const int m = tid >> 1, uo = tid & 1, sz = fmt_size(cv.fmt);
+    const int m = tid & 127, uo = tid >> 7, sz = fmt_size(cv.fmt);
     const bool in = m >= en.dst && m < en.dst + en.nrows;
     const int j0 = 16 * cv.step + 8 * uo;
     float v[8];
@@ -575,16 +586,32 @@ __global__ void __launch_bounds__(kThreads, 2) tc_phase2(TcArgs a) {
 
 // ------------------------------------------------------------------ fp32 blocks
 // fp32 factors and inputs as three exact bf16 slices, six products (slice
-// indices summing to at most 2).  Every stage's MMAs start a fresh pair of
-// accumulators (main product, corrections) in one of two tensor-memory banks,
-// and the threads add the finished bank into fp32 registers (round to
-// nearest) while the next stage's MMAs fill the other bank: the tensor core's
-// truncating accumulation then acts once per 16-term stage instead of
-// growing with the length of the contraction, which keeps fp32 accuracy.
-// 160 KB of shared memory and 512 tensor-memory columns: one CTA per SM.
+// indices summing to at most 2).  Every pair of stages (32 terms of the
+// contraction) starts a fresh pair of accumulators (main product,
+// corrections) in one of two tensor-memory banks, and the drain warps add the
+// finished bank into fp32 registers (round to nearest) while the next pair's
+// MMAs fill the other bank: the tensor core's truncating accumulation acts on
+// 32-term partial sums instead of growing with the length of the
+// contraction, which keeps fp32 accuracy.
+//
+// Warp roles, no CTA-wide barrier inside the loop (each hand-off is an
+// mbarrier with a bounded wait that also gives up when another role aborted):
+//   warp 0     producer: copies of the stage's operand bytes into a
+//              kWsDepth-deep ring (bulk copies for the contiguous input and T
+//              slices and U rows, per-lane 16-byte cp.async for the 64-byte V
+//              rows), completion counted on full[s]
+//   warp 1     one thread issues the MMAs of a stage once it is converted
+//              (conv[s]) and, for a pair's first stage, its bank is drained
+//              (bempty[b]); tcgen05.commit frees the stage (empty[s]) and,
+//              after a pair's second stage, hands the bank over (bfull[b])
+//   warps 2-3  convert raw fp32 bytes into bf16 slices in the operand layout
+//   warps 4-7  drain the banks (one tensor-memory lane quarter each) into
+//              fp32 registers, then write the results
+// ~195 KB of shared memory and 512 tensor-memory columns: one CTA per SM.
+constexpr int kWsDepth = 6;
 constexpr int kF1XOp = 3 * 4096;                   // X slices [3][128 rows x 32 B]
 constexpr int kF1VOp = 3 * kTcGroupRanks * 32;     // V slices [3][nk rows x 32 B]
-constexpr int kF1Raw = kTcGroupRanks * 64;         // raw fp32 V [nk ranks][16 positions]
+constexpr int kF1Raw = kTcGroupRanks * 64;         // raw fp32 V [4 chunks of 4 positions][nk ranks] x 16 B
 constexpr int kF1Stage = kF1XOp + kF1VOp + kF1Raw;
 constexpr int kF2Raw = 16 * kTcRows * 4;           // raw fp32 U [16 ranks][128 rows]
 constexpr int kF2UOp = 3 * kTcRows * 32;           // U slices [3][128 rows x 32 B]
@@ -595,19 +622,136 @@ constexpr uint32_t kFTmemCols = 512;               // bank b: main at 256 b, cor
 __device__ __forceinline__ int fpf(int p) { return (0x210100 >> (4 * p)) & 0xf; }
 __device__ __forceinline__ int fpx(int p) { return (0x012010 >> (4 * p)) & 0xf; }
 
-// add a finished bank (this thread's lane, 64 columns from col0) into acc
-__device__ __forceinline__ void drain_bank(const Ctl* ctl, int bank, int col0, int ncols, float* acc) {
+struct WsCtl {
+  uint64_t full[kWsDepth], conv[kWsDepth], empty[kWsDepth];
+  uint64_t bfull[2], bempty[2];
+  uint32_t tmem;
+  int abort;
+  int last;
+};
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_once(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                               uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          saddr(dst)),
+      "l"(src), "r"(bytes), "r"(saddr(bar)), "l"(policy)
+      : "memory");
+}
+// the mbarrier counts the completion of this thread's earlier cp.async copies
+// (it raises the pending count first, so no arrival needs to be pre-counted)
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(saddr(bar)) : "memory");
+}
+__device__ __forceinline__ uint64_t evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// bounded wait that also gives up when another role set the abort flag
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  uint32_t ok;
+  auto probe = [&]() {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+  };
+  if (probe()) return true;
+  const long long t0 = clock64();
+  for (int n = 1;; ++n) {
+    if (probe()) return true;
+    if ((n & 63) == 0 && *abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void ws_setup(WsCtl* c) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWsDepth; ++s) {
+      mbar_init(&c->full[s], 1);
+      mbar_init(&c->conv[s], 2);
+      mbar_init(&c->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&c->bfull[b], 1);
+      mbar_init(&c->bempty[b], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    c->abort = 0;
+    c->last = 0;
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&c->tmem)),
+                 "r"(kFTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// after the role loops: on an abort the producer waits for the copies it
+// issued and the MMA thread for its last MMAs, then tensor memory is freed
+__device__ __forceinline__ void ws_teardown(WsCtl* c, int produced, int mmas, int* status) {
+  asm volatile("cp.async.wait_all;" ::: "memory");  // the producer's per-lane copies (not in commit groups)
+  __syncthreads();
+  if (c->abort) {
+    volatile int no = 0;
+    if (threadIdx.x == 0)
+      for (int i = produced > kWsDepth ? produced - kWsDepth : 0; i < produced; ++i)
+        ws_wait(&c->full[i % kWsDepth], (i / kWsDepth) & 1, &no);
+    if (threadIdx.x == 32 && mmas > 0) ws_wait(&c->empty[(mmas - 1) % kWsDepth], ((mmas - 1) / kWsDepth) & 1, &no);
+    if (threadIdx.x == 0) atomicOr(status, 8);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c->tmem), "r"(kFTmemCols));
+}
+
+// drain warps: add bank b (this lane, columns 0 .. ncols) into acc, 32
+// columns (main and corrections) per tcgen05.wait::ld
+__device__ __forceinline__ void ws_drain(const WsCtl* c, int bank, int ncols, float* acc) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int w = threadIdx.x >> 5;
-  const uint32_t t = ctl->tmem + (static_cast<uint32_t>(32 * (w & 3)) << 16) + 256 * bank;
+  const uint32_t t = c->tmem + (static_cast<uint32_t>(32 * (w & 3)) << 16) + 256 * bank;
 #pragma unroll
   for (int cb = 0; cb < 4; ++cb) {
-    if (col0 + 16 * cb < ncols) {
-      float hi[16], lo[16];
-      tmem_ld16(t + col0 + 16 * cb, hi);
-      tmem_ld16(t + 128 + col0 + 16 * cb, lo);
+    if (32 * cb < ncols) {
+      uint32_t h0[16], h1[16], l0[16], l1[16];
+      tmem_ld16_nowait(t + 32 * cb, h0);
+      tmem_ld16_nowait(t + 32 * cb + 16, h1);
+      tmem_ld16_nowait(t + 128 + 32 * cb, l0);
+      tmem_ld16_nowait(t + 128 + 32 * cb + 16, l1);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < 16; ++j) acc[16 * cb + j] += hi[j] + lo[j];
+      for (int j = 0; j < 16; ++j) {
+        acc[32 * cb + j] += __uint_as_float(h0[j]) + __uint_as_float(l0[j]);
+        acc[32 * cb + 16 + j] += __uint_as_float(h1[j]) + __uint_as_float(l1[j]);
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -616,11 +760,11 @@ __device__ __forceinline__ void drain_bank(const Ctl* ctl, int bank, int col0, i
 __global__ void __launch_bounds__(kThreads, 1) tc_phase1_f32(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align128(smem_raw);
-  Ctl* ctl = reinterpret_cast<Ctl*>(base + kDepth * kF1Stage);
-  const uint8_t** colp = reinterpret_cast<const uint8_t**>(ctl + 1);
+  WsCtl* c = reinterpret_cast<WsCtl*>(base + kWsDepth * kF1Stage);
+  const uint8_t** colp = reinterpret_cast<const uint8_t**>(c + 1);
   int* rowpiece = reinterpret_cast<int*>(colp + kTcGroupRanks);
   const TcGroup g = a.groups[blockIdx.x];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   if (tid < g.count) {
     const TcPiece& q = a.pieces[g.first + tid];
     for (int j = 0; j < q.kp; ++j) {
@@ -628,119 +772,129 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1_f32(TcArgs a) {
       colp[q.col + j] = j < q.k ? q.f1 + static_cast<int64_t>(j) * q.ld1 * 4 : nullptr;
     }
   }
-  tc_begin(ctl, kFTmemCols);
+  ws_setup(c);  // its barrier also publishes colp / rowpiece
   const int nk = g.nk;
   const int nst = (g.p1 - g.p0 + 15) >> 4;
-  const uint32_t idesc = idesc_bf16(nk);
-  // this thread's factor unit: rank vj, positions 8 vc .. 8 vc + 7 of the stage
-  const int vj = tid >> 1, vc = tid & 1;
-  const bool vown = vj < nk;
-  const uint8_t* vcol = vown ? colp[vj] : nullptr;
-  const int w = tid >> 5, col0 = 64 * (w >> 2);
-  float acc[64];
+  volatile int* abort = &c->abort;
+  int produced = 0, mmas = 0;
+  float acc[128];
 #pragma unroll
-  for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+  for (int j = 0; j < 128; ++j) acc[j] = 0.f;
 
-  auto issue_loads = [&](int i) {
-    if (i < nst) {
-      uint8_t* st = base + (i % kDepth) * kF1Stage;
+  if (w == 0) {  // producer: V rows by cp.async (16 bytes per lane copy), X slices by bulk copy
+    for (int i = 0; i < nst; ++i) {
+      const int s = i % kWsDepth;
+      if (i >= kWsDepth && !ws_wait(&c->empty[s], ((i / kWsDepth) - 1) & 1, abort)) break;
+      uint8_t* st = base + s * kF1Stage;
       const int p = g.p0 + 16 * i;
       const int64_t blk = (static_cast<int64_t>(g.in_off) + p) >> 4;
+      for (int j = lane; j < nk; j += 32)
+        if (colp[j]) {
 #pragma unroll
-      for (int sl = 0; sl < 3; ++sl)
-        cp16(st + sl * 4096 + tid * 16, a.ximg + ((static_cast<int64_t>(sl) * a.nblk + blk) << 12) + tid * 16);
-      if (vcol) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int pos = p + 8 * vc + 4 * h;
-          if (pos < g.p1) cp16(st + kF1XOp + kF1VOp + vj * 64 + vc * 32 + h * 16, vcol + 4 * pos);
+          for (int q = 0; q < 4; ++q)
+            if (p + 4 * q < g.p1)
+              cp16(st + kF1XOp + kF1VOp + (q * nk + j) * 16, colp[j] + 4 * static_cast<int64_t>(p + 4 * q));
         }
+      cp_async_arrive(&c->full[s]);
+      __syncwarp();
+      if (lane == 0) {
+        mbar_expect_tx(&c->full[s], 3u * 4096u);
+        for (int sl = 0; sl < 3; ++sl)
+          bulk_copy(st + sl * 4096, a.ximg + ((static_cast<int64_t>(sl) * a.nblk + blk) << 12), 4096, &c->full[s]);
+      }
+      produced = i + 1;
+    }
+  } else if (w == 1) {  // MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(nk);
+      for (int i = 0; i < nst; ++i) {
+        // banks alternate per pair of stages: the pair's first stage starts
+        // fresh accumulators, the second adds to them, then the bank is drained
+        const int s = i % kWsDepth, q = i >> 1, b = q & 1, second = i & 1;
+        // the stage's bulk copies (operands the converters do not touch) and its conversion
+        if (!ws_wait(&c->full[s], (i / kWsDepth) & 1, abort)) break;
+        if (!ws_wait(&c->conv[s], (i / kWsDepth) & 1, abort)) break;
+        if (!second && q >= 2 && !ws_wait(&c->bempty[b], ((q >> 1) - 1) & 1, abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint8_t* st = base + s * kF1Stage;
+        const uint32_t tb = c->tmem + 256 * b;
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+          const uint64_t da = op_desc(st + fpx(p) * 4096);
+          const uint64_t db = op_desc(st + kF1XOp + fpf(p) * (nk * 32));
+          mma(tb + (p ? 128 : 0), da, db, idesc, (p >= 2 || second) ? 1u : 0u);
+        }
+        mma_commit(&c->empty[s]);
+        if (second || i == nst - 1) mma_commit(&c->bfull[b]);
+        mmas = i + 1;
       }
     }
-    cp_commit();
-  };
-  auto convert = [&](int i) {
-    if (!vown) return;
-    uint8_t* st = base + (i % kDepth) * kF1Stage;
-    const int pos = g.p0 + 16 * i + 8 * vc;
-    const float* raw = reinterpret_cast<const float*>(st + kF1XOp + kF1VOp + vj * 64 + vc * 32);
-    float v[8];
+  } else if (w < 4) {  // converters
+    const int ct = tid - 64;
+    for (int i = 0; i < nst; ++i) {
+      const int s = i % kWsDepth;
+      if (!ws_wait(&c->full[s], (i / kWsDepth) & 1, abort)) break;
+      uint8_t* st = base + s * kF1Stage;
+      const int p = g.p0 + 16 * i;
+      for (int u = ct; u < 2 * nk; u += 64) {
+        const int j = u < nk ? u : u - nk, half = u < nk ? 0 : 1, pos = p + 8 * half;
+        // chunks 2 half and 2 half + 1 of rank j (a quarter warp reads 128 contiguous bytes)
+        const float4 r0 = *reinterpret_cast<const float4*>(st + kF1XOp + kF1VOp + ((2 * half) * nk + j) * 16);
+        const float4 r1 = *reinterpret_cast<const float4*>(st + kF1XOp + kF1VOp + ((2 * half + 1) * nk + j) * 16);
+        const float raw[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        const bool live = colp[j] != nullptr;
+        float v[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = (vcol && pos + t < g.p1) ? raw[t] : 0.f;
-    store_slices3(v, st + kF1XOp + core_off(vj, vc), nk * 32);
-  };
-
-  for (int i = 0; i < kDepth - 1; ++i) issue_loads(i);
-  bool ok = true;
-  for (int i = 0; i < nst; ++i) {
-    const int s = i % kDepth;
-    uint8_t* st = base + s * kF1Stage;
-    cp_wait<kDepth - 2>();
-    convert(i);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (__syncthreads_or(!ok)) {
-      ok = false;
-      break;
-    }
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t tb = ctl->tmem + 256 * (i & 1);
-#pragma unroll
-      for (int p = 0; p < 6; ++p) {
-        const uint64_t da = op_desc(st + fpx(p) * 4096);
-        const uint64_t db = op_desc(st + kF1XOp + fpf(p) * (nk * 32));
-        mma(tb + (p ? 128 : 0), da, db, idesc, p >= 2 ? 1u : 0u);
+        for (int t = 0; t < 8; ++t) v[t] = (live && pos + t < g.p1) ? raw[t] : 0.f;
+        store_slices3(v, st + kF1XOp + core_off(j, half), nk * 32);
       }
-      mma_commit(&ctl->bar[s]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&c->conv[s]);
     }
-    if (i >= 1) {
-      if (bar_wait(&ctl->bar[(i - 1) % kDepth], ((i - 1) / kDepth) & 1))
-        drain_bank(ctl, (i - 1) & 1, col0, nk, acc);
-      else
-        ok = false;
+  } else {  // drain warps
+    for (int q = 0; 2 * q < nst; ++q) {
+      const int b = q & 1;
+      if (!ws_wait(&c->bfull[b], (q >> 1) & 1, abort)) break;
+      ws_drain(c, b, nk, acc);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&c->bempty[b]);
     }
-    issue_loads(i + kDepth - 1);
   }
-  if (ok && nst > 0) {
-    if (bar_wait(&ctl->bar[(nst - 1) % kDepth], ((nst - 1) / kDepth) & 1))
-      drain_bank(ctl, (nst - 1) & 1, col0, nk, acc);
-    else
-      ok = false;
-  }
-  if (__syncthreads_or(!ok)) {
-    if (tid == 0) atomicOr(a.status, 8);
-    tc_end(ctl, kFTmemCols);
+  if (__syncthreads_or(c->abort)) {
+    ws_teardown(c, produced, mmas, a.status);
     return;
   }
-  // epilogue: right-hand side r, ranks col0 .. col0 + 63 of the group
-  const int r = 32 * (w & 3) + (tid & 31);
+  // epilogue (drain warps): right-hand side r, ranks 0 .. nk of the group
+  const int r = 32 * (w & 3) + lane;
   const int64_t pstride = static_cast<int64_t>(128) * nk;
+  if (w >= 4) {
 #pragma unroll
-  for (int cb = 0; cb < 4; ++cb) {
-    const int c16 = col0 + 16 * cb;
-    if (c16 >= nk) break;
-    float v[16];
+    for (int cb = 0; cb < 8; ++cb) {
+      const int c16 = 16 * cb;
+      if (c16 >= nk) break;
+      float v[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = acc[16 * cb + j];
-    if (g.nsplit == 1) {
-      write_t(a, a.pieces[rowpiece[c16]], c16, r, v);
-    } else {
-      float4* dst = reinterpret_cast<float4*>(a.part + g.poff + static_cast<int64_t>(r) * nk + c16);
+      for (int j = 0; j < 16; ++j) v[j] = acc[c16 + j];
+      if (g.nsplit == 1) {
+        write_t(a, a.pieces[rowpiece[c16]], c16, r, v);
+      } else {
+        float4* dst = reinterpret_cast<float4*>(a.part + g.poff + static_cast<int64_t>(r) * nk + c16);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+      }
     }
   }
   if (g.nsplit > 1) {
     __threadfence();
     __syncthreads();
-    if (tid == 0) ctl->last = atomicAdd(a.cnt + g.gid, 1) == g.nsplit - 1;
+    if (tid == 0) c->last = atomicAdd(a.cnt + g.gid, 1) == g.nsplit - 1;
     __syncthreads();
-    if (ctl->last) {
+    if (c->last && w >= 4) {
       __threadfence();
       const float* p0 = a.part + g.poff - static_cast<int64_t>(g.split) * pstride;
-#pragma unroll
-      for (int cb = 0; cb < 4; ++cb) {
-        const int c16 = col0 + 16 * cb;
+      for (int cb = 0; cb < 8; ++cb) {
+        const int c16 = 16 * cb;
         if (c16 >= nk) break;
         float v[16];
 #pragma unroll
@@ -758,121 +912,124 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1_f32(TcArgs a) {
         }
         write_t(a, a.pieces[rowpiece[c16]], c16, r, v);
       }
-      if (tid == 0) a.cnt[g.gid] = 0;
     }
+    if (c->last && tid == 0) a.cnt[g.gid] = 0;
   }
-  tc_end(ctl, kFTmemCols);
+  ws_teardown(c, produced, mmas, a.status);
 }
 
 __global__ void __launch_bounds__(kThreads, 1) tc_phase2_f32(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align128(smem_raw);
-  Ctl* ctl = reinterpret_cast<Ctl*>(base + kDepth * kF2Stage);
+  WsCtl* c = reinterpret_cast<WsCtl*>(base + kWsDepth * kF2Stage);
   const TcTile tl = a.tiles[blockIdx.x];
-  const int tid = threadIdx.x, rp = a.rp;
-  tc_begin(ctl, kFTmemCols);
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, rp = a.rp;
+  ws_setup(c);
   int nst = 0;
   for (int e = 0; e < tl.count; ++e) nst += a.pieces[a.entries[tl.first + e].piece].kp >> 4;
-  const uint32_t idesc = idesc_bf16(rp);
-  const int w = tid >> 5, col0 = 64 * (w >> 2);
-  float acc[64];
+  volatile int* abort = &c->abort;
+  int produced = 0, mmas = 0;
+  float acc[128];
 #pragma unroll
-  for (int j = 0; j < 64; ++j) acc[j] = 0.f;
-  Cursor ld{}, cv{};
-  cursor_load(ld, a, tl);
-  cv = ld;
-  // copies of stage i: T slices straight into the operand; raw fp32 U rows
-  // [src, src + nrows) of the 16 ranks, [rank][tile row], 4 rows per copy
-  auto issue_loads = [&](int i) {
-    if (i < nst) {
-      const TcEntry& en = ld.en;
-      uint8_t* st = base + (i % kDepth) * kF2Stage;
-      const uint8_t* tsrc = a.timg + ld.toff + static_cast<int64_t>(ld.step) * 4096;
-      const int tunits = rp * 2;
-      for (int u = tid; u < 3 * tunits; u += kThreads) {
-        const int sl = u / tunits, wu = u - sl * tunits;
-        cp16(st + kF2Raw + kF2UOp + sl * 4096 + wu * 16, tsrc + static_cast<int64_t>(sl) * ld.steps * 4096 + wu * 16);
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int u = tid + h * kThreads, j = u >> 5, m0 = 4 * (u & 31);
-        const int jj = 16 * ld.step + j;
-        if (jj < ld.k && m0 >= en.dst && m0 < en.dst + en.nrows)
-          cp16(st + j * (kTcRows * 4) + m0 * 4, ld.f2 + (static_cast<int64_t>(jj) * ld.ld2 + en.src + (m0 - en.dst)) * 4);
-      }
-      cursor_advance(ld, a, tl);
-    }
-    cp_commit();
-  };
-  auto convert = [&](int i) {
-    if (i >= nst) return;
-    const TcEntry& en = cv.en;
-    uint8_t* st = base + (i % kDepth) * kF2Stage;
-    const int m = tid >> 1, uo = tid & 1;
-    const bool in = m >= en.dst && m < en.dst + en.nrows;
-    const int j0 = 16 * cv.step + 8 * uo;
-    const float* raw = reinterpret_cast<const float*>(st);
-    float v[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = (in && j0 + t < cv.k) ? raw[(8 * uo + t) * kTcRows + m] : 0.f;
-    store_slices3(v, st + kF2Raw + core_off(m, uo), kTcRows * 32);
-    cursor_advance(cv, a, tl);
-  };
+  for (int j = 0; j < 128; ++j) acc[j] = 0.f;
 
-  for (int i = 0; i < kDepth - 1; ++i) issue_loads(i);
-  cp_wait<kDepth - 2>();
-  __syncthreads();
-  convert(0);
-  bool ok = true;
-  for (int i = 0; i < nst; ++i) {
-    const int s = i % kDepth;
-    uint8_t* st = base + s * kF2Stage;
-    cp_wait<kDepth - 3>();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (__syncthreads_or(!ok)) {
-      ok = false;
-      break;
+  if (w == 0) {  // producer: T slices (rp rows each) and the raw fp32 U rows of 16 ranks
+    Cursor ld{};
+    cursor_load(ld, a, tl);
+    const uint64_t pol = evict_first();
+    for (int i = 0; i < nst; ++i) {
+      const int s = i % kWsDepth;
+      if (i >= kWsDepth && !ws_wait(&c->empty[s], ((i / kWsDepth) - 1) & 1, abort)) break;
+      uint8_t* st = base + s * kF2Stage;
+      const TcEntry& en = ld.en;
+      const int nj = min(16, ld.k - 16 * ld.step);
+      const uint32_t segb = 16u * static_cast<uint32_t>((en.nrows + 3) >> 2);
+      if (lane == 0) mbar_expect_tx(&c->full[s], 3u * static_cast<uint32_t>(rp) * 32u + static_cast<uint32_t>(nj) * segb);
+      __syncwarp();
+      if (lane < 3)
+        bulk_copy(st + kF2Raw + kF2UOp + lane * 4096,
+                  a.timg + ld.toff + (static_cast<int64_t>(lane) * ld.steps + ld.step) * 4096,
+                  static_cast<uint32_t>(rp) * 32u, &c->full[s]);
+      if (lane < nj)
+        bulk_copy_once(st + (lane * kTcRows + en.dst) * 4,
+                       ld.f2 + (static_cast<int64_t>(16 * ld.step + lane) * ld.ld2 + en.src) * 4, segb, &c->full[s],
+                       pol);
+      cursor_advance(ld, a, tl);
+      produced = i + 1;
     }
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t tb = ctl->tmem + 256 * (i & 1);
+  } else if (w == 1) {  // MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(rp);
+      for (int i = 0; i < nst; ++i) {
+        // banks alternate per pair of stages: the pair's first stage starts
+        // fresh accumulators, the second adds to them, then the bank is drained
+        const int s = i % kWsDepth, q = i >> 1, b = q & 1, second = i & 1;
+        // the stage's bulk copies (operands the converters do not touch) and its conversion
+        if (!ws_wait(&c->full[s], (i / kWsDepth) & 1, abort)) break;
+        if (!ws_wait(&c->conv[s], (i / kWsDepth) & 1, abort)) break;
+        if (!second && q >= 2 && !ws_wait(&c->bempty[b], ((q >> 1) - 1) & 1, abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint8_t* st = base + s * kF2Stage;
+        const uint32_t tb = c->tmem + 256 * b;
 #pragma unroll
-      for (int p = 0; p < 6; ++p) {
-        const uint64_t da = op_desc(st + kF2Raw + fpf(p) * (kTcRows * 32));
-        const uint64_t db = op_desc(st + kF2Raw + kF2UOp + fpx(p) * 4096);
-        mma(tb + (p ? 128 : 0), da, db, idesc, p >= 2 ? 1u : 0u);
+        for (int p = 0; p < 6; ++p) {
+          const uint64_t da = op_desc(st + kF2Raw + fpf(p) * (kTcRows * 32));
+          const uint64_t db = op_desc(st + kF2Raw + kF2UOp + fpx(p) * 4096);
+          mma(tb + (p ? 128 : 0), da, db, idesc, (p >= 2 || second) ? 1u : 0u);
+        }
+        mma_commit(&c->empty[s]);
+        if (second || i == nst - 1) mma_commit(&c->bfull[b]);
+        mmas = i + 1;
       }
-      mma_commit(&ctl->bar[s]);
     }
-    if (i >= 1) {
-      if (bar_wait(&ctl->bar[(i - 1) % kDepth], ((i - 1) / kDepth) & 1))
-        drain_bank(ctl, (i - 1) & 1, col0, rp, acc);
-      else
-        ok = false;
+  } else if (w < 4) {  // converters: U rows from [rank][row] to K-major slices
+    const int ct = tid - 64;
+    Cursor cv{};
+    cursor_load(cv, a, tl);
+    for (int i = 0; i < nst; ++i) {
+      const int s = i % kWsDepth;
+      if (!ws_wait(&c->full[s], (i / kWsDepth) & 1, abort)) break;
+      uint8_t* st = base + s * kF2Stage;
+      const TcEntry& en = cv.en;
+      const float* raw = reinterpret_cast<const float*>(st);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int u = ct + 64 * k, m = u & 127, uo = u >> 7;
+        const bool in = m >= en.dst && m < en.dst + en.nrows;
+        const int j0 = 16 * cv.step + 8 * uo;
+        float v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = (in && j0 + t < cv.k) ? raw[(8 * uo + t) * kTcRows + m] : 0.f;
+        store_slices3(v, st + kF2Raw + core_off(m, uo), kTcRows * 32);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&c->conv[s]);
+      cursor_advance(cv, a, tl);
     }
-    issue_loads(i + kDepth - 1);
-    convert(i + 1);
+  } else {  // drain warps
+    for (int q = 0; 2 * q < nst; ++q) {
+      const int b = q & 1;
+      if (!ws_wait(&c->bfull[b], (q >> 1) & 1, abort)) break;
+      ws_drain(c, b, rp, acc);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&c->bempty[b]);
+    }
   }
-  if (ok && nst > 0) {
-    if (bar_wait(&ctl->bar[(nst - 1) % kDepth], ((nst - 1) / kDepth) & 1))
-      drain_bank(ctl, (nst - 1) & 1, col0, rp, acc);
-    else
-      ok = false;
+  if (__syncthreads_or(c->abort)) {
+    ws_teardown(c, produced, mmas, a.status);
+    return;
   }
-  if (__syncthreads_or(!ok)) {
-    if (tid == 0) atomicOr(a.status, 8);
-  } else if (nst > 0) {
-    // epilogue: tile row of this lane, right-hand sides col0 .. col0 + 63
-    const int row = 32 * (w & 3) + (tid & 31);
+  // epilogue (drain warps): tile row of this lane, right-hand sides 0 .. rp
+  if (w >= 4 && nst > 0) {
+    const int row = 32 * (w & 3) + lane;
     if (row < tl.rows) {
 #pragma unroll
-      for (int j = 0; j < 64; ++j) {
-        const int rr = col0 + j;
-        if (rr < a.nr) a.acc[static_cast<int64_t>(rr) * a.npad + tl.row0 + row] += static_cast<double>(acc[j]);
-      }
+      for (int j = 0; j < 128; ++j)
+        if (j < a.nr) a.acc[static_cast<int64_t>(j) * a.npad + tl.row0 + row] += static_cast<double>(acc[j]);
     }
   }
-  tc_end(ctl, kFTmemCols);
+  ws_teardown(c, produced, mmas, a.status);
 }
 
 // X (caller's order, column-major, ld) -> tree order, fp32, three bf16 slices in
@@ -919,7 +1076,8 @@ cudaError_t launch_tc_prep(const double* x, int64_t ld, int nr, const int32_t* p
 cudaError_t launch_tc(int phase, const TcArgs& a, cudaStream_t st, bool f32) {
   if (a.rp < 16 || a.rp > 128 || (a.rp & 15)) return cudaErrorInvalidValue;
   if (f32) {
-    const size_t smem = (phase == 1 ? kDepth * kF1Stage : kDepth * kF2Stage) + 128 + sizeof(Ctl) + kTcGroupRanks * 12;
+    const size_t smem =
+        (phase == 1 ? kWsDepth * kF1Stage : kWsDepth * kF2Stage) + 128 + sizeof(WsCtl) + kTcGroupRanks * 12;
     if (phase == 1) {
       if (a.n_groups <= 0) return cudaSuccess;
       cudaError_t e = cudaFuncSetAttribute(tc_phase1_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -169,11 +169,19 @@ def timed_loop(torch, H, x, y, steps, ws):
 
 
 def max_over_ranks(torch, v, ws):
+    """The largest of the ranks' values (on the process group's device)."""
     if ws == 1:
         return v
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cpu" if torch.distributed.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(ws, units_per_rank, t_ms_max):
+    """Whole-job throughput of ws independent replicas: every rank processed
+    units_per_rank units; the job took the slowest rank's time."""
+    return ws * units_per_rank / (t_ms_max / 1000.0)
 
 
 def traffic_for(kernel: str, algorithmic_bytes: float):
@@ -295,7 +303,7 @@ def run_ours(args):
     t_64 = max_over_ranks(torch, t_64, ws)
     Ham.sync_status()
     ms_amp, ms_64 = t_amp / args.steps, t_64 / args.steps
-    value = ws * args.steps / (t_amp / 1000.0)
+    value = replica_value(ws, args.steps, t_amp)
     hbm, peak_kind = peaks()
 
     # per-launch device times (CUDA events between the four launches)
@@ -410,7 +418,7 @@ def run_many(args):
     t_ms = max_over_ranks(torch, t_ms, ws)
     H.sync_status()
     ms = t_ms / args.steps
-    value = ws * args.steps * R / (t_ms / 1000.0)
+    value = replica_value(ws, args.steps * R, t_ms)
 
     # per-launch device times of the sequence (CUDA events around every launch)
     nst = max(3, min(args.steps, 20))
@@ -562,7 +570,7 @@ def run_batch(args):
     mats[0].sync_status()
     ms = t_graph / args.steps
     count = len(mats)
-    value = ws * args.steps * count / (t_graph / 1000.0)
+    value = replica_value(ws, args.steps * count, t_graph)
     hbm, peak_kind = peaks()
     gbs = total_bytes / (ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,

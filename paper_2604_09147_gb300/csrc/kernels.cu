@@ -20,18 +20,23 @@ __global__ void prep_kernel(const double* __restrict__ in, int64_t ld, int nr,
                             float* __restrict__ xs, float* __restrict__ xs_lo, double* __restrict__ acc,
                             int* __restrict__ counters) {
   if (counters && blockIdx.x == 0 && threadIdx.x < 2) counters[threadIdx.x] = 0;
-  for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < npad;
-       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  // one gather per tree position q, written into the four copies at q - s
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < npad + 3;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t u = q < n ? static_cast<int64_t>(perm[q]) : -1;
     for (int r = 0; r < nr; ++r) {
+      const double v = u >= 0 ? in[u + r * ld] : 0.0;
+      const float hi = __double2float_rn(v);
+      const float lo = __double2float_rn(v - static_cast<double>(hi));
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        const int64_t q = p + s;
-        const double v = q < n ? in[static_cast<int64_t>(perm[q]) + r * ld] : 0.0;
-        const float hi = __double2float_rn(v);
-        xs[(static_cast<int64_t>(s) * nr + r) * npad + p] = hi;
-        xs_lo[(static_cast<int64_t>(s) * nr + r) * npad + p] = __double2float_rn(v - static_cast<double>(hi));
+        const int64_t p = q - s;
+        if (p >= 0 && p < npad) {
+          xs[(static_cast<int64_t>(s) * nr + r) * npad + p] = hi;
+          xs_lo[(static_cast<int64_t>(s) * nr + r) * npad + p] = lo;
+        }
       }
-      acc[static_cast<int64_t>(r) * npad + p] = 0.0;
+      if (q < npad) acc[static_cast<int64_t>(r) * npad + q] = 0.0;
     }
   }
 }
@@ -49,7 +54,7 @@ __global__ void finish_kernel(const double* __restrict__ acc, int nr, const int3
 
 cudaError_t launch_prep(const double* in, int64_t ld, int nr, const int32_t* perm, int64_t n,
                         int64_t npad, float* xs, float* xs_lo, double* acc, cudaStream_t st, int* counters) {
-  int64_t blocks = (npad + 255) / 256;
+  int64_t blocks = (npad + 3 + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   prep_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(in, ld, nr, perm, n, npad, xs, xs_lo, acc, counters);
   return cudaGetLastError();

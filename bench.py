@@ -495,8 +495,10 @@ def run_many(args):
         "metric": "H_h matvec right-hand sides/s (adaptive precision, many right-hand sides)",
         "value": value, "unit": "rhs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "dtype_note": "fp32 FMA for fp32 factors; tensor-core bf16 slices with fp32 accumulation "
-                                      "for 16/8-bit factors; fp32 pairs for the fp64 dense diagonal; fp64 output",
+        "dtype": "f32", "dtype_note": "tensor cores on bf16 slices with fp32 accumulation (fp32 factors: three "
+                                      "slices, accumulators drained every 32 terms; 16/8-bit factors: two input "
+                                      "slices); CUDA-core fp32 FMA for blocks on unaligned clusters; fp32 pairs for "
+                                      "the fp64 dense diagonal; fp64 output",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "n": n, "nrhs": R, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (%.2f GB of factors and dense blocks per step)"

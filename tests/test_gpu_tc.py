@@ -210,3 +210,24 @@ def test_many_rhs_fp64_matrix(P, tmp_path, nrhs):
         ref = M.matvec_T(O, x) if tr else M.matvec(O, x)
         cols = np.linalg.norm(y - ref, axis=0) / np.linalg.norm(ref, axis=0)
         assert cols.max() <= 1e-12, cols.max()
+
+
+@pytest.mark.parametrize("n,leaf", [(100, 128), (700, 64), (1, 64)])
+def test_many_rhs_tiny_matrices(P, tmp_path, n, leaf):
+    """Matrices with no low-rank block (a single dense block, or one point)
+    and one that is mostly dense: the many-column sequence with empty
+    tensor-core and CUDA-core tables."""
+    from oracle import build as OB
+    pts = W.points(n, 2, 7700 + n)
+    O = OB.build(pts, W.EXP, 1.0, leaf, 1.0, -1, 1e-6, 31)
+    path = str(tmp_path / "t.hhm")
+    hhfile.write(O, path)
+    H = P.HMatrix.load(path, 0)
+    x = W.rhs(n, 33, "uniform", 7800 + n)
+    xg = torch.from_numpy(np.ascontiguousarray(x.T)).cuda().t()
+    for tr in (False, True):
+        y = H.matvec(xg, transpose=tr).cpu().numpy()
+        H.sync_status()
+        ref = M.matvec_T(O, x) if tr else M.matvec(O, x)
+        ab = abs_product(O, x, tr)
+        assert np.linalg.norm(y - ref) <= TOL * np.linalg.norm(ref) + np.linalg.norm(ab)

@@ -18,8 +18,9 @@
  *    The caller owns them; the library never frees or keeps them.
  *  - Matrix-vector calls are asynchronous on the given cudaStream_t (NULL =
  *    the legacy default stream) and never synchronise, allocate or copy to the
- *    host (except the first tensor-core call of a handle, which allocates its
- *    workspace, and hh_matvec_host / hh_matvec_timed, which synchronise);
+ *    host (except the first tensor-core call of a handle in each direction,
+ *    which allocates its workspace and packs its operand panels, and
+ *    hh_matvec_host / hh_matvec_timed, which synchronise);
  *    they overwrite the output (no accumulation).  Input and output must
  *    not overlap.
  *  - A handle owns its host metadata and device arenas; it is immutable after
@@ -106,6 +107,9 @@ typedef struct {
   int32_t blocks_per_sm[4];       /* streaming CTAs per SM chosen by hh_autotune:
                                      {fwd phase 1, fwd phase 2, T phase 1, T phase 2};
                                      0 = the occupancy maximum                       */
+  int64_t tc_panel_bytes[2];      /* device bytes of the tensor-core operand panels
+                                     {forward, transpose}, packed on the first
+                                     tensor-core product in that direction          */
 } hh_info_t;
 
 /*
@@ -168,13 +172,18 @@ int hh_perm(hh_handle h, int32_t* perm);
  * of fp32 halves (about 2^-48 relative, the fp64 path's 1e-12 parity); the
  * output is accumulated in fp64.  With nrhs <= 31 the columns go through the
  * streaming passes in chunks of up to 4.  With nrhs >= 32 (HH_TC_MIN_NRHS in
- * the environment overrides; 0 disables) the fp16, bf16 and e4m3 blocks
- * whose clusters start at multiples of 16 run on the tensor cores in chunks
- * of up to 128 columns (bf16 slices, fp32 accumulation accurate to about
- * 2^-17 of those blocks' products, below their unit roundoff), the other
- * blocks on the streaming passes; the tensor-core workspace is allocated on
- * the first such call (an implicit device synchronisation; HH_ENOMEM if it
- * cannot be).  Uses the handle's workspaces.
+ * the environment overrides; 0 disables) the columns go in chunks of up to
+ * 128 through one pass over the blocks: the fp32, fp16, bf16 and e4m3 blocks
+ * whose clusters start at multiples of 16 on the tensor cores (exact bf16
+ * slices of the factors and of the fp32 input; products kept down to about
+ * 2^-24 for fp32 blocks and below the unit roundoff of the 16- and 8-bit
+ * formats; fp32 accumulation drained every 32 terms), the other 32/16/8-bit
+ * blocks on CUDA-core fp32 kernels, the dense blocks as fp32 pairs, the fp64
+ * low-rank blocks on the streaming passes.  The first such call in each
+ * direction allocates the tensor-core workspace and the factor panels packed
+ * for the tensor cores (hh_info tc_panel_bytes; an implicit device
+ * synchronisation; HH_ENOMEM if they cannot be allocated).  Uses the
+ * handle's workspaces.
  */
 int hh_matvec(hh_handle h, const double* x, double* y, int nrhs, int64_t ldx, int64_t ldy,
               void* stream);

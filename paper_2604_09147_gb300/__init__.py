@@ -52,6 +52,7 @@ class _Info(ctypes.Structure):
         ("tc_u_elems", ctypes.c_int64), ("tc_v_elems", ctypes.c_int64),
         ("mr_u_elems", ctypes.c_int64), ("mr_v_elems", ctypes.c_int64), ("dense_elems", ctypes.c_int64),
         ("tuned", ctypes.c_int32), ("split_positions", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32 * 4),
+        ("tc_panel_bytes", ctypes.c_int64 * 2),
     ]
 
 
@@ -216,6 +217,7 @@ class HMatrix:
         d["factor_bytes_per_fmt"] = {FMT_NAMES[i]: int(s.factor_bytes_per_fmt[i]) for i in range(5)}
         d["csp"] = [int(s.csp[i]) for i in range(s.L + 1)]
         d["blocks_per_sm"] = [int(v) for v in s.blocks_per_sm]
+        d["tc_panel_bytes"] = [int(v) for v in s.tc_panel_bytes]
         return d
 
     def autotune(self, nrhs_many: int = 0) -> dict:

@@ -54,19 +54,21 @@ struct StreamSet {
   std::vector<double> h_cost[2];
 };
 
-// Work tables of the tensor-core path (tc.cu) for one direction.
-// Groups and tiles come in two variants: [0] fp16/bf16/e4m3 pieces, [1] fp32
-// pieces (the kernels with per-stage draining, tc.cu).
+// Work tables of the tensor-core path (tc.cu) for one direction, and the
+// factor panels packed for it (allocated and packed on the first
+// tensor-core product in that direction).
 struct TcSet {
   hh::dev::TcPiece* d_pieces = nullptr;
-  hh::dev::TcGroup* d_groups[2] = {nullptr, nullptr};
-  hh::dev::TcTile* d_tiles[2] = {nullptr, nullptr};
-  hh::dev::TcEntry* d_entries[2] = {nullptr, nullptr};
-  int n_pieces = 0, n_groups[2] = {0, 0}, n_tiles[2] = {0, 0};
+  hh::dev::TcGroup* d_groups = nullptr;
+  hh::dev::TcTile* d_tiles = nullptr;
+  hh::dev::TcEntry* d_entries = nullptr;
+  int n_pieces = 0, n_groups = 0, n_tiles = 0, n_entries = 0;
   int64_t t_bytes = 0;                  // T images of all pieces
   int64_t part_floats = 0;              // partial sums of the split groups
-  int n_cnt = 0;                        // split groups (arrival counters)
+  int n_cnt = 0;                        // arrival counters (four per split group)
   int64_t n_blocks = 0, factor_bytes = 0;
+  int64_t img_bytes = 0;                // packed panels: groups, then entries
+  uint8_t* d_img = nullptr;
 };
 
 // Work tables of the CUDA-core products for many right-hand sides (mr.cu)
@@ -114,6 +116,26 @@ struct hh_matrix {
 
 namespace {
 
+// the many-column tables of one direction (and the packed panels)
+void free_many(hh_matrix* h, int d) {
+  TcSet& ts = h->tc[d];
+  cudaFree(ts.d_pieces);
+  cudaFree(ts.d_groups);
+  cudaFree(ts.d_tiles);
+  cudaFree(ts.d_entries);
+  cudaFree(ts.d_img);
+  MrSet& ms = h->mr[d];
+  cudaFree(ms.d_pieces);
+  cudaFree(ms.d_groups);
+  cudaFree(ms.d_tiles);
+  cudaFree(ms.d_entries);
+  cudaFree(ms.d_dpieces);
+  cudaFree(ms.d_dtiles);
+  cudaFree(ms.d_dentries);
+  ts = TcSet();
+  ms = MrSet();
+}
+
 void free_device(hh_matrix* h) {
   if (h->device < 0) return;
   int cur = -1;
@@ -128,19 +150,7 @@ void free_device(hh_matrix* h) {
       cudaFree(h->ss_rest[d].d_desc[p]);
       cudaFree(h->ss_rest[d].d_items[p]);
     }
-    cudaFree(h->tc[d].d_pieces);
-    for (int v = 0; v < 2; ++v) {
-      cudaFree(h->tc[d].d_groups[v]);
-      cudaFree(h->tc[d].d_tiles[v]);
-      cudaFree(h->tc[d].d_entries[v]);
-    }
-    cudaFree(h->mr[d].d_pieces);
-    cudaFree(h->mr[d].d_groups);
-    cudaFree(h->mr[d].d_tiles);
-    cudaFree(h->mr[d].d_entries);
-    cudaFree(h->mr[d].d_dpieces);
-    cudaFree(h->mr[d].d_dtiles);
-    cudaFree(h->mr[d].d_dentries);
+    free_many(h, d);
   }
   cudaFree(h->d_tc_ws);
   cudaFree(h->d_dense_pad);
@@ -299,13 +309,9 @@ void build_stream_set(hh_matrix* h, int dir, const std::vector<int64_t>& toff, c
 }
 
 // Formats the tensor-core path takes and the most ranks of one piece.
-// fp32 blocks take the variant that drains tensor memory into fp32 registers
-// every stage (the tensor core's accumulation truncates; over a whole
-// contraction that costs about 2^-17 of a block's product, far below the unit
-// roundoff of the 16- and 8-bit formats but not of fp32).
 bool tc_format(int fmt) { return fmt == hh::F32 || fmt == hh::F16 || fmt == hh::BF16 || fmt == hh::E4M3; }
 int tc_piece_cap(int) { return hh::dev::kTcGroupRanks; }
-int tc_input_slices(int fmt) { return fmt == hh::F32 ? 3 : 2; }
+int64_t align128(int64_t v) { return (v + 127) / 128 * 128; }
 
 // A block goes to the tensor cores when its format is one they take and both
 // of its clusters start at a tree position that is a multiple of 16 (the
@@ -316,9 +322,11 @@ bool tc_eligible(const hh::LRBlock& B) {
 
 // Work tables of the tensor-core path for one direction: pieces of at most
 // kTcGroupRanks ranks, grouped by (input cluster, format) into phase-1 groups
-// of at most kTcGroupRanks ranks and split into items of at most
-// kTcSplitPositions positions, and the kTcRows-row output tiles of phase 2
-// with the piece rows that fall in them.
+// of at most kTcGroupRanks ranks and split into items of at most split_len
+// positions, and the kTcRows-row output tiles of phase 2 with the piece rows
+// that fall in them; the byte offsets of every group's and entry's packed
+// panel (16-position blocks x factor slices x nk rows x 32 B; 16-rank steps x
+// factor slices x 4 KB).
 void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
   using namespace hh::dev;
   const hh::HostMatrix& H = h->H;
@@ -385,7 +393,7 @@ void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
         TcPiece q = raw[t].second;
         q.col = g.nk;
         q.toff = toff;
-        toff += int64_t(tc_input_slices(q.fmt)) * (q.kp / 16) * 4096;
+        toff += int64_t(hh::dev::tc_input_slices(q.fmt)) * (q.kp / 16) * 4096;
         g.nk += q.kp;
         g.count += 1;
         pieces.push_back(q);
@@ -393,7 +401,12 @@ void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
       }
       const int nsplit = (g.rows + split_len - 1) / split_len;
       g.nsplit = nsplit;
-      if (nsplit > 1) g.gid = out.n_cnt++;
+      if (nsplit > 1) {
+        g.gid = out.n_cnt / 4;
+        out.n_cnt += 4;
+      }
+      g.img = out.img_bytes;
+      out.img_bytes += align128(int64_t((g.rows + 15) / 16) * hh::dev::tc_factor_slices(g.fmt) * g.nk * 32);
       for (int sp = 0; sp < nsplit; ++sp) {
         TcGroup gs = g;
         gs.split = sp;
@@ -403,60 +416,61 @@ void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
           gs.poff = out.part_floats;
           out.part_floats += int64_t(128) * g.nk;
         }
-        groups.push_back({gs, double(gs.p1 - gs.p0) * g.nk * hh::fmt_bytes(g.fmt)});
+        groups.push_back({gs, double((gs.p1 - gs.p0 + 15) / 16) *
+                                   double(hh::dev::tc_factor_slices(g.fmt) * g.nk * 32 + hh::dev::tc_input_slices(g.fmt) * 4096)});
       }
     }
     i = j;
   }
   std::stable_sort(groups.begin(), groups.end(), [](const CGroup& x, const CGroup& y) { return x.cost > y.cost; });
-  // phase-2 tiles, per variant (the entries of fp32 pieces and of the others)
+  // phase-2 tiles over every piece
   const int64_t ntiles = (H.n + kTcRows - 1) / kTcRows;
-  std::vector<std::vector<TcEntry>> per_tile[2];
-  for (int v = 0; v < 2; ++v) per_tile[v].resize(static_cast<size_t>(ntiles));
+  std::vector<std::vector<TcEntry>> per_tile(static_cast<size_t>(ntiles));
   for (size_t pi = 0; pi < pieces.size(); ++pi) {
     const TcPiece& q = pieces[pi];
-    const int v = q.fmt == hh::F32;
     const int64_t lo = q.out_off, hi = int64_t(q.out_off) + q.rows2;
     for (int64_t t = lo / kTcRows; t * kTcRows < hi; ++t) {
       const int64_t r0 = t * kTcRows, a = std::max(lo, r0), b = std::min(hi, r0 + kTcRows);
-      per_tile[v][t].push_back(TcEntry{(int32_t)pi, (int32_t)(a - lo), (int32_t)(a - r0), (int32_t)(b - a)});
+      per_tile[t].push_back(TcEntry{(int32_t)pi, (int32_t)(a - lo), (int32_t)(a - r0), (int32_t)(b - a), 0});
     }
   }
+  struct CTile {
+    TcTile t;
+    double cost;
+  };
+  std::vector<CTile> tiles;
+  std::vector<TcEntry> entries;
+  for (int64_t t = 0; t < ntiles; ++t) {
+    if (per_tile[t].empty()) continue;
+    TcTile tl;
+    tl.row0 = (int32_t)(t * kTcRows);
+    tl.rows = (int32_t)std::min<int64_t>(kTcRows, H.n - t * kTcRows);
+    tl.first = (int32_t)entries.size();
+    tl.count = (int32_t)per_tile[t].size();
+    double cost = 0;
+    for (TcEntry e : per_tile[t]) {
+      const TcPiece& q = pieces[e.piece];
+      const int64_t step = int64_t(hh::dev::tc_factor_slices(q.fmt)) * 4096;
+      e.img = out.img_bytes;
+      out.img_bytes += (q.kp / 16) * step;
+      entries.push_back(e);
+      cost += double(q.kp / 16) * double(step + hh::dev::tc_input_slices(q.fmt) * 4096);
+    }
+    tiles.push_back({tl, cost});
+  }
+  std::stable_sort(tiles.begin(), tiles.end(), [](const CTile& x, const CTile& y) { return x.cost > y.cost; });
+  std::vector<TcGroup> gflat;
+  for (auto& g : groups) gflat.push_back(g.g);
+  std::vector<TcTile> tflat;
+  for (auto& t : tiles) tflat.push_back(t.t);
   out.d_pieces = upload(pieces);
   out.n_pieces = (int)pieces.size();
-  for (int v = 0; v < 2; ++v) {
-    struct CTile {
-      TcTile t;
-      double cost;
-    };
-    std::vector<CTile> tiles;
-    std::vector<TcEntry> entries;
-    for (int64_t t = 0; t < ntiles; ++t) {
-      if (per_tile[v][t].empty()) continue;
-      TcTile tl;
-      tl.row0 = (int32_t)(t * kTcRows);
-      tl.rows = (int32_t)std::min<int64_t>(kTcRows, H.n - t * kTcRows);
-      tl.first = (int32_t)entries.size();
-      tl.count = (int32_t)per_tile[v][t].size();
-      double cost = 0;
-      for (const TcEntry& e : per_tile[v][t]) {
-        entries.push_back(e);
-        cost += double(pieces[e.piece].kp) * (kTcRows * hh::fmt_bytes(pieces[e.piece].fmt) + 4096.0);
-      }
-      tiles.push_back({tl, cost});
-    }
-    std::stable_sort(tiles.begin(), tiles.end(), [](const CTile& x, const CTile& y) { return x.cost > y.cost; });
-    std::vector<TcGroup> gflat;
-    for (auto& g : groups)
-      if ((g.g.fmt == hh::F32) == (v == 1)) gflat.push_back(g.g);
-    std::vector<TcTile> tflat;
-    for (auto& t : tiles) tflat.push_back(t.t);
-    out.d_groups[v] = upload(gflat);
-    out.d_tiles[v] = upload(tflat);
-    out.d_entries[v] = upload(entries);
-    out.n_groups[v] = (int)gflat.size();
-    out.n_tiles[v] = (int)tflat.size();
-  }
+  out.d_groups = upload(gflat);
+  out.d_tiles = upload(tflat);
+  out.d_entries = upload(entries);
+  out.n_groups = (int)gflat.size();
+  out.n_tiles = (int)tflat.size();
+  out.n_entries = (int)entries.size();
   out.t_bytes = toff;
 }
 
@@ -742,7 +756,7 @@ struct TcWs {
 
 size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
   const int64_t nblk = (h->npad + 15) / 16 + 4;
-  const int64_t tb = std::max(h->tc[0].t_bytes, h->tc[1].t_bytes);
+  const int64_t tb = std::max(h->tc[0].t_bytes, h->tc[1].t_bytes);  // [direction]
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -751,7 +765,7 @@ size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
   };
   const int64_t pf = std::max(h->tc[0].part_floats, h->tc[1].part_floats);
   const int nc = std::max(h->tc[0].n_cnt, h->tc[1].n_cnt);
-  uint8_t* ximg = (uint8_t*)take(size_t(3) * nblk * 4096);  // three bf16 slices
+  uint8_t* ximg = (uint8_t*)take(size_t(3) * nblk * 4096);  // [block][three bf16 slices][4 KB]
   uint8_t* timg = (uint8_t*)take(std::max<size_t>(256, size_t(tb)));
   float* part = (float*)take(sizeof(float) * std::max<int64_t>(64, pf));
   int* cnt = (int*)take(sizeof(int) * std::max(64, nc));
@@ -795,11 +809,12 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   hh::dev::TcArgs a;
   std::memset(&a, 0, sizeof(a));
   a.pieces = ts.d_pieces;
-  a.groups = ts.d_groups[0];
-  a.tiles = ts.d_tiles[0];
-  a.entries = ts.d_entries[0];
-  a.n_groups = ts.n_groups[0];
-  a.n_tiles = ts.n_tiles[0];
+  a.groups = ts.d_groups;
+  a.tiles = ts.d_tiles;
+  a.entries = ts.d_entries;
+  a.n_groups = ts.n_groups;
+  a.n_tiles = ts.n_tiles;
+  a.img = ts.d_img;
   a.nr = nr;
   a.rp = (nr + 15) / 16 * 16;
   a.ximg = t.ximg;
@@ -833,24 +848,16 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   md.entries = ms.d_dentries;
   md.n_groups = 0;
   md.n_tiles = ms.n_dtiles;
-  hh::dev::TcArgs a32 = a;  // the fp32 pieces
-  a32.groups = ts.d_groups[1];
-  a32.tiles = ts.d_tiles[1];
-  a32.entries = ts.d_entries[1];
-  a32.n_groups = ts.n_groups[1];
-  a32.n_tiles = ts.n_tiles[1];
   mark(2);
   if (e == cudaSuccess) e = hh::dev::launch_mr(1, m, st);
   mark(3);
-  if (e == cudaSuccess) e = hh::dev::launch_tc(1, a32, st, true);
-  if (e == cudaSuccess) e = hh::dev::launch_tc(1, a, st);
+  if (e == cudaSuccess) e = hh::dev::launch_tc(1, a, h->sms, st);
   mark(4);
   if (e == cudaSuccess) e = hh::dev::launch_mr(2, m, st);
   mark(5);
   if (e == cudaSuccess) e = hh::dev::launch_mr(3, md, st);
   mark(6);
-  if (e == cudaSuccess) e = hh::dev::launch_tc(2, a32, st, true);
-  if (e == cudaSuccess) e = hh::dev::launch_tc(2, a, st);
+  if (e == cudaSuccess) e = hh::dev::launch_tc(2, a, h->sms, st);
   mark(7);
   if (e == cudaSuccess) e = hh::dev::launch_finish(t.acc, nr, h->d_perm, h->H.n, h->npad, out, ld_out, st);
   mark(8);
@@ -900,6 +907,21 @@ int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, 
       h->tc_ws_bytes = tneed;
     }
     tc_ws_layout(h, &t, (char*)h->d_tc_ws);
+    TcSet& ts = h->tc[dir];
+    if (!ts.d_img && ts.img_bytes > 0) {
+      cudaStreamSynchronize(st);
+      if (cudaMalloc(&ts.d_img, size_t(ts.img_bytes)) != cudaSuccess) {
+        ts.d_img = nullptr;
+        if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+        return fail(HH_ENOMEM, "cannot allocate the packed tensor-core panels");
+      }
+      const cudaError_t pe = hh::dev::launch_tc_pack(ts.d_pieces, ts.d_groups, ts.n_groups, ts.d_entries,
+                                                     ts.n_entries, ts.d_img, st);
+      if (pe != cudaSuccess) {
+        if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+        return fail(HH_ECUDA, std::string("panel packing failed: ") + cudaGetErrorString(pe));
+      }
+    }
   }
   for (int rb = 0; rb < nrhs;) {
     const int rem = nrhs - rb;
@@ -930,21 +952,7 @@ int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, 
 // handle's current split length.
 void rebuild_many(hh_matrix* h) {
   for (int d = 0; d < 2; ++d) {
-    cudaFree(h->tc[d].d_pieces);
-    for (int v = 0; v < 2; ++v) {
-      cudaFree(h->tc[d].d_groups[v]);
-      cudaFree(h->tc[d].d_tiles[v]);
-      cudaFree(h->tc[d].d_entries[v]);
-    }
-    cudaFree(h->mr[d].d_pieces);
-    cudaFree(h->mr[d].d_groups);
-    cudaFree(h->mr[d].d_tiles);
-    cudaFree(h->mr[d].d_entries);
-    cudaFree(h->mr[d].d_dpieces);
-    cudaFree(h->mr[d].d_dtiles);
-    cudaFree(h->mr[d].d_dentries);
-    h->tc[d] = TcSet();
-    h->mr[d] = MrSet();
+    free_many(h, d);
     build_tc_set(h, d, h->tc[d]);
     build_mr_set(h, d, h->doff, h->dexp, h->mr[d]);
   }
@@ -1122,6 +1130,7 @@ int hh_info(hh_handle h, hh_info_t* o) {
   o->split_positions = h->split_len;
   for (int d = 0; d < 2; ++d)
     for (int p = 1; p <= 2; ++p) o->blocks_per_sm[2 * d + p - 1] = h->blocks_per_sm[d][p];
+  for (int d = 0; d < 2; ++d) o->tc_panel_bytes[d] = h->device >= 0 ? h->tc[d].img_bytes : 0;
   return HH_OK;
 }
 

@@ -85,7 +85,7 @@ struct TcPiece {
   const uint8_t* f1;
   const uint8_t* f2;
   int64_t ld1, ld2;
-  int64_t toff;        // byte offset of the piece's T image: [slice][k-step][128 rows x 32 B]
+  int64_t toff;        // byte offset of the piece's T image: [k-step][slice][128 rows x 32 B]
   int32_t rows1, rows2;
   int32_t in_off, out_off;
   int32_t k, kp;       // ranks, ranks rounded up to 16
@@ -95,24 +95,31 @@ struct TcPiece {
 };
 // phase-1 item: positions [p0, p1) of the input cluster [in_off, in_off + rows)
 // for the pieces [first, first + count) of one format (nk = sum of their kp,
-// at most kTcGroupRanks).  A group whose cluster is longer than
-// kTcSplitPositions is split into nsplit items; each writes its partial sums
-// to part + poff (fp32 [128][nk]) and the last to finish (counter cnt[gid])
-// adds them in split order and writes the T images.
+// at most kTcGroupRanks).  img: byte offset of the group's packed operand
+// panel, [16-position block][slice][nk rows x 32 B] (all items of a group
+// share it).  A group whose cluster is longer than the split length is split
+// into nsplit items; each writes its partial sums to part + poff (fp32
+// [128][nk]), and for each quarter of the right-hand sides the last item to
+// finish (counter cnt[4 gid + quarter]) adds them in split order and writes
+// the T images.
 struct TcGroup {
   int32_t first, count, nk, fmt;
   int32_t in_off, rows, p0, p1;
   int32_t nsplit, split, gid, pad;
   int64_t poff;
+  int64_t img;
 };
 // phase-2 item: output rows [row0, row0 + rows) (row0 a multiple of kTcRows)
 // and entries [first, first + count)
 struct TcTile {
   int32_t row0, rows, first, count;
 };
-// rows [src, src + nrows) of a piece's output cluster land on tile rows [dst, dst + nrows)
+// rows [src, src + nrows) of a piece's output cluster land on tile rows
+// [dst, dst + nrows); img: byte offset of the entry's packed operand panel
+// [k-step][slice][128 tile rows x 32 B] (tensor-core path only)
 struct TcEntry {
   int32_t piece, src, dst, nrows;
+  int64_t img;
 };
 struct TcArgs {
   const TcPiece* pieces;
@@ -121,8 +128,9 @@ struct TcArgs {
   const TcEntry* entries;
   int32_t n_groups, n_tiles;
   int32_t nr, rp;        // right-hand sides of this launch (<= 128), nr rounded up to 16
-  const uint8_t* ximg;   // input image [3][nblk][128 rows x 32 B] (tc prep)
+  const uint8_t* ximg;   // input image [nblk][3 slices][128 rows x 32 B] (tc prep)
   int64_t nblk;
+  const uint8_t* img;    // packed factor panels (groups, then entries)
   uint8_t* timg;         // T images of the pieces
   float* part;           // partial sums of split groups
   int* cnt;              // arrival counters of split groups (cleared by the prep launch)
@@ -134,12 +142,18 @@ struct TcArgs {
 constexpr int kTcMaxRhs = 128;          // right-hand sides per tensor-core launch sequence
 constexpr int kTcRows = 128;            // phase-2 tile rows
 constexpr int kTcGroupRanks = 128;      // ranks of one phase-1 group
-constexpr int kTcSplitPositions = 1024; // positions of one phase-1 item
+constexpr int kTcSplitPositions = 1024; // positions of one phase-1 item (default)
+// bf16 slices per element: factor panels (fp32 3, fp16 2, bf16 / e4m3 1),
+// input and T images (fp32 pieces 3, the others 2)
+inline __host__ __device__ int tc_factor_slices(int fmt) { return fmt == 1 ? 3 : (fmt == 2 ? 2 : 1); }
+inline __host__ __device__ int tc_input_slices(int fmt) { return fmt == 1 ? 3 : 2; }
 cudaError_t launch_tc_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t nblk,
                            uint8_t* ximg, double* acc, int64_t npad, int* cnt, int n_cnt, cudaStream_t st);
-// f32: the kernels for fp32 pieces (groups / tiles of fp32 pieces only)
-cudaError_t launch_tc(int phase, const TcArgs& a, cudaStream_t st, bool f32 = false);
-size_t tc_smem_bytes(int phase);
+// packs the factor panels of a set's groups (phase 1) and entries (phase 2) into img
+cudaError_t launch_tc_pack(const TcPiece* pieces, const TcGroup* groups, int n_groups, const TcEntry* entries,
+                           int n_entries, uint8_t* img, cudaStream_t st);
+// phase 1 or 2 over every group / tile; grid: persistent CTAs (<= SMs)
+cudaError_t launch_tc(int phase, const TcArgs& a, int grid, cudaStream_t st);
 
 // ---- CUDA-core products for many right-hand sides (mr.cu) ----
 // Work lists in the tensor-core structures: phase-1 groups of at most

@@ -124,6 +124,12 @@ def test_oracle_written_file_roundtrips_through_library(P, tmp_path):
     assert inf["n_lowrank"] == len(O.lowrank) and inf["n_dense"] == len(O.dense)
     assert inf["storage_amp"] == pytest.approx(O.storage(), rel=1e-12)
     assert inf["storage_fp64"] == pytest.approx(O.storage(True), rel=1e-12)
+    # the trailing fields of hh_info_t (their offsets in the Python mirror)
+    tc = [b for b in O.lowrank if b.k > 0 and b.fmt in (1, 2, 3, 4) and b.row_off % 16 == 0 and b.col_off % 16 == 0]
+    assert inf["tc_blocks"] == len(tc)
+    assert inf["tc_v_elems"] == sum(b.n * b.k for b in tc) and inf["tc_u_elems"] == sum(b.m * b.k for b in tc)
+    assert inf["dense_elems"] == sum(d.m * d.n for d in O.dense)
+    assert inf["tuned"] == 0 and inf["split_positions"] == 1024 and inf["tc_panel_bytes"] == [0, 0]
 
 
 def test_reencode_equals_direct_build(P, tmp_path):

@@ -38,11 +38,14 @@
 //
 // Kernels.  Both phases are persistent and warp-specialized, one CTA per SM
 // (192 threads, ~193 KB of shared memory, all 512 tensor-memory columns):
-//   warp 0     lane 0 fills a kDepth-deep ring of 24 KB stages with two bulk
-//              copies each (input or T slices, factor panel slices);
+//   warp 0     lane 0 fills a 4-deep ring of 48 KB stages, two K steps each,
+//              with bulk copies (input or T slices, factor panel slices);
 //   warp 1     lane 0 issues the MMAs of a stage once its copies landed and,
 //              for a chunk's first stage, once its bank has been drained;
-//              tcgen05.commit frees the stage and hands a bank over;
+//              tcgen05.commit frees the stage and hands a bank over (an MMA
+//              instruction costs its issuing thread tens of cycles whatever
+//              its size, so a stage carries two K steps and the descriptors
+//              are advanced by additions);
 //   warps 2-5  drain the banks (tensor-memory lane quarter w mod 4) into fp32
 //              registers and write each item's result.
 // Items are cost-sorted on the host and dealt to the CTAs in snake order;
@@ -66,25 +69,25 @@ namespace {
 
 constexpr long long kWaitCycles = 4000000000LL;
 constexpr int kThreads = 192;
-constexpr int kDepth = 8;
-constexpr int kOpA = 3 * 4096;           // phase 1: X slices [3][128 x 32 B]; phase 2: U slices [3][128 x 32 B]
-constexpr int kOpB = 3 * 4096;           // phase 1: V slices [3][nk x 32 B];  phase 2: T slices [3][rp x 32 B]
+constexpr int kKS = 2;                   // K steps per stage
+constexpr int kDepth = 4;
+// a stage: kKS K steps of the A operand (phase 1: X slices [3][128 x 32 B]
+// per step; phase 2: U slices [sf][128 x 32 B] per step), then kKS K steps of
+// the B operand (phase 1: V slices [sf][nk x 32 B]; phase 2: T slices
+// [sx][rp x 32 B])
+constexpr int kOpA = kKS * 3 * 4096;
+constexpr int kOpB = kKS * 3 * 4096;
 constexpr int kStage = kOpA + kOpB;
 constexpr uint32_t kTmemCols = 512;      // bank b: main at 256 b, corrections at 256 b + 128
-// K steps that add into one bank before it is drained.  Each MMA's addition
-// into an fp32 accumulator truncates (at most one unit in the last place of
-// the running sum), so over L steps the error is at most about L * 2^-24 of
-// the absolute sum of the chunk's products: fp32 pieces use L = 4 (2^-22,
-// below what their 2^-24 unit roundoff and the three-slice products leave),
-// the 16- and 8-bit pieces L = 32 (2^-19, far below their unit roundoff).
-#ifndef HH_TC_CHUNK_F32
-#define HH_TC_CHUNK_F32 4
-#endif
-#ifndef HH_TC_CHUNK_16
-#define HH_TC_CHUNK_16 32
-#endif
-constexpr int kChunkF32 = HH_TC_CHUNK_F32;
-constexpr int kChunk16 = HH_TC_CHUNK_16;
+// Stages whose K steps add into one bank before it is drained.  Each MMA's
+// addition into an fp32 accumulator truncates (at most one unit in the last
+// place of the running sum), so over n steps the error is at most about
+// n * 2^-24 of the absolute sum of the chunk's products: fp32 pieces drain
+// after 2 stages (4 steps: 2^-22, below what their 2^-24 unit roundoff and
+// the three-slice products leave), the 16- and 8-bit pieces after 16 (32
+// steps: 2^-19, far below their unit roundoff).
+constexpr int kChunkF32 = 2;
+constexpr int kChunk16 = 16;
 
 constexpr int kF32 = 1, kF16 = 2, kBF16 = 3, kE4M3 = 4;
 
@@ -119,6 +122,34 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint3
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// The np products of one K step into the bank at tmem (main at +0, corrections
+// at +128).  Descriptors are advanced by adding to the start-address field
+// (bits 0-13, address / 16): da / db address slice 0 of the A and B operands,
+// a_step / b_step are the slice strides / 16.  Phase 1: A = input slices
+// fpx(p), B = factor slices fpf(p); phase 2: A = factor slices, B = input
+// (T) slices.  acc0: whether the main and first correction products add to
+// the bank (later corrections always do).
+template <int NP, bool PH2>
+__device__ __forceinline__ void issue_products(uint32_t tmem, uint64_t da, uint64_t db, uint32_t a_step,
+                                               uint32_t b_step, uint32_t idesc, uint32_t acc0) {
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int ia = PH2 ? fpf(p) : fpx(p), ib = PH2 ? fpx(p) : fpf(p);
+    mma(tmem + (p ? 128 : 0), da + ia * a_step, db + ib * b_step, idesc, p >= 2 ? 1u : acc0);
+  }
+}
+
+template <bool PH2>
+__device__ __forceinline__ void issue_step(int np, uint32_t tmem, uint64_t da, uint64_t db, uint32_t a_step,
+                                           uint32_t b_step, uint32_t idesc, uint32_t acc0) {
+  if (np == 6)
+    issue_products<6, PH2>(tmem, da, db, a_step, b_step, idesc, acc0);
+  else if (np == 3)
+    issue_products<3, PH2>(tmem, da, db, a_step, b_step, idesc, acc0);
+  else
+    issue_products<2, PH2>(tmem, da, db, a_step, b_step, idesc, acc0);
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -350,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
         const TcGroup g = a.groups[it];
         const uint32_t xbytes = tc_input_slices(g.fmt) * 4096u;
         const uint32_t vbytes = tc_factor_slices(g.fmt) * static_cast<uint32_t>(g.nk) * 32u;
-        const int nst = (g.p1 - g.p0 + 15) >> 4;
+        const int nblk = (g.p1 - g.p0 + 15) >> 4, nst = (nblk + kKS - 1) / kKS;
         for (int i = 0; i < nst; ++i, ++gs) {
           const int s = gs % kDepth;
           if (gs >= kDepth && !ws_wait(&c->empty[s], ((gs / kDepth) - 1) & 1, abort)) {
@@ -358,53 +389,62 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
             break;
           }
           uint8_t* st = base + s * kStage;
-          const int p = g.p0 + 16 * i;  // position in the cluster (a multiple of 16)
-          const int64_t blk = (static_cast<int64_t>(g.in_off) + p) >> 4;
-          mbar_expect_tx(&c->full[s], xbytes + vbytes);
-          bulk_copy(st, a.ximg + blk * (3 * 4096), xbytes, &c->full[s]);
-          bulk_copy_once(st + kOpA, a.img + g.img + static_cast<int64_t>(p >> 4) * vbytes, vbytes, &c->full[s],
-                         pol);
+          // 16-position blocks b0 .. b0 + nb - 1 of the cluster
+          const int b0 = (g.p0 >> 4) + kKS * i, nb = min(kKS, nblk - kKS * i);
+          const int64_t blk = (static_cast<int64_t>(g.in_off) >> 4) + b0;
+          mbar_expect_tx(&c->full[s], nb * (xbytes + vbytes));
+          for (int t = 0; t < nb; ++t) bulk_copy(st + t * (3 * 4096), a.ximg + (blk + t) * (3 * 4096), xbytes, &c->full[s]);
+          bulk_copy_once(st + kOpA, a.img + g.img + static_cast<int64_t>(b0) * vbytes, nb * vbytes, &c->full[s], pol);
           produced = gs + 1;
         }
       }
     }
   } else if (w == 1) {  // MMA issuer
     if (lane == 0) {
+      const uint64_t d0 = op_desc(base);
       int gs = 0, gp = 0;
       bool ok = true;
       for (int k = 0; ok; ++k) {
         const int it = item_of(k, a.n_groups);
         if (it < 0) break;
         const TcGroup g = a.groups[it];
-        const int np = n_products(g.fmt), nst = (g.p1 - g.p0 + 15) >> 4, L = chunk_of(g.fmt);
-        const uint32_t idesc = idesc_bf16(g.nk), vstride = static_cast<uint32_t>(g.nk) * 32u;
-        for (int i = 0; i < nst; ++i, ++gs) {
+        const int np = n_products(g.fmt), nblk = (g.p1 - g.p0 + 15) >> 4, nst = (nblk + kKS - 1) / kKS;
+        const int L = chunk_of(g.fmt);
+        const uint32_t idesc = idesc_bf16(g.nk), vstep = static_cast<uint32_t>(g.nk) * 2u;
+        const uint32_t vstage = tc_factor_slices(g.fmt) * vstep;  // V bytes of one K step / 16
+        int s = gs % kDepth, par = (gs / kDepth) & 1;
+        for (int i = 0, j = 0; i < nst; ++i, ++gs) {
           // chunks of L stages alternate between the banks: a chunk's first
-          // stage starts fresh accumulators, the others add to them, then
+          // K step starts fresh accumulators, the others add to them, then
           // the bank is handed to the drain warps
-          const int s = gs % kDepth, j = i % L, second = j != 0, b = gp & 1;
-          if (!ws_wait(&c->full[s], (gs / kDepth) & 1, abort)) {
+          const int b = gp & 1;
+          if (!ws_wait(&c->full[s], par, abort)) {
             ok = false;
             break;
           }
-          if (!second && gp >= 2 && !ws_wait(&c->bempty[b], ((gp >> 1) - 1) & 1, abort)) {
-            ok = false;
-            break;
+          if (j == 0) {
+            if (gp >= 2 && !ws_wait(&c->bempty[b], ((gp >> 1) - 1) & 1, abort)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          uint8_t* st = base + s * kStage;
-          const uint32_t tb = c->tmem + 256 * b;
-          for (int q = 0; q < np; ++q) {
-            const uint64_t da = op_desc(st + fpx(q) * 4096);
-            const uint64_t db = op_desc(st + kOpA + fpf(q) * vstride);
-            mma(tb + (q ? 128 : 0), da, db, idesc, (q >= 2 || second) ? 1u : 0u);
-          }
+          const uint64_t da = d0 + static_cast<uint32_t>(s * (kStage >> 4));
+          const int nb = min(kKS, nblk - kKS * i);
+          for (int t = 0; t < nb; ++t)
+            issue_step<false>(np, c->tmem + 256 * b, da + t * (3 * 256), da + (kOpA >> 4) + t * vstage, 256u, vstep,
+                              idesc, (j != 0 || t != 0));
           mma_commit(&c->empty[s]);
-          if (j == L - 1 || i == nst - 1) {
+          if (++j == L || i == nst - 1) {
             mma_commit(&c->bfull[b]);
             ++gp;
+            j = 0;
           }
           mmas = gs + 1;
+          if (++s == kDepth) {
+            s = 0;
+            par ^= 1;
+          }
         }
       }
     }
@@ -417,7 +457,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
       const int it = item_of(k, a.n_groups);
       if (it < 0) break;
       const TcGroup g = a.groups[it];
-      const int L = chunk_of(g.fmt), nk = g.nk, nchunks = (((g.p1 - g.p0 + 15) >> 4) + L - 1) / L;
+      const int L = chunk_of(g.fmt), nk = g.nk, nst = (((g.p1 - g.p0 + 15) >> 4) + kKS - 1) / kKS;
+      const int nchunks = (nst + L - 1) / L;
 #pragma unroll
       for (int j = 0; j < 128; ++j) acc[j] = 0.f;
       for (int q = 0; q < nchunks; ++q, ++gp) {
@@ -496,7 +537,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
   volatile int* abort = &c->abort;
   int produced = 0, mmas = 0;
 
-  if (w == 0) {  // producer: U panel slices and T slices of one 16-rank step
+  if (w == 0) {  // producer: U panel slices and T slices of up to kKS 16-rank steps of one entry
     if (lane == 0) {
       const uint64_t pol = evict_first();
       int gs = 0;
@@ -510,16 +551,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
           const TcPiece& q = a.pieces[en.piece];
           const uint32_t ub = tc_factor_slices(q.fmt) * 4096u, tb = tc_input_slices(q.fmt) * 4096u;
           const int nks = q.kp >> 4;
-          for (int ks = 0; ks < nks; ++ks, ++gs) {
-            const int s = gs % kDepth;
+          for (int ks = 0; ks < nks; ks += kKS, ++gs) {
+            const int s = gs % kDepth, nb = min(kKS, nks - ks);
             if (gs >= kDepth && !ws_wait(&c->empty[s], ((gs / kDepth) - 1) & 1, abort)) {
               ok = false;
               break;
             }
             uint8_t* st = base + s * kStage;
-            mbar_expect_tx(&c->full[s], ub + tb);
-            bulk_copy_once(st, a.img + en.img + static_cast<int64_t>(ks) * ub, ub, &c->full[s], pol);
-            bulk_copy(st + kOpA, a.timg + q.toff + static_cast<int64_t>(ks) * tb, tb, &c->full[s]);
+            mbar_expect_tx(&c->full[s], nb * (ub + tb));
+            bulk_copy_once(st, a.img + en.img + static_cast<int64_t>(ks) * ub, nb * ub, &c->full[s], pol);
+            bulk_copy(st + kOpA, a.timg + q.toff + static_cast<int64_t>(ks) * tb, nb * tb, &c->full[s]);
             produced = gs + 1;
           }
         }
@@ -528,6 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
   } else if (w == 1) {  // MMA issuer
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(rp);
+      const uint64_t d0 = op_desc(base);
       int gs = 0, gp = 0;
       bool ok = true;
       for (int k = 0; ok; ++k) {
@@ -537,37 +579,43 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
         int nst = 0, L = kChunk16;
         for (int e = 0; e < tl.count; ++e) {
           const TcPiece& q = a.pieces[a.entries[tl.first + e].piece];
-          nst += q.kp >> 4;
+          nst += ((q.kp >> 4) + kKS - 1) / kKS;
           L = min(L, chunk_of(q.fmt));
         }
-        int i = 0;
+        int i = 0, j = 0, s = gs % kDepth, par = (gs / kDepth) & 1;
         for (int e = 0; e < tl.count && ok; ++e) {
           const TcPiece& q = a.pieces[a.entries[tl.first + e].piece];
           const int np = n_products(q.fmt), nks = q.kp >> 4;
-          for (int ks = 0; ks < nks; ++ks, ++i, ++gs) {
-            const int s = gs % kDepth, second = (i % L) != 0, b = gp & 1;
-            if (!ws_wait(&c->full[s], (gs / kDepth) & 1, abort)) {
+          const uint32_t ustep = tc_factor_slices(q.fmt) * 256u, tstep = tc_input_slices(q.fmt) * 256u;
+          for (int ks = 0; ks < nks; ks += kKS, ++i, ++gs) {
+            const int b = gp & 1;
+            if (!ws_wait(&c->full[s], par, abort)) {
               ok = false;
               break;
             }
-            if (!second && gp >= 2 && !ws_wait(&c->bempty[b], ((gp >> 1) - 1) & 1, abort)) {
-              ok = false;
-              break;
+            if (j == 0) {
+              if (gp >= 2 && !ws_wait(&c->bempty[b], ((gp >> 1) - 1) & 1, abort)) {
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint8_t* st = base + s * kStage;
-            const uint32_t tb = c->tmem + 256 * b;
-            for (int p = 0; p < np; ++p) {
-              const uint64_t da = op_desc(st + fpf(p) * 4096);
-              const uint64_t db = op_desc(st + kOpA + fpx(p) * 4096);
-              mma(tb + (p ? 128 : 0), da, db, idesc, (p >= 2 || second) ? 1u : 0u);
-            }
+            const uint64_t da = d0 + static_cast<uint32_t>(s * (kStage >> 4));
+            const int nb = min(kKS, nks - ks);
+            for (int t = 0; t < nb; ++t)
+              issue_step<true>(np, c->tmem + 256 * b, da + t * ustep, da + (kOpA >> 4) + t * tstep, 256u, 256u, idesc,
+                               (j != 0 || t != 0));
             mma_commit(&c->empty[s]);
-            if (i % L == L - 1 || i == nst - 1) {
+            if (++j == L || i == nst - 1) {
               mma_commit(&c->bfull[b]);
               ++gp;
+              j = 0;
             }
             mmas = gs + 1;
+            if (++s == kDepth) {
+              s = 0;
+              par ^= 1;
+            }
           }
         }
       }
@@ -584,7 +632,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
       int nst = 0, L = kChunk16;
       for (int e = 0; e < tl.count; ++e) {
         const TcPiece& q = a.pieces[a.entries[tl.first + e].piece];
-        nst += q.kp >> 4;
+        nst += ((q.kp >> 4) + kKS - 1) / kKS;
         L = min(L, chunk_of(q.fmt));
       }
 #pragma unroll

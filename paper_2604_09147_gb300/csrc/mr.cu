@@ -341,7 +341,7 @@ __device__ __forceinline__ void dd_fma(float& S, float& C, float ah, float al, f
 }
 
 template <int RPT>
-__global__ void __launch_bounds__(kThreads) mr_dense(MrArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) mr_dense(MrArgs a) {
   constexpr int RP = 16 * RPT;
   extern __shared__ __align__(16) float sm3[];
   float* sDh = sm3;                              // [2][kK2][64]

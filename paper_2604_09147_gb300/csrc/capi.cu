@@ -431,7 +431,8 @@ void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
     const int64_t lo = q.out_off, hi = int64_t(q.out_off) + q.rows2;
     for (int64_t t = lo / kTcRows; t * kTcRows < hi; ++t) {
       const int64_t r0 = t * kTcRows, a = std::max(lo, r0), b = std::min(hi, r0 + kTcRows);
-      per_tile[t].push_back(TcEntry{(int32_t)pi, (int32_t)(a - lo), (int32_t)(a - r0), (int32_t)(b - a), 0});
+      per_tile[t].push_back(
+          TcEntry{(int32_t)pi, (int32_t)(a - lo), (int32_t)(a - r0), (int32_t)(b - a), 0, q.toff, q.kp / 16, q.fmt});
     }
   }
   struct CTile {
@@ -442,11 +443,13 @@ void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
   std::vector<TcEntry> entries;
   for (int64_t t = 0; t < ntiles; ++t) {
     if (per_tile[t].empty()) continue;
-    TcTile tl;
+    TcTile tl{};
     tl.row0 = (int32_t)(t * kTcRows);
     tl.rows = (int32_t)std::min<int64_t>(kTcRows, H.n - t * kTcRows);
     tl.first = (int32_t)entries.size();
     tl.count = (int32_t)per_tile[t].size();
+    tl.nst = 0;
+    tl.chunk = kTcChunk16;
     double cost = 0;
     for (TcEntry e : per_tile[t]) {
       const TcPiece& q = pieces[e.piece];
@@ -454,6 +457,8 @@ void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
       e.img = out.img_bytes;
       out.img_bytes += (q.kp / 16) * step;
       entries.push_back(e);
+      tl.nst += (q.kp / 16 + kTcKSteps - 1) / kTcKSteps;
+      tl.chunk = std::min(tl.chunk, q.fmt == hh::F32 ? kTcChunkF32 : kTcChunk16);
       cost += double(q.kp / 16) * double(step + hh::dev::tc_input_slices(q.fmt) * 4096);
     }
     tiles.push_back({tl, cost});
@@ -494,7 +499,7 @@ void build_tiles(int64_t n, int rows, const std::vector<hh::dev::TcPiece>& piece
   std::vector<std::pair<TcTile, double>> tiles;
   for (int64_t t = 0; t < ntiles; ++t) {
     if (per_tile[t].empty()) continue;
-    TcTile tl;
+    TcTile tl{};
     tl.row0 = (int32_t)(t * rows);
     tl.rows = (int32_t)std::min<int64_t>(rows, n - t * rows);
     tl.first = (int32_t)entries.size();

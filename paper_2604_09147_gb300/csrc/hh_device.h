@@ -110,16 +110,22 @@ struct TcGroup {
   int64_t img;
 };
 // phase-2 item: output rows [row0, row0 + rows) (row0 a multiple of kTcRows)
-// and entries [first, first + count)
+// and entries [first, first + count); tensor-core path: nst stages of up to
+// kTcKSteps K steps, accumulators drained every `chunk` stages
 struct TcTile {
   int32_t row0, rows, first, count;
+  int32_t nst, chunk;
 };
 // rows [src, src + nrows) of a piece's output cluster land on tile rows
-// [dst, dst + nrows); img: byte offset of the entry's packed operand panel
-// [k-step][slice][128 tile rows x 32 B] (tensor-core path only)
+// [dst, dst + nrows).  Tensor-core path: img, byte offset of the entry's
+// packed operand panel [k-step][slice][128 tile rows x 32 B]; toff, nks, fmt:
+// the piece's T image offset, K steps and format (so that a stage needs no
+// second lookup)
 struct TcEntry {
   int32_t piece, src, dst, nrows;
   int64_t img;
+  int64_t toff;
+  int32_t nks, fmt;
 };
 struct TcArgs {
   const TcPiece* pieces;
@@ -143,6 +149,11 @@ constexpr int kTcMaxRhs = 128;          // right-hand sides per tensor-core laun
 constexpr int kTcRows = 128;            // phase-2 tile rows
 constexpr int kTcGroupRanks = 128;      // ranks of one phase-1 group
 constexpr int kTcSplitPositions = 1024; // positions of one phase-1 item (default)
+constexpr int kTcKSteps = 2;            // K steps (16 positions or ranks) per pipeline stage
+// stages whose K steps add into one tensor-memory bank before it is drained
+// (fp32 pieces; the 16- and 8-bit pieces)
+constexpr int kTcChunkF32 = 2;
+constexpr int kTcChunk16 = 16;
 // bf16 slices per element: factor panels (fp32 3, fp16 2, bf16 / e4m3 1),
 // input and T images (fp32 pieces 3, the others 2)
 inline __host__ __device__ int tc_factor_slices(int fmt) { return fmt == 1 ? 3 : (fmt == 2 ? 2 : 1); }

@@ -69,7 +69,7 @@ namespace {
 
 constexpr long long kWaitCycles = 4000000000LL;
 constexpr int kThreads = 192;
-constexpr int kKS = 2;                   // K steps per stage
+constexpr int kKS = kTcKSteps;           // K steps per stage
 constexpr int kDepth = 4;
 // a stage: kKS K steps of the A operand (phase 1: X slices [3][128 x 32 B]
 // per step; phase 2: U slices [sf][128 x 32 B] per step), then kKS K steps of
@@ -79,15 +79,16 @@ constexpr int kOpA = kKS * 3 * 4096;
 constexpr int kOpB = kKS * 3 * 4096;
 constexpr int kStage = kOpA + kOpB;
 constexpr uint32_t kTmemCols = 512;      // bank b: main at 256 b, corrections at 256 b + 128
-// Stages whose K steps add into one bank before it is drained.  Each MMA's
-// addition into an fp32 accumulator truncates (at most one unit in the last
-// place of the running sum), so over n steps the error is at most about
-// n * 2^-24 of the absolute sum of the chunk's products: fp32 pieces drain
-// after 2 stages (4 steps: 2^-22, below what their 2^-24 unit roundoff and
-// the three-slice products leave), the 16- and 8-bit pieces after 16 (32
-// steps: 2^-19, far below their unit roundoff).
-constexpr int kChunkF32 = 2;
-constexpr int kChunk16 = 16;
+// Stages whose K steps add into one bank before it is drained
+// (kTcChunkF32 / kTcChunk16).  Each MMA's addition into an fp32 accumulator
+// truncates (at most one unit in the last place of the running sum), so over
+// n steps the error is at most about n * 2^-24 of the absolute sum of the
+// chunk's products: fp32 pieces drain after 2 stages (4 steps: 2^-22, below
+// what their 2^-24 unit roundoff and the three-slice products leave), the
+// 16- and 8-bit pieces after 16 (32 steps: 2^-19, far below their unit
+// roundoff).
+constexpr int kChunkF32 = kTcChunkF32;
+constexpr int kChunk16 = kTcChunk16;
 
 constexpr int kF32 = 1, kF16 = 2, kBF16 = 3, kE4M3 = 4;
 
@@ -375,10 +376,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
       const uint64_t pol = evict_first();
       int gs = 0;
       bool ok = true;
-      for (int k = 0; ok; ++k) {
-        const int it = item_of(k, a.n_groups);
-        if (it < 0) break;
-        const TcGroup g = a.groups[it];
+      int itn = item_of(0, a.n_groups);
+      TcGroup gn{};
+      if (itn >= 0) gn = a.groups[itn];  // the next item, loaded one ahead
+      for (int k = 0; ok && itn >= 0; ++k) {
+        const TcGroup g = gn;
+        itn = item_of(k + 1, a.n_groups);
+        if (itn >= 0) gn = a.groups[itn];
         const uint32_t xbytes = tc_input_slices(g.fmt) * 4096u;
         const uint32_t vbytes = tc_factor_slices(g.fmt) * static_cast<uint32_t>(g.nk) * 32u;
         const int nblk = (g.p1 - g.p0 + 15) >> 4, nst = (nblk + kKS - 1) / kKS;
@@ -404,10 +408,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
       const uint64_t d0 = op_desc(base);
       int gs = 0, gp = 0;
       bool ok = true;
-      for (int k = 0; ok; ++k) {
-        const int it = item_of(k, a.n_groups);
-        if (it < 0) break;
-        const TcGroup g = a.groups[it];
+      int itn = item_of(0, a.n_groups);
+      TcGroup gn{};
+      if (itn >= 0) gn = a.groups[itn];  // the next item, loaded one ahead
+      for (int k = 0; ok && itn >= 0; ++k) {
+        const TcGroup g = gn;
+        itn = item_of(k + 1, a.n_groups);
+        if (itn >= 0) gn = a.groups[itn];
         const int np = n_products(g.fmt), nblk = (g.p1 - g.p0 + 15) >> 4, nst = (nblk + kKS - 1) / kKS;
         const int L = chunk_of(g.fmt);
         const uint32_t idesc = idesc_bf16(g.nk), vstep = static_cast<uint32_t>(g.nk) * 2u;
@@ -453,10 +460,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
     float acc[128];
     int gp = 0;
     bool ok = true;
-    for (int k = 0; ok; ++k) {
-      const int it = item_of(k, a.n_groups);
-      if (it < 0) break;
-      const TcGroup g = a.groups[it];
+    int itn = item_of(0, a.n_groups);
+    TcGroup gn{};
+    if (itn >= 0) gn = a.groups[itn];
+    for (int k = 0; ok && itn >= 0; ++k) {
+      const TcGroup g = gn;
+      itn = item_of(k + 1, a.n_groups);
+      if (itn >= 0) gn = a.groups[itn];
       const int L = chunk_of(g.fmt), nk = g.nk, nst = (((g.p1 - g.p0 + 15) >> 4) + kKS - 1) / kKS;
       const int nchunks = (nst + L - 1) / L;
 #pragma unroll
@@ -542,15 +552,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
       const uint64_t pol = evict_first();
       int gs = 0;
       bool ok = true;
-      for (int k = 0; ok; ++k) {
-        const int it = item_of(k, a.n_tiles);
-        if (it < 0) break;
-        const TcTile tl = a.tiles[it];
+      int itn = item_of(0, a.n_tiles);
+      TcTile tn{};
+      if (itn >= 0) tn = a.tiles[itn];  // the next item, loaded one ahead
+      for (int k = 0; ok && itn >= 0; ++k) {
+        const TcTile tl = tn;
+        itn = item_of(k + 1, a.n_tiles);
+        if (itn >= 0) tn = a.tiles[itn];
+        TcEntry nx = a.entries[tl.first];  // the next entry, loaded one ahead
         for (int e = 0; e < tl.count && ok; ++e) {
-          const TcEntry en = a.entries[tl.first + e];
-          const TcPiece& q = a.pieces[en.piece];
-          const uint32_t ub = tc_factor_slices(q.fmt) * 4096u, tb = tc_input_slices(q.fmt) * 4096u;
-          const int nks = q.kp >> 4;
+          const TcEntry en = nx;
+          if (e + 1 < tl.count) nx = a.entries[tl.first + e + 1];
+          const uint32_t ub = tc_factor_slices(en.fmt) * 4096u, tb = tc_input_slices(en.fmt) * 4096u;
+          const int nks = en.nks;
           for (int ks = 0; ks < nks; ks += kKS, ++gs) {
             const int s = gs % kDepth, nb = min(kKS, nks - ks);
             if (gs >= kDepth && !ws_wait(&c->empty[s], ((gs / kDepth) - 1) & 1, abort)) {
@@ -560,7 +574,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
             uint8_t* st = base + s * kStage;
             mbar_expect_tx(&c->full[s], nb * (ub + tb));
             bulk_copy_once(st, a.img + en.img + static_cast<int64_t>(ks) * ub, nb * ub, &c->full[s], pol);
-            bulk_copy(st + kOpA, a.timg + q.toff + static_cast<int64_t>(ks) * tb, nb * tb, &c->full[s]);
+            bulk_copy(st + kOpA, a.timg + en.toff + static_cast<int64_t>(ks) * tb, nb * tb, &c->full[s]);
             produced = gs + 1;
           }
         }
@@ -572,21 +586,21 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
       const uint64_t d0 = op_desc(base);
       int gs = 0, gp = 0;
       bool ok = true;
-      for (int k = 0; ok; ++k) {
-        const int it = item_of(k, a.n_tiles);
-        if (it < 0) break;
-        const TcTile tl = a.tiles[it];
-        int nst = 0, L = kChunk16;
-        for (int e = 0; e < tl.count; ++e) {
-          const TcPiece& q = a.pieces[a.entries[tl.first + e].piece];
-          nst += ((q.kp >> 4) + kKS - 1) / kKS;
-          L = min(L, chunk_of(q.fmt));
-        }
+      int itn = item_of(0, a.n_tiles);
+      TcTile tn{};
+      if (itn >= 0) tn = a.tiles[itn];  // the next item, loaded one ahead
+      for (int k = 0; ok && itn >= 0; ++k) {
+        const TcTile tl = tn;
+        itn = item_of(k + 1, a.n_tiles);
+        if (itn >= 0) tn = a.tiles[itn];
+        const int nst = tl.nst, L = tl.chunk;
         int i = 0, j = 0, s = gs % kDepth, par = (gs / kDepth) & 1;
+        int2 nx = *reinterpret_cast<const int2*>(&a.entries[tl.first].nks);  // {nks, fmt} of the next entry
         for (int e = 0; e < tl.count && ok; ++e) {
-          const TcPiece& q = a.pieces[a.entries[tl.first + e].piece];
-          const int np = n_products(q.fmt), nks = q.kp >> 4;
-          const uint32_t ustep = tc_factor_slices(q.fmt) * 256u, tstep = tc_input_slices(q.fmt) * 256u;
+          const int nks = nx.x, fmt = nx.y;
+          if (e + 1 < tl.count) nx = *reinterpret_cast<const int2*>(&a.entries[tl.first + e + 1].nks);
+          const int np = n_products(fmt);
+          const uint32_t ustep = tc_factor_slices(fmt) * 256u, tstep = tc_input_slices(fmt) * 256u;
           for (int ks = 0; ks < nks; ks += kKS, ++i, ++gs) {
             const int b = gp & 1;
             if (!ws_wait(&c->full[s], par, abort)) {
@@ -625,16 +639,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
     float acc[128];
     int gp = 0;
     bool ok = true;
-    for (int k = 0; ok; ++k) {
-      const int it = item_of(k, a.n_tiles);
-      if (it < 0) break;
-      const TcTile tl = a.tiles[it];
-      int nst = 0, L = kChunk16;
-      for (int e = 0; e < tl.count; ++e) {
-        const TcPiece& q = a.pieces[a.entries[tl.first + e].piece];
-        nst += ((q.kp >> 4) + kKS - 1) / kKS;
-        L = min(L, chunk_of(q.fmt));
-      }
+    int itn = item_of(0, a.n_tiles);
+    TcTile tn{};
+    if (itn >= 0) tn = a.tiles[itn];
+    for (int k = 0; ok && itn >= 0; ++k) {
+      const TcTile tl = tn;
+      itn = item_of(k + 1, a.n_tiles);
+      if (itn >= 0) tn = a.tiles[itn];
+      const int nst = tl.nst, L = tl.chunk;
 #pragma unroll
       for (int j = 0; j < 128; ++j) acc[j] = 0.f;
       for (int q = 0; q < (nst + L - 1) / L; ++q, ++gp) {

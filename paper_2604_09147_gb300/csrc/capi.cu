@@ -95,6 +95,7 @@ struct hh_matrix {
   int64_t t32_elems = 0, t64_elems = 0;  // per right-hand side
   uint8_t* d_arena = nullptr;
   int32_t* d_perm = nullptr;
+  int32_t* d_iperm = nullptr;  // caller position -> tree position
   int* d_status = nullptr;
   void* d_ws = nullptr;
   size_t ws_bytes = 0;
@@ -143,6 +144,7 @@ void free_device(hh_matrix* h) {
   if (cur != h->device) cudaSetDevice(h->device);
   cudaFree(h->d_arena);
   cudaFree(h->d_perm);
+  cudaFree(h->d_iperm);
   for (int d = 0; d < 2; ++d) {
     for (int p = 0; p < 2; ++p) {
       cudaFree(h->ss[d].d_desc[p]);
@@ -643,6 +645,11 @@ void upload_matrix(hh_matrix* h, int device) {
   ck(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device), "device attribute");
   h->d_arena = upload(H.arena);
   h->d_perm = upload(H.perm);
+  {
+    std::vector<int32_t> iperm(H.perm.size());
+    for (size_t p = 0; p < H.perm.size(); ++p) iperm[static_cast<size_t>(H.perm[p])] = static_cast<int32_t>(p);
+    h->d_iperm = upload(iperm);
+  }
   h->npad = (H.n + 32 + 3) / 4 * 4;
   // t offsets per block (room for kMaxNR right-hand sides)
   std::vector<int64_t> toff(H.lr.size(), 0);
@@ -800,9 +807,7 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   const TcSet& ts = h->tc[dir];
   const MrSet& ms = h->mr[dir];
   cudaError_t e = hh::dev::launch_tc_prep(in, ld_in, nr, h->d_perm, h->H.n, t.nblk, t.ximg, t.acc, h->npad, t.cnt,
-                                          ts.n_cnt, st);
-  if (e == cudaSuccess)
-    e = hh::dev::launch_mr_prep(in, ld_in, nr, h->d_perm, h->H.n, h->npad, t.xh, t.xl, t.t32, ms.t_floats, st);
+                                          ts.n_cnt, t.xh, t.xl, h->npad, t.t32, ms.t_floats, st);
   const StreamSet& rest = h->ss_rest[dir];
   mark(1);
   if (rest.n_items[0] + rest.n_items[1] > 0)
@@ -864,7 +869,7 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   mark(6);
   if (e == cudaSuccess) e = hh::dev::launch_tc(2, a, h->sms, st);
   mark(7);
-  if (e == cudaSuccess) e = hh::dev::launch_finish(t.acc, nr, h->d_perm, h->H.n, h->npad, out, ld_out, st);
+  if (e == cudaSuccess) e = hh::dev::launch_finish(t.acc, nr, h->d_iperm, h->H.n, h->npad, out, ld_out, st);
   mark(8);
   return e;
 }
@@ -940,7 +945,7 @@ int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, 
       e = run_stream(h, h->ss[dir], in + (int64_t)rb * ld_in, ld_in, nr, w.acc, w, st, ev);
       if (ev) cudaEventRecord(ev[3], st);
       if (e == cudaSuccess)
-        e = hh::dev::launch_finish(w.acc, nr, h->d_perm, h->H.n, h->npad, out + (int64_t)rb * ld_out, ld_out, st);
+        e = hh::dev::launch_finish(w.acc, nr, h->d_iperm, h->H.n, h->npad, out + (int64_t)rb * ld_out, ld_out, st);
       if (ev) cudaEventRecord(ev[4], st);
     }
     if (e != cudaSuccess) {
@@ -1725,7 +1730,7 @@ extern "C" int hh_matvec_noalloc(hh_handle h, int transpose, const double* in, d
       int grid = std::max(1, std::min(h->ss[dir].grid[phase][1], s.n_items));
       e = hh::dev::launch_stream(phase, h->ss[dir].fset, s, grid, st);
     }
-    if (e == cudaSuccess) e = hh::dev::launch_finish(acc, 1, h->d_perm, h->H.n, npad, out, h->H.n, st);
+    if (e == cudaSuccess) e = hh::dev::launch_finish(acc, 1, h->d_iperm, h->H.n, npad, out, h->H.n, st);
     if (e != cudaSuccess) rc = fail(HH_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
   }
   if (cur >= 0 && cur != h->device) cudaSetDevice(cur);

@@ -60,7 +60,8 @@ constexpr unsigned kSetF32 = 1u | 2u;    // fp64 + fp32
 constexpr unsigned kSetAll = 31u;        // every format
 unsigned pass_set_for(unsigned fmts_present);
 
-cudaError_t launch_finish(const double* acc, int nr, const int32_t* perm, int64_t n, int64_t npad,
+// out[u + r ld] = acc[r npad + iperm[u]] (iperm: caller position -> tree position)
+cudaError_t launch_finish(const double* acc, int nr, const int32_t* iperm, int64_t n, int64_t npad,
                           double* out, int64_t ld, cudaStream_t st);
 
 constexpr int kMaxNR = 4;  // right-hand sides per launch sequence
@@ -158,8 +159,12 @@ constexpr int kTcChunk16 = 16;
 // input and T images (fp32 pieces 3, the others 2)
 inline __host__ __device__ int tc_factor_slices(int fmt) { return fmt == 1 ? 3 : (fmt == 2 ? 2 : 1); }
 inline __host__ __device__ int tc_input_slices(int fmt) { return fmt == 1 ? 3 : 2; }
+// input images of the many-column sequence (both the tensor-core image and
+// the fp32 halves [npos][128] of mr.cu, npos <= 16 nblk) and the clearing of
+// acc, cnt and t32
 cudaError_t launch_tc_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t nblk,
-                           uint8_t* ximg, double* acc, int64_t npad, int* cnt, int n_cnt, cudaStream_t st);
+                           uint8_t* ximg, double* acc, int64_t npad, int* cnt, int n_cnt, float* xh, float* xl,
+                           int64_t npos, float* t32, int64_t t_floats, cudaStream_t st);
 // packs the factor panels of a set's groups (phase 1) and entries (phase 2) into img
 cudaError_t launch_tc_pack(const TcPiece* pieces, const TcGroup* groups, int n_groups, const TcEntry* entries,
                            int n_entries, uint8_t* img, cudaStream_t st);
@@ -190,8 +195,6 @@ struct MrArgs {
 constexpr int kMrRanks = 64;
 constexpr int kMrRows = 128;
 constexpr int kMrDenseRows = 64;
-cudaError_t launch_mr_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t npos,
-                           float* xh, float* xl, float* t32, int64_t t_floats, cudaStream_t st);
 // kind 1: phase 1, 2: phase 2, 3: dense blocks
 cudaError_t launch_mr(int kind, const MrArgs& a, cudaStream_t st);
 

@@ -6,7 +6,8 @@
 //            so that every 16-byte vector of a factor column meets an aligned
 //            vector of the input; clears the fp64 output accumulator and the
 //            work counters of the two passes.
-//   finish : output accumulator (tree order) -> the caller's order.
+//   finish : output accumulator (tree order) -> the caller's order, through
+//            the inverse permutation (caller position -> tree position).
 // The two streaming passes between them live in stream.cu.
 #include "hh_device.h"
 
@@ -41,11 +42,14 @@ __global__ void prep_kernel(const double* __restrict__ in, int64_t ld, int nr,
   }
 }
 
-__global__ void finish_kernel(const double* __restrict__ acc, int nr, const int32_t* __restrict__ perm,
+// out[u + r ld] = acc[r npad + iperm[u]]: a thread owns caller position u
+// and walks the columns, so the writes of a warp are coalesced and the
+// gathered reads of the threads in flight stay in a few accumulator columns
+__global__ void finish_kernel(const double* __restrict__ acc, int nr, const int32_t* __restrict__ iperm,
                               int64_t n, int64_t npad, double* __restrict__ out, int64_t ld) {
-  for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
-       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t u = perm[p];
+  for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u < n;
+       u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t p = iperm[u];
     for (int r = 0; r < nr; ++r) out[u + r * ld] = acc[static_cast<int64_t>(r) * npad + p];
   }
 }
@@ -60,11 +64,12 @@ cudaError_t launch_prep(const double* in, int64_t ld, int nr, const int32_t* per
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish(const double* acc, int nr, const int32_t* perm, int64_t n, int64_t npad,
+cudaError_t launch_finish(const double* acc, int nr, const int32_t* iperm, int64_t n, int64_t npad,
                           double* out, int64_t ld, cudaStream_t st) {
   int64_t blocks = (n + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  finish_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(acc, nr, perm, n, npad, out, ld);
+  if (blocks > 8192) blocks = 8192;
+  if (blocks < 1) blocks = 1;
+  finish_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(acc, nr, iperm, n, npad, out, ld);
   return cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ constexpr int kK1 = 32;       // positions per phase-1 stage
 constexpr int kK2 = 16;       // ranks (dense: K columns) per phase-2 stage
 constexpr int kDenseRows = 64;
 
-constexpr int kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3, kE4M3 = 4;
+constexpr int kF32 = 1, kBF16 = 3, kE4M3 = 4;
 
 __device__ __forceinline__ int fsize(int f) { return f == kF32 ? 4 : (f == kE4M3 ? 1 : 2); }
 
@@ -452,24 +452,6 @@ __global__ void __launch_bounds__(kThreads, 2) mr_dense(MrArgs a) {
   add_tile<RPT, kDenseRows, 4>(a, tl, sm3, acc, tr, tc);
 }
 
-// X (caller's order, column-major, ld) -> tree order, fp32 leading and
-// trailing halves [npos][128]; columns r >= nr and positions >= n are zero.
-// Also clears the T arena of the CUDA-core pieces (split ranges add into it).
-__global__ void mr_prep_kernel(const double* __restrict__ x, int64_t ld, int nr, const int32_t* __restrict__ perm,
-                               int64_t n, int64_t npos, float* __restrict__ xh, float* __restrict__ xl,
-                               float* __restrict__ t32, int64_t t_floats) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  for (int64_t q = t0; q < npos * 128; q += stride) {
-    const int64_t p = q >> 7;
-    const int r = static_cast<int>(q & 127);
-    const double v = (r < nr && p < n) ? x[static_cast<int64_t>(perm[p]) + r * ld] : 0.0;
-    const float h = __double2float_rn(v);
-    xh[q] = h;
-    xl[q] = __double2float_rn(v - static_cast<double>(h));
-  }
-  for (int64_t q = t0; q < t_floats; q += stride) t32[q] = 0.f;
-}
 
 template <int RPT>
 cudaError_t launch_rpt(int kind, const MrArgs& a, cudaStream_t st) {
@@ -492,14 +474,6 @@ cudaError_t launch_rpt(int kind, const MrArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_mr_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t npos,
-                           float* xh, float* xl, float* t32, int64_t t_floats, cudaStream_t st) {
-  int64_t blocks = (npos * 128 + 255) / 256;
-  if (blocks > 8192) blocks = 8192;
-  if (blocks < 1) blocks = 1;
-  mr_prep_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(x, ld, nr, perm, n, npos, xh, xl, t32, t_floats);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_mr(int kind, const MrArgs& a, cudaStream_t st) {
   if ((kind == 1 && a.n_groups <= 0) || (kind != 1 && a.n_tiles <= 0)) return cudaSuccess;

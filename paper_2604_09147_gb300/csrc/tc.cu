@@ -722,13 +722,19 @@ __global__ void tc_pack2_kernel(const TcPiece* __restrict__ pieces, const TcEntr
   }
 }
 
-// X (caller's order, column-major, ld) -> tree order, fp32, three bf16 slices
-// in the phase-1 operand image [16-position block][slice][128 rows x 32 B];
-// rows r >= nr and positions >= n are zero.  Also clears the output
-// accumulator and the arrival counters of the split groups.
+// X (caller's order, column-major, ld) -> tree order, once per product:
+//   * fp32 of each value as three bf16 slices in the phase-1 operand image
+//     [16-position block][slice][128 rows x 32 B] (rows r >= nr and positions
+//     >= n are zero);
+//   * its fp32 leading and trailing halves [npos][128] for the CUDA-core
+//     kernels (mr.cu);
+// and clears the output accumulator, the arrival counters of the split
+// groups and the T arena of the CUDA-core pieces.  One gather of X feeds
+// both images.
 __global__ void tc_prep_kernel(const double* __restrict__ x, int64_t ld, int nr, const int32_t* __restrict__ perm,
                                int64_t n, int64_t nblk, uint8_t* __restrict__ ximg, double* __restrict__ acc,
-                               int64_t npad, int* __restrict__ cnt, int n_cnt) {
+                               int64_t npad, int* __restrict__ cnt, int n_cnt, float* __restrict__ xh,
+                               float* __restrict__ xl, int64_t npos, float* __restrict__ t32, int64_t t_floats) {
   const int64_t total = nblk * 256;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -739,23 +745,32 @@ __global__ void tc_prep_kernel(const double* __restrict__ x, int64_t ld, int nr,
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int64_t p = 16 * blk + 8 * c + t;
-      v[t] = (r < nr && p < n) ? __double2float_rn(x[static_cast<int64_t>(perm[p]) + r * ld]) : 0.f;
+      const double d = (r < nr && p < n) ? x[static_cast<int64_t>(perm[p]) + r * ld] : 0.0;
+      v[t] = __double2float_rn(d);
+      if (p < npos) {
+        xh[p * 128 + r] = v[t];
+        xl[p * 128 + r] = __double2float_rn(d - static_cast<double>(v[t]));
+      }
     }
     store_slices(v, 3, ximg + blk * (3 * 4096) + core_off(r, c), 4096);
   }
   const int64_t ntot = static_cast<int64_t>(nr) * npad;
   for (int64_t q = t0; q < ntot; q += stride) acc[q] = 0.0;
   for (int64_t q = t0; q < n_cnt; q += stride) cnt[q] = 0;
+  for (int64_t q = t0; q < t_floats; q += stride) t32[q] = 0.f;
 }
 
 }  // namespace
 
 cudaError_t launch_tc_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t nblk,
-                           uint8_t* ximg, double* acc, int64_t npad, int* cnt, int n_cnt, cudaStream_t st) {
+                           uint8_t* ximg, double* acc, int64_t npad, int* cnt, int n_cnt, float* xh, float* xl,
+                           int64_t npos, float* t32, int64_t t_floats, cudaStream_t st) {
+  if (16 * nblk < npos) return cudaErrorInvalidValue;  // the fp32 images must be covered
   int64_t blocks = (nblk * 256 + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   if (blocks < 1) blocks = 1;
-  tc_prep_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(x, ld, nr, perm, n, nblk, ximg, acc, npad, cnt, n_cnt);
+  tc_prep_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(x, ld, nr, perm, n, nblk, ximg, acc, npad, cnt, n_cnt, xh,
+                                                          xl, npos, t32, t_floats);
   return cudaGetLastError();
 }
 

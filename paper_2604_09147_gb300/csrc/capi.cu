@@ -721,6 +721,7 @@ cudaError_t run_stream(hh_matrix* h, const StreamSet& set, const double* in, int
                        const WsView& w, cudaStream_t st, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], st);
   cudaError_t e = hh::dev::launch_prep(in, ld_in, nr, h->d_perm, h->H.n, h->npad, w.xs, w.xs_lo, acc, st, w.counters);
+  bool p1 = false;  // phase 1 launched: phase 2 may follow it as a programmatic dependent
   for (int phase = 1; phase <= 2 && e == cudaSuccess; ++phase) {
     if (ev) cudaEventRecord(ev[phase], st);
     hh::dev::StreamArgs s;
@@ -739,7 +740,8 @@ cudaError_t run_stream(hh_matrix* h, const StreamSet& set, const double* in, int
     s.counter = w.counters + (phase - 1);
     if (s.n_items == 0) continue;
     int grid = std::max(1, std::min(set.grid[phase][nr], s.n_items));
-    e = hh::dev::launch_stream(phase, set.fset, s, grid, st);
+    e = hh::dev::launch_stream(phase, set.fset, s, grid, st, p1 && !ev);
+    p1 = phase == 1;
   }
   return e;
 }
@@ -1424,6 +1426,7 @@ void free_batch(hh_batch_s* b) {
 cudaError_t batch_launches(hh_batch_s* b, int dir, const double* x, double* y, cudaStream_t st) {
   cudaError_t e = hh::dev::launch_batch_prep(x, b->d_xofs, b->d_perm, b->d_pofs, b->d_ns, b->count, b->np, b->xs,
                                              b->xs_lo, b->acc, b->counters, st);
+  bool p1 = false;
   for (int phase = 1; phase <= 2 && e == cudaSuccess; ++phase) {
     const StreamSet& set = b->ss[dir];
     hh::dev::StreamArgs a;
@@ -1442,7 +1445,8 @@ cudaError_t batch_launches(hh_batch_s* b, int dir, const double* x, double* y, c
     a.counter = b->counters + (phase - 1);
     if (a.n_items == 0) continue;
     const int grid = std::max(1, std::min(set.grid[phase][1], a.n_items));
-    e = hh::dev::launch_stream(phase, set.fset, a, grid, st);
+    e = hh::dev::launch_stream(phase, set.fset, a, grid, st, p1);
+    p1 = phase == 1;
   }
   if (e == cudaSuccess)
     e = hh::dev::launch_batch_finish(b->acc, b->d_xofs, b->d_perm, b->d_pofs, b->d_ns, b->count, b->np, y, st);
@@ -1712,6 +1716,7 @@ extern "C" int hh_matvec_noalloc(hh_handle h, int transpose, const double* in, d
     cudaStream_t st = (cudaStream_t)stream;
     int* counters = (int*)(p + align256(sizeof(float2) * std::max<int64_t>(1, t64 * hh::dev::kMaxNR)));
     cudaError_t e = hh::dev::launch_prep(in, h->H.n, 1, h->d_perm, h->H.n, npad, xs, xs_lo, acc, st, counters);
+    bool p1 = false;
     for (int phase = 1; phase <= 2 && e == cudaSuccess; ++phase) {
       hh::dev::StreamArgs s;
       std::memset(&s, 0, sizeof(s));
@@ -1728,7 +1733,8 @@ extern "C" int hh_matvec_noalloc(hh_handle h, int transpose, const double* in, d
       s.status = h->d_status;
       s.counter = counters + (phase - 1);
       int grid = std::max(1, std::min(h->ss[dir].grid[phase][1], s.n_items));
-      e = hh::dev::launch_stream(phase, h->ss[dir].fset, s, grid, st);
+      e = hh::dev::launch_stream(phase, h->ss[dir].fset, s, grid, st, p1);
+      p1 = phase == 1 && s.n_items > 0;
     }
     if (e == cudaSuccess) e = hh::dev::launch_finish(acc, 1, h->d_iperm, h->H.n, npad, out, h->H.n, st);
     if (e != cudaSuccess) rc = fail(HH_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));

@@ -50,7 +50,10 @@ struct StreamArgs {
 cudaError_t launch_prep(const double* in, int64_t ld, int nr, const int32_t* perm, int64_t n,
                         int64_t npad, float* xs, float* xs_lo, double* acc, cudaStream_t st,
                         int* counters = nullptr);
-cudaError_t launch_stream(int phase, unsigned fset, const StreamArgs& a, int grid, cudaStream_t st);
+// pdl (phase 2 only, and only directly after a phase-1 launch of the same
+// sequence): programmatic dependent launch, see stream.cu
+cudaError_t launch_stream(int phase, unsigned fset, const StreamArgs& a, int grid, cudaStream_t st,
+                          bool pdl = false);
 int stream_blocks_per_sm(int phase, unsigned fset, int nr);
 int stream_rows_per_item(int fmt);   // phase-2 rows per item (1 KB of factor data per column)
 int stream_cols_per_item();          // phase-1 columns per item

@@ -47,6 +47,8 @@ __global__ void prep_kernel(const double* __restrict__ in, int64_t ld, int nr,
 // gathered reads of the threads in flight stay in a few accumulator columns
 __global__ void finish_kernel(const double* __restrict__ acc, int nr, const int32_t* __restrict__ iperm,
                               int64_t n, int64_t npad, double* __restrict__ out, int64_t ld) {
+  // launched as a programmatic dependent of the last pass: wait for it
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u < n;
        u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t p = iperm[u];
@@ -69,8 +71,17 @@ cudaError_t launch_finish(const double* acc, int nr, const int32_t* iperm, int64
   int64_t blocks = (n + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   if (blocks < 1) blocks = 1;
-  finish_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(acc, nr, iperm, n, npad, out, ld);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(blocks));
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, finish_kernel, acc, nr, iperm, n, npad, out, ld);
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 unsigned pass_set_for(unsigned fmts_present) {

@@ -23,6 +23,13 @@
 // launch).  Every wait on an mbarrier has a clock-based limit; on expiry the
 // kernel sets bit 2 of the status word, lets the copies it issued complete
 // (again bounded) and returns.
+//
+// Programmatic dependent launch: every CTA lets the next kernel of the stream
+// start early (griddepcontrol.launch_dependents).  Phase 2 may be launched
+// that way after phase 1: its producer streams U factors (which phase 1 does
+// not write) while phase 1 drains, and its consumers wait for phase 1 to
+// complete (griddepcontrol.wait, a no-op for a normal launch) before they
+// read t.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -293,10 +300,12 @@ __device__ void produce(Smem<PHASE, FSET>& sm, const StreamArgs& a) {
         for (int q = lane; q < nseg; q += 32)
           bulk_g2s(sm.data[stage] + q * slot, src0 + q * seg_stride, static_cast<uint32_t>(bytes_each),
                    &sm.full[stage], pol);
-      if (PHASE == 1 && xbytes > 0 && lane == 31)
-        bulk_g2s_plain(sm.x[stage], xsrc, static_cast<uint32_t>(xbytes), &sm.full[stage]);
-      if (PHASE == 1 && xbytes > 0 && d.fmt == 0 && lane == 30)
-        bulk_g2s_plain(sm.x[stage] + kXBytes / 2, xsrc_lo, static_cast<uint32_t>(xbytes), &sm.full[stage]);
+      if constexpr (PHASE == 1) {
+        if (xbytes > 0 && lane == 31)
+          bulk_g2s_plain(sm.x[stage], xsrc, static_cast<uint32_t>(xbytes), &sm.full[stage]);
+        if (xbytes > 0 && d.fmt == 0 && lane == 30)
+          bulk_g2s_plain(sm.x[stage] + kXBytes / 2, xsrc_lo, static_cast<uint32_t>(xbytes), &sm.full[stage]);
+      }
       issued_mask |= 1 << stage;
       issued_par[stage] = par ^ 1u;
       if (++stage == kStages) {
@@ -563,6 +572,7 @@ __device__ void consume(Smem<PHASE, FSET>& sm, const StreamArgs& a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wc = warp - 1;           // consumer warp index
   const int ct = threadIdx.x - 32;   // consumer thread index (0..127)
+  if constexpr (PHASE == 2) asm volatile("griddepcontrol.wait;" ::: "memory");  // t of phase 1
   int stage = 0;
   uint32_t par = 0;
   float acc1[2][NR][4];
@@ -644,26 +654,43 @@ __global__ void __launch_bounds__(kStreamThreads) stream_kernel(StreamArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (threadIdx.x < 32) produce<PHASE, FSET>(sm, a);
   else consume<PHASE, NR, FSET>(sm, a);
 }
 
+// launch with (pdl) or without programmatic stream serialization
+template <class Kern>
+cudaError_t launch_k(Kern k, int grid, size_t smem, cudaStream_t st, bool pdl, const StreamArgs& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(kStreamThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, a);
+}
+
 template <int PHASE, unsigned FSET>
-cudaError_t launch_stream_t(const StreamArgs& a, int grid, cudaStream_t st) {
+cudaError_t launch_stream_t(const StreamArgs& a, int grid, cudaStream_t st, bool pdl) {
   const size_t smem = sizeof(Smem<PHASE, FSET>);
   cudaError_t e = cudaSuccess;
   switch (a.nr) {
     case 1:
       e = cudaFuncSetAttribute(stream_kernel<PHASE, 1, FSET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) stream_kernel<PHASE, 1, FSET><<<grid, kStreamThreads, smem, st>>>(a);
+      if (e == cudaSuccess) e = launch_k(stream_kernel<PHASE, 1, FSET>, grid, smem, st, pdl, a);
       break;
     case 2:
       e = cudaFuncSetAttribute(stream_kernel<PHASE, 2, FSET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) stream_kernel<PHASE, 2, FSET><<<grid, kStreamThreads, smem, st>>>(a);
+      if (e == cudaSuccess) e = launch_k(stream_kernel<PHASE, 2, FSET>, grid, smem, st, pdl, a);
       break;
     case 4:
       e = cudaFuncSetAttribute(stream_kernel<PHASE, 4, FSET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) stream_kernel<PHASE, 4, FSET><<<grid, kStreamThreads, smem, st>>>(a);
+      if (e == cudaSuccess) e = launch_k(stream_kernel<PHASE, 4, FSET>, grid, smem, st, pdl, a);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -691,11 +718,14 @@ int stream_occupancy(int nr) {
 
 }  // namespace
 
-cudaError_t launch_stream(int phase, unsigned fset, const StreamArgs& a, int grid, cudaStream_t st) {
+cudaError_t launch_stream(int phase, unsigned fset, const StreamArgs& a, int grid, cudaStream_t st, bool pdl) {
   if (a.n_items == 0) return cudaSuccess;
-  if (fset == kSetF64) return phase == 1 ? launch_stream_t<1, kSetF64>(a, grid, st) : launch_stream_t<2, kSetF64>(a, grid, st);
-  if (fset == kSetF32) return phase == 1 ? launch_stream_t<1, kSetF32>(a, grid, st) : launch_stream_t<2, kSetF32>(a, grid, st);
-  return phase == 1 ? launch_stream_t<1, kSetAll>(a, grid, st) : launch_stream_t<2, kSetAll>(a, grid, st);
+  if (phase == 1) pdl = false;  // phase 1 needs the prep launch complete before it starts
+  if (fset == kSetF64)
+    return phase == 1 ? launch_stream_t<1, kSetF64>(a, grid, st, false) : launch_stream_t<2, kSetF64>(a, grid, st, pdl);
+  if (fset == kSetF32)
+    return phase == 1 ? launch_stream_t<1, kSetF32>(a, grid, st, false) : launch_stream_t<2, kSetF32>(a, grid, st, pdl);
+  return phase == 1 ? launch_stream_t<1, kSetAll>(a, grid, st, false) : launch_stream_t<2, kSetAll>(a, grid, st, pdl);
 }
 
 int stream_blocks_per_sm(int phase, unsigned fset, int nr) {

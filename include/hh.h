@@ -177,7 +177,8 @@ int hh_perm(hh_handle h, int32_t* perm);
  * whose clusters start at multiples of 16 on the tensor cores (exact bf16
  * slices of the factors and of the fp32 input; products kept down to about
  * 2^-24 for fp32 blocks and below the unit roundoff of the 16- and 8-bit
- * formats; fp32 accumulation drained every 32 terms), the other 32/16/8-bit
+ * formats; fp32 accumulation drained into round-to-nearest registers every
+ * 64 terms for fp32 blocks, every 512 for the others), the other 32/16/8-bit
  * blocks on CUDA-core fp32 kernels, the dense blocks as fp32 pairs, the fp64
  * low-rank blocks on the streaming passes.  The first such call in each
  * direction allocates the tensor-core workspace and the factor panels packed

@@ -171,12 +171,6 @@ T* upload(const std::vector<T>& v) {
   return p;
 }
 
-int next_pow2_32(int64_t v) {
-  int g = 1;
-  while (g < v && g < 32) g <<= 1;
-  return g;
-}
-
 // Dense blocks with an even leading dimension (16-byte aligned columns), each
 // scaled by a power of two so that its largest magnitude lies in (1/2, 1]
 // (exact; the kernels split fp64 values into fp32 halves).

@@ -107,9 +107,10 @@ typedef struct {
   int32_t blocks_per_sm[4];       /* streaming CTAs per SM chosen by hh_autotune:
                                      {fwd phase 1, fwd phase 2, T phase 1, T phase 2};
                                      0 = the occupancy maximum                       */
-  int64_t tc_panel_bytes[2];      /* device bytes of the tensor-core operand panels
-                                     {forward, transpose}, packed on the first
-                                     tensor-core product in that direction          */
+  int64_t tc_panel_bytes[2];      /* device bytes held by the tensor-core operand
+                                     panels {forward, transpose}: 0 until the first
+                                     tensor-core product in that direction packs
+                                     them                                           */
 } hh_info_t;
 
 /*

@@ -1136,7 +1136,7 @@ int hh_info(hh_handle h, hh_info_t* o) {
   o->split_positions = h->split_len;
   for (int d = 0; d < 2; ++d)
     for (int p = 1; p <= 2; ++p) o->blocks_per_sm[2 * d + p - 1] = h->blocks_per_sm[d][p];
-  for (int d = 0; d < 2; ++d) o->tc_panel_bytes[d] = h->device >= 0 ? h->tc[d].img_bytes : 0;
+  for (int d = 0; d < 2; ++d) o->tc_panel_bytes[d] = h->tc[d].d_img ? h->tc[d].img_bytes : 0;
   return HH_OK;
 }
 

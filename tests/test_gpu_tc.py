@@ -163,6 +163,26 @@ def test_tc_split_groups(P, tmp_path_factory, monkeypatch):
         check(H, O, nrhs, tr, 7800 + nrhs)  # counters were reset by the previous call
 
 
+def test_tc_panels_packed_per_direction(P, tmp_path_factory):
+    """A fresh handle holds no tensor-core panels; the first tensor-core
+    product in a direction packs that direction's panels (reported by
+    hh_info), and later products reuse them."""
+    _, O = case(P, tmp_path_factory, "gauss_narrow")
+    path = str(tmp_path_factory.mktemp("panels") / "m.hhm")
+    hhfile.write(O, path)
+    H = P.HMatrix.load(path, 0)
+    assert H.info()["tc_panel_bytes"] == [0, 0]
+    check(H, O, 32, False, 7900)
+    fwd = H.info()["tc_panel_bytes"]
+    assert fwd[0] > 0 and fwd[1] == 0
+    check(H, O, 32, True, 7901)
+    both = H.info()["tc_panel_bytes"]
+    assert both[0] == fwd[0] and both[1] > 0
+    check(H, O, 48, False, 7902)
+    check(H, O, 48, True, 7903)
+    assert H.info()["tc_panel_bytes"] == both
+
+
 def test_tc_agrees_with_streaming_path(P, tmp_path_factory):
     """The same product through the tensor cores (one call with 32 columns) and
     through the streaming passes (eight calls with 4 columns)."""

@@ -151,6 +151,27 @@ int hh_load(const char* path, int device, hh_handle* out);
  * The new handle is independent of src and uploaded to `device` (-1: none). */
 int hh_reencode(hh_handle src, uint32_t fmt_mask, int device, hh_handle* out);
 
+/* hh_optimal_switch_level -- Algorithm 2: the switching level ell* whose H_h
+ * matrix gains the most storage over the H_s matrix (standard admissibility
+ * down to the leaves, ell = L).  The two storages share the far-field blocks
+ * of levels 1..ell and the dense diagonal (Section 3.3), so the gain of a
+ * level is S_1(ell) - S_2(ell) = S_s - S_h(ell), counted in fp64 words with
+ * every low-rank block at its assigned format's bits (Section 5.2's count;
+ * with fmt_mask = HH_F64 the uniform-precision gain).  Starting at ell = L
+ * (gain 0) the algorithm moves to ell - 1 while the gain grows strictly and
+ * stops at the first level whose gain does not.
+ *   points ... seed   as for hh_build (switch_level is what is searched).
+ *   ell_star          receives ell*.
+ *   depth             receives L (may be NULL).
+ *   gains             NULL or HH_MAX_LEVELS doubles: gains[l] = S_s - S_h(l)
+ *                     for each level evaluated, NaN for the others.
+ * Host-synchronous and host-only: one construction (Algorithm 1, 5, 3) per
+ * evaluated level.  HH_EINVAL for bad arguments or a tree deeper than
+ * HH_MAX_LEVELS - 1. */
+int hh_optimal_switch_level(const double* points, int64_t n, int dim, int kernel, double kernel_param,
+                            int leaf_size, double eta, double tol, uint32_t fmt_mask, uint64_t seed,
+                            int* ell_star, int* depth, double* gains);
+
 /* hh_save -- write the handle's matrix (points, tree, block tables, factor
  * arena in stored formats, dense blocks) to `path`. */
 int hh_save(hh_handle h, const char* path);

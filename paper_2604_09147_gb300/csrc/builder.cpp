@@ -645,6 +645,38 @@ void reencode(const HostMatrix& src, uint32_t fmt_mask, int threads, HostMatrix&
   layout_and_store(refs, threads, h);
 }
 
+// Algorithm 2.  The H_s and H_h(ell) storages share the far-field blocks of
+// levels 1..ell and the dense diagonal (Section 3.3), so their difference is
+// S_1(ell) - S_2(ell); storage is Section 5.2's count in fp64 words with each
+// block's format bits (summarize().storage_amp).  Each S_2 evaluation is a
+// construction of that H_h matrix (Algorithm 1).
+int optimal_switch_level(const double* points, int64_t n, int dim, const BuildParams& p, std::vector<double>& gains,
+                         int& depth) {
+  if (n < 1 || dim < 1 || p.leaf < 1) throw std::invalid_argument("bad sizes");
+  const int L = tree_depth(n, p.leaf);
+  depth = L;
+  gains.assign(static_cast<size_t>(L) + 1, std::nan(""));
+  auto storage_at = [&](int ell) {
+    BuildParams q = p;
+    q.ell = ell;
+    HostMatrix h;
+    build(points, n, dim, q, h);
+    return summarize(h).storage_amp;
+  };
+  const double ss = storage_at(L);
+  int ell = L;
+  double s = 0.0;  // S_1(L) - S_2(L)
+  gains[L] = 0.0;
+  while (ell > 0) {
+    const double s_new = ss - storage_at(ell - 1);
+    gains[ell - 1] = s_new;
+    if (s_new <= s) break;
+    s = s_new;
+    --ell;
+  }
+  return ell;
+}
+
 Summary summarize(const HostMatrix& h) {
   Summary s;
   s.csp.assign(static_cast<size_t>(h.L) + 1, 0);

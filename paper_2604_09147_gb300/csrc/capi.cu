@@ -1029,6 +1029,29 @@ int hh_build(const double* points, int64_t n, int dim, int kernel, double kernel
   return finish_construction(h, device, out);
 }
 
+int hh_optimal_switch_level(const double* points, int64_t n, int dim, int kernel, double kernel_param,
+                            int leaf_size, double eta, double tol, uint32_t fmt_mask, uint64_t seed,
+                            int* ell_star, int* depth, double* gains) {
+  if (!points || !ell_star) return fail(HH_EINVAL, "points or ell_star is NULL");
+  try {
+    hh::BuildParams p{kernel, kernel_param, leaf_size, eta, 0, tol, fmt_mask, seed, 0};
+    if (const char* e = std::getenv("HH_BUILD_THREADS")) p.threads = std::atoi(e);
+    std::vector<double> g;
+    int L = 0;
+    const int ell = hh::optimal_switch_level(points, n, dim, p, g, L);
+    if (L >= HH_MAX_LEVELS) return fail(HH_EINVAL, "tree deeper than HH_MAX_LEVELS - 1");
+    *ell_star = ell;
+    if (depth) *depth = L;
+    if (gains)
+      for (int l = 0; l < HH_MAX_LEVELS; ++l) gains[l] = l <= L ? g[static_cast<size_t>(l)] : std::nan("");
+  } catch (const std::bad_alloc&) {
+    return fail(HH_ENOMEM, "out of host memory during the level search");
+  } catch (const std::exception& e) {
+    return fail(HH_EINVAL, e.what());
+  }
+  return HH_OK;
+}
+
 int hh_load(const char* path, int device, hh_handle* out) {
   if (!out) return fail(HH_EINVAL, "out is NULL");
   *out = nullptr;

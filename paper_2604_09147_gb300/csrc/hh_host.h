@@ -83,6 +83,13 @@ void load_file(const std::string& path, HostMatrix& h);
 // Validate offsets, sizes and alignment of a matrix (throws on violation).
 void validate(const HostMatrix& h);
 
+// Algorithm 2: the switching level with the largest storage gain
+// S_1(ell) - S_2(ell) = S_s - S_h(ell) over the H_s matrix (ell = L), walking
+// up from the leaves while the gain grows.  Returns ell*; gains[l] holds the
+// gain of every level evaluated (NaN elsewhere), sized L + 1; depth = L.
+int optimal_switch_level(const double* points, int64_t n, int dim, const BuildParams& p, std::vector<double>& gains,
+                         int& depth);
+
 // Derived quantities for hh_info.
 struct Summary {
   int64_t blocks_per_fmt[NFMT] = {0, 0, 0, 0, 0};

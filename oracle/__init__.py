@@ -20,6 +20,8 @@ no blocking, fusion or reordering beyond what the paper states:
   build.py      Algorithm 1 + Algorithm 5 (Frobenius norms) + Algorithm 3
                 (adaptive precision assignment) + storage formulas.
   matvec.py     Algorithm 4 (b = H_hat x), its transpose, dense assembly.
+  switch.py     Algorithm 2 (the switching level with the largest storage
+                gain over the H_s matrix).
   bounds.py     Theorem 4.2 / 4.4 error bounds and Lemma 3.1.
   hhfile.py     reader/writer of the serialized H_h file (the input both the
                 oracle and the CUDA path consume).

@@ -51,6 +51,14 @@ def points(n: int, dim: int, seed: int) -> np.ndarray:
     return _rng(seed).random((int(n), int(dim)))
 
 
+def sphere_points(n: int, dim: int, seed: int) -> np.ndarray:
+    """N points on the surface of the unit hypersphere in R^dim (the paper's
+    second particle set, Section 5), uniform on the surface: normalized
+    standard normal vectors.  float64, row-major (n, dim)."""
+    g = _rng(seed).standard_normal((int(n), int(dim)))
+    return g / np.linalg.norm(g, axis=1, keepdims=True)
+
+
 def rhs(n: int, nrhs: int, dist: str, seed: int) -> np.ndarray:
     """Right-hand sides, float64, column-major (n, nrhs) as a Fortran-ordered array.
 

@@ -111,6 +111,9 @@ typedef struct {
                                      panels {forward, transpose}: 0 until the first
                                      tensor-core product in that direction packs
                                      them                                           */
+  int32_t tree_step;              /* binary levels per tree level: 1 for the KD tree,
+                                     d for the 2^d-tree (L, ell, csp are binary)   */
+  int32_t pad_;
 } hh_info_t;
 
 /*
@@ -136,6 +139,28 @@ typedef struct {
 int hh_build(const double* points, int64_t n, int dim, int kernel, double kernel_param,
              int leaf_size, double eta, int switch_level, double tol, uint32_t fmt_mask,
              uint64_t seed, int device, hh_handle* out);
+
+/* cluster trees (hh_build_ex) */
+enum hh_tree {
+  HH_TREE_KD = 0,  /* binary KD bisection at the median of the widest axis  */
+  HH_TREE_2D = 1   /* balanced 2^d-tree (quad-tree in 2-D, oct-tree in 3-D) */
+};
+
+/* hh_build_ex -- hh_build with a choice of cluster tree (Section 2.1).
+ *   tree   HH_TREE_KD: as hh_build.  HH_TREE_2D: the geometrically balanced
+ *          2^d-tree of the paper: the root is the smallest axis-aligned
+ *          hypercube around the points, every cell is split into its 2^d
+ *          sub-cubes (a point on a splitting plane goes to the upper cell),
+ *          depth the smallest L with ceil(n / 2^{dL}) <= leaf_size; cells
+ *          may be empty.  switch_level counts 2^d-tree levels (-1:
+ *          floor(L/2)); eta = sqrt(d) is the paper's choice.
+ * The 2^d-tree is held as a binary tree whose level b halves its cells along
+ * axis b mod d, so hh_info's L and ell and the block levels of hh_save's
+ * file are binary levels (d per tree level; the file records d).  Other
+ * arguments and errors as hh_build. */
+int hh_build_ex(const double* points, int64_t n, int dim, int kernel, double kernel_param,
+                int leaf_size, double eta, int switch_level, double tol, uint32_t fmt_mask,
+                uint64_t seed, int tree, int device, hh_handle* out);
 
 /* hh_load -- read a file written by hh_save (or by any writer of the same
  * documented layout) and upload it to `device` (-1: host only).  The layout

@@ -35,7 +35,7 @@ import numpy as np
 from . import formats as F
 from .compress import kernel_entries, lr_compress
 from .partition import KIND_NBR, Partition, measured_csp, partition
-from .tree import Tree, build_tree
+from .tree import Tree, build_tree, build_tree_2d
 
 
 @dataclass
@@ -150,13 +150,23 @@ def block_tau(tol: float, level: int, norm_b: float, norm_all: float) -> float:
 
 
 def build(points: np.ndarray, kernel: int, kernel_param: float, leaf_size: int,
-          eta: float, ell: int, tol: float, fmt_mask: int) -> HMatrix:
+          eta: float, ell: int, tol: float, fmt_mask: int, tree_kind: str = "kd") -> HMatrix:
+    """tree_kind "kd": binary KD bisection; "2d": the balanced 2^d-tree, with
+    ell given in its tree levels (-1: floor(L/2)) and stored as the binary
+    level d ell, like every block level (so 2^{l/2} of the rule is the
+    paper's 2^{d l'/2} at tree level l')."""
     pts = np.ascontiguousarray(points, dtype=np.float64)
     n, dim = pts.shape
-    tree = build_tree(pts, leaf_size)
+    if tree_kind == "2d":
+        tree = build_tree_2d(pts, leaf_size)
+    elif tree_kind == "kd":
+        tree = build_tree(pts, leaf_size)
+    else:
+        raise ValueError("tree_kind must be 'kd' or '2d'")
     L = tree.L
     if ell < 0:
-        ell = L // 2
+        ell = (L // tree.step) // 2
+    ell *= tree.step
     part: Partition = partition(tree, eta, ell)
     tp = pts[tree.perm]                              # points in tree order
     H = HMatrix(n=n, dim=dim, kernel=kernel, kernel_param=kernel_param, leaf_size=leaf_size,

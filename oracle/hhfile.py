@@ -3,7 +3,11 @@
 Little-endian layout (version 1):
   magic      8 bytes  b"HHMATv01"
   ints       int64[16]: N, dim, L, ell, leaf_size, kernel, n_lr, n_dense,
-                        fmt_mask, arena_bytes, dense_elems, n_nodes, seed, 0, 0, 0
+                        fmt_mask, arena_bytes, dense_elems, n_nodes, seed,
+                        step, 0, 0
+             (step: binary levels per tree level, 1 for the KD tree, d for
+             the 2^d-tree; 0 is read as 1.  L, ell and block levels are
+             binary levels.)
   reals      float64[8]: eta, tol, kernel_param, ||H~||_F, 0, 0, 0, 0
   points     float64[N * dim]   (user order, row-major)
   perm       int32[N]           (perm[p] = user index of tree position p)
@@ -84,7 +88,7 @@ def write(H: HMatrix, path: str, seed: int = 0) -> None:
     nodes = np.zeros(nn, dtype=_node_dt(H.dim))
     nodes["off"], nodes["size"], nodes["lo"], nodes["hi"] = t.off, t.size, t.lo, t.hi
     ints = np.array([H.n, H.dim, t.L, H.ell, H.leaf_size, H.kernel, len(lr), len(dn),
-                     H.fmt_mask, pos, dpos, nn, seed, 0, 0, 0], dtype="<i8")
+                     H.fmt_mask, pos, dpos, nn, seed, t.step, 0, 0], dtype="<i8")
     reals = np.array([H.eta, H.tol, H.kernel_param, H.norm_Ht, 0, 0, 0, 0], dtype="<f8")
     with open(path, "wb") as f:
         f.write(MAGIC)
@@ -123,7 +127,7 @@ def read(path: str) -> HMatrix:
     if p != len(data):
         raise ValueError("trailing or missing bytes in H_h file")
     tree = Tree(L=L, perm=perm, off=nodes["off"].astype(np.int64), size=nodes["size"].astype(np.int64),
-                lo=np.array(nodes["lo"]), hi=np.array(nodes["hi"]))
+                lo=np.array(nodes["lo"]), hi=np.array(nodes["hi"]), step=max(1, int(ints[13])))
     H = HMatrix(n=n, dim=dim, kernel=kernel, kernel_param=float(reals[2]), leaf_size=leaf,
                 eta=float(reals[0]), ell=ell, tol=float(reals[1]), fmt_mask=mask, points=pts,
                 tree=tree, norm_Ht=float(reals[3]))

@@ -20,6 +20,12 @@ l >= 1 becomes
 and otherwise its four child pairs are visited.  ell = L gives an H_s
 matrix and ell = 0 a HODLR matrix (Section 3.2 special cases).
 
+On a 2^d-tree (tree.step = d, levels in binary-level form) only the levels
+that are multiples of d are tree levels: a pair is refined into the
+2^d x 2^d pairs of its clusters' children d binary levels down, ell is
+given as a binary level (d times the tree level), and pairs with an empty
+cluster are dropped (they hold no entries).
+
 Sparsity constants C', C'', C''' (Eqs. 2.3, 2.5, 2.8) in closed form, and the
 measured C_sp(l) = max over row clusters i at level l of the number of
 admissible blocks in row i (reading R3).
@@ -53,8 +59,18 @@ def dist(t: Tree, n1: int, n2: int) -> float:
     return math.sqrt(s)
 
 
+# On the 2^d-tree the clusters are congruent cells, and at eta = sqrt(d) two
+# cells one cell apart meet Eq. 2.2 with equality (the case the closed forms
+# of Eqs. 2.3 and 2.5 count as admissible); rounding decides such a tie
+# either way, so there the comparison carries a relative slack of 1e-12.
+TIE_SLACK_2D = 1.0 + 1e-12
+
+
 def adm_s(t: Tree, n1: int, n2: int, eta: float) -> bool:
-    return min(diam(t, n1), diam(t, n2)) <= eta * dist(t, n1, n2)
+    rhs = eta * dist(t, n1, n2)
+    if t.step > 1:
+        rhs = rhs * TIE_SLACK_2D
+    return min(diam(t, n1), diam(t, n2)) <= rhs
 
 
 @dataclass
@@ -66,14 +82,16 @@ class Partition:
 
 
 def partition(t: Tree, eta: float, ell: int) -> Partition:
-    L = t.L
-    if not (0 <= ell <= L):
-        raise ValueError("switch level must satisfy 0 <= ell <= L")
+    L, step = t.L, t.step
+    if not (0 <= ell <= L) or ell % step:
+        raise ValueError("switch level must satisfy 0 <= ell <= L (a tree level)")
     P = Partition(L=L, ell=ell)
     stack = [(0, 0, 0)]
     while stack:
         l, i, j = stack.pop()
         ni, nj = t.node(l, i), t.node(l, j)
+        if step > 1 and (t.size[ni] == 0 or t.size[nj] == 0):
+            continue
         if l >= 1:
             if l <= ell and adm_s(t, ni, nj, eta):
                 P.lowrank.append((l, i, j, KIND_STD))
@@ -88,9 +106,10 @@ def partition(t: Tree, eta: float, ell: int) -> Partition:
             P.dense.append((l, i, j, -1 if i == j else KIND_NBR))
             continue
         # children pairs, pushed in reverse so they pop in (0,0),(0,1),(1,0),(1,1) order
-        for a in (1, 0):
-            for b in (1, 0):
-                stack.append((l + 1, 2 * i + a, 2 * j + b))
+        c = 1 << step
+        for a in range(c - 1, -1, -1):
+            for b in range(c - 1, -1, -1):
+                stack.append((l + step, c * i + a, c * j + b))
     return P
 
 

@@ -52,7 +52,7 @@ class _Info(ctypes.Structure):
         ("tc_u_elems", ctypes.c_int64), ("tc_v_elems", ctypes.c_int64),
         ("mr_u_elems", ctypes.c_int64), ("mr_v_elems", ctypes.c_int64), ("dense_elems", ctypes.c_int64),
         ("tuned", ctypes.c_int32), ("split_positions", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32 * 4),
-        ("tc_panel_bytes", ctypes.c_int64 * 2),
+        ("tc_panel_bytes", ctypes.c_int64 * 2), ("tree_step", ctypes.c_int32), ("pad_", ctypes.c_int32),
     ]
 
 
@@ -64,6 +64,7 @@ def _load():
     P, I64, I32, U32, U64, D = c.c_void_p, c.c_int64, c.c_int, c.c_uint32, c.c_uint64, c.c_double
     sig = {
         "hh_build": (I32, [P, I64, I32, I32, D, I32, D, I32, D, U32, U64, I32, c.POINTER(P)]),
+        "hh_build_ex": (I32, [P, I64, I32, I32, D, I32, D, I32, D, U32, U64, I32, I32, c.POINTER(P)]),
         "hh_load": (I32, [c.c_char_p, I32, c.POINTER(P)]),
         "hh_reencode": (I32, [P, U32, I32, c.POINTER(P)]),
         "hh_optimal_switch_level": (I32, [P, I64, I32, I32, D, I32, D, D, U32, U64, c.POINTER(I32),
@@ -146,16 +147,21 @@ class HMatrix:
     @classmethod
     def build(cls, points, kernel: int = INV_R, kernel_param: float = 1.0, leaf_size: int = 128,
               eta: float = 1.0, switch_level: int = -1, tol: float = 1e-6, fmt_mask: int = F64 | F32 | F16 | BF16,
-              seed: int = 0, device: int | None = None) -> "HMatrix":
+              seed: int = 0, device: int | None = None, tree: str = "kd") -> "HMatrix":
+        """hh_build_ex; tree "kd" (binary KD bisection) or "2d" (the balanced
+        2^d-tree, switch_level in its levels)."""
         pts = np.ascontiguousarray(points.cpu().numpy() if isinstance(points, torch.Tensor) else points,
                                    dtype=np.float64)
         if pts.ndim != 2:
             raise ValueError("points must be (n, dim)")
+        if tree not in ("kd", "2d"):
+            raise ValueError("tree must be 'kd' or '2d'")
         if device is None:
             device = torch.cuda.current_device() if torch.cuda.is_available() else -1
         out = ctypes.c_void_p()
-        _check(_L().hh_build(pts.ctypes.data, pts.shape[0], pts.shape[1], kernel, kernel_param, leaf_size,
-                             eta, switch_level, tol, fmt_mask, seed, device, ctypes.byref(out)))
+        _check(_L().hh_build_ex(pts.ctypes.data, pts.shape[0], pts.shape[1], kernel, kernel_param, leaf_size,
+                                eta, switch_level, tol, fmt_mask, seed, 1 if tree == "2d" else 0, device,
+                                ctypes.byref(out)))
         return cls(out.value, device)
 
     @classmethod

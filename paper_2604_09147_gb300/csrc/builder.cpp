@@ -112,6 +112,74 @@ void build_tree(const double* pts, int64_t n, int dim, int leaf, HostMatrix& h) 
   for (int64_t q = 0; q < n; ++q) h.perm[q] = static_cast<int32_t>(perm[q]);
 }
 
+// The balanced 2^d-tree (Section 2.1) held in the same heap: binary level b
+// splits its cell at the midpoint of axis b mod dim (a point goes up when its
+// coordinate is >= the midpoint; each half keeps its parent's order), so
+// 2^d-tree level l is binary level dim * l.  The root cell is the smallest
+// axis-aligned hypercube around the points; the depth is the smallest l2
+// with ceil(n / 2^{dim l2}) <= leaf.  Cells may be empty.  A cluster's
+// geometry (node_lo / node_hi) is its cell, the hypercube of Section 2.1's
+// analysis.
+void build_tree_2d(const double* pts, int64_t n, int dim, int leaf, HostMatrix& h) {
+  int l2 = 0;
+  while (dim * l2 < 46 && ((n + (int64_t(1) << (dim * l2)) - 1) >> (dim * l2)) > leaf) ++l2;
+  const int L = dim * l2;
+  const int64_t nn = (int64_t(2) << L) - 1;
+  h.L = L;
+  h.step = dim;
+  h.node_off.assign(nn, 0);
+  h.node_size.assign(nn, 0);
+  h.node_lo.assign(nn * dim, 0.0);
+  h.node_hi.assign(nn * dim, 0.0);
+  std::vector<double>& clo = h.node_lo;  // cells
+  std::vector<double>& chi = h.node_hi;
+  double half = 0.0;
+  std::vector<double> mn(dim), mx(dim);
+  for (int d = 0; d < dim; ++d) mn[d] = mx[d] = pts[d];
+  for (int64_t q = 0; q < n; ++q)
+    for (int d = 0; d < dim; ++d) {
+      mn[d] = std::min(mn[d], pts[q * dim + d]);
+      mx[d] = std::max(mx[d], pts[q * dim + d]);
+    }
+  for (int d = 0; d < dim; ++d) half = std::max(half, mx[d] - mn[d]);
+  half = 0.5 * half;
+  for (int d = 0; d < dim; ++d) {
+    const double c = 0.5 * (mn[d] + mx[d]);
+    clo[d] = c - half;
+    chi[d] = c + half;
+  }
+  std::vector<int64_t> perm(n), tmp(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  h.node_size[0] = n;
+  for (int64_t node = 0; node < nn; ++node) {
+    const int64_t o = h.node_off[node], s = h.node_size[node];
+    const int level = 63 - __builtin_clzll(static_cast<unsigned long long>(node + 1));
+    if (level == L) continue;
+    const int axis = level % dim;
+    const double mid = 0.5 * (clo[node * dim + axis] + chi[node * dim + axis]);
+    int64_t lower = 0;
+    for (int64_t q = o; q < o + s; ++q)
+      if (pts[perm[q] * dim + axis] < mid) tmp[o + lower++] = perm[q];
+    int64_t up = o + lower;
+    for (int64_t q = o; q < o + s; ++q)
+      if (!(pts[perm[q] * dim + axis] < mid)) tmp[up++] = perm[q];
+    for (int64_t q = o; q < o + s; ++q) perm[q] = tmp[q];
+    for (int c = 1; c <= 2; ++c)
+      for (int d = 0; d < dim; ++d) {
+        clo[(2 * node + c) * dim + d] = clo[node * dim + d];
+        chi[(2 * node + c) * dim + d] = chi[node * dim + d];
+      }
+    chi[(2 * node + 1) * dim + axis] = mid;
+    clo[(2 * node + 2) * dim + axis] = mid;
+    h.node_off[2 * node + 1] = o;
+    h.node_size[2 * node + 1] = lower;
+    h.node_off[2 * node + 2] = o + lower;
+    h.node_size[2 * node + 2] = s - lower;
+  }
+  h.perm.resize(n);
+  for (int64_t q = 0; q < n; ++q) h.perm[q] = static_cast<int32_t>(perm[q]);
+}
+
 // --------------------------------------------------------------- partition
 double box_diam(const HostMatrix& h, int64_t node) {
   double s = 0.0;
@@ -133,24 +201,34 @@ double box_dist(const HostMatrix& h, int64_t a, int64_t b) {
   return std::sqrt(s);
 }
 
-// Eq. 2.2, inclusive
+// Eq. 2.2, inclusive.  On the 2^d-tree the clusters are congruent cells and,
+// at eta = sqrt(d), cells one cell apart meet the condition with equality
+// (admissible in the closed forms of Eqs. 2.3 and 2.5); rounding decides
+// such a tie either way, so there the comparison carries a relative slack
+// of 1e-12.
 bool adm_s(const HostMatrix& h, int64_t a, int64_t b, double eta) {
-  return std::min(box_diam(h, a), box_diam(h, b)) <= eta * box_dist(h, a, b);
+  double rhs = eta * box_dist(h, a, b);
+  if (h.step > 1) rhs = rhs * (1.0 + 1e-12);
+  return std::min(box_diam(h, a), box_diam(h, b)) <= rhs;
 }
 
 struct Pair {
   int level, i, j, kind;  // kind: LR kinds, or -1 diagonal dense / KIND_NBR dense candidate
 };
 
+// On a 2^d-tree (h.step = dim) a pair is refined into the 2^d x 2^d pairs of
+// its clusters' children step binary levels down, and pairs with an empty
+// cluster are dropped.
 void hybrid_partition(const HostMatrix& h, double eta, int ell, std::vector<Pair>& lr,
                       std::vector<Pair>& dense) {
-  const int L = h.L;
+  const int L = h.L, step = h.step;
   std::vector<Pair> stack{{0, 0, 0, 0}};
   while (!stack.empty()) {
     Pair p = stack.back();
     stack.pop_back();
     const int l = p.level;
     const int64_t ni = (int64_t(1) << l) - 1 + p.i, nj = (int64_t(1) << l) - 1 + p.j;
+    if (step > 1 && (h.node_size[ni] == 0 || h.node_size[nj] == 0)) continue;
     if (l >= 1) {
       if (l <= ell && adm_s(h, ni, nj, eta)) {
         lr.push_back({l, p.i, p.j, KIND_STD});
@@ -169,8 +247,9 @@ void hybrid_partition(const HostMatrix& h, double eta, int ell, std::vector<Pair
       dense.push_back({l, p.i, p.j, p.i == p.j ? -1 : KIND_NBR});
       continue;
     }
-    for (int a = 1; a >= 0; --a)
-      for (int b = 1; b >= 0; --b) stack.push_back({l + 1, 2 * p.i + a, 2 * p.j + b, 0});
+    const int c = 1 << step;
+    for (int a = c - 1; a >= 0; --a)
+      for (int b = c - 1; b >= 0; --b) stack.push_back({l + step, c * p.i + a, c * p.j + b, 0});
   }
 }
 
@@ -476,10 +555,17 @@ void build(const double* points, int64_t n, int dim, const BuildParams& p, HostM
   h.fmt_mask = p.fmt_mask | 1u;
   h.seed = p.seed;
   h.points.assign(points, points + n * dim);
-  build_tree(points, n, dim, p.leaf, h);
+  if (p.tree == 1)
+    build_tree_2d(points, n, dim, p.leaf, h);
+  else if (p.tree == 0)
+    build_tree(points, n, dim, p.leaf, h);
+  else
+    throw std::invalid_argument("unknown tree kind");
   if (h.L + 1 > 47) throw std::invalid_argument("tree too deep");
-  int ell = p.ell < 0 ? h.L / 2 : p.ell;
-  if (ell > h.L) throw std::domain_error("switch level exceeds the tree depth L");
+  // ell in tree levels, stored as a binary level
+  int ell = (p.ell < 0 ? (h.L / h.step) / 2 : p.ell);
+  if (ell > h.L / h.step) throw std::domain_error("switch level exceeds the tree depth L");
+  ell *= h.step;
   h.ell = ell;
 
   std::vector<Pair> lrp, dnp;
@@ -653,7 +739,11 @@ void reencode(const HostMatrix& src, uint32_t fmt_mask, int threads, HostMatrix&
 int optimal_switch_level(const double* points, int64_t n, int dim, const BuildParams& p, std::vector<double>& gains,
                          int& depth) {
   if (n < 1 || dim < 1 || p.leaf < 1) throw std::invalid_argument("bad sizes");
-  const int L = tree_depth(n, p.leaf);
+  int L = tree_depth(n, p.leaf);  // in tree levels
+  if (p.tree == 1) {
+    L = 0;
+    while (dim * L < 46 && ((n + (int64_t(1) << (dim * L)) - 1) >> (dim * L)) > p.leaf) ++L;
+  }
   depth = L;
   gains.assign(static_cast<size_t>(L) + 1, std::nan(""));
   auto storage_at = [&](int ell) {

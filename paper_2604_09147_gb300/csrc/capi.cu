@@ -1003,14 +1003,22 @@ const char* hh_last_error(void) { return g_last_error.c_str(); }
 int hh_build(const double* points, int64_t n, int dim, int kernel, double kernel_param, int leaf_size,
              double eta, int switch_level, double tol, uint32_t fmt_mask, uint64_t seed, int device,
              hh_handle* out) {
+  return hh_build_ex(points, n, dim, kernel, kernel_param, leaf_size, eta, switch_level, tol, fmt_mask, seed,
+                     HH_TREE_KD, device, out);
+}
+
+int hh_build_ex(const double* points, int64_t n, int dim, int kernel, double kernel_param, int leaf_size,
+                double eta, int switch_level, double tol, uint32_t fmt_mask, uint64_t seed, int tree, int device,
+                hh_handle* out) {
   if (!out) return fail(HH_EINVAL, "out is NULL");
+  if (tree != HH_TREE_KD && tree != HH_TREE_2D) return fail(HH_EINVAL, "unknown tree kind");
   *out = nullptr;
   if (!points) return fail(HH_EINVAL, "points is NULL");
   if (device < -1) return fail(HH_EINVAL, "device must be >= -1");
   hh_matrix* h = make_handle();
   if (!h) return fail(HH_ENOMEM, "out of host memory");
   try {
-    hh::BuildParams p{kernel, kernel_param, leaf_size, eta, switch_level, tol, fmt_mask, seed, 0};
+    hh::BuildParams p{kernel, kernel_param, leaf_size, eta, switch_level, tol, fmt_mask, seed, 0, tree};
     if (const char* t = std::getenv("HH_BUILD_THREADS")) p.threads = std::atoi(t);
     hh::build(points, n, dim, p, h->H);
   } catch (const std::domain_error& e) {
@@ -1160,6 +1168,7 @@ int hh_info(hh_handle h, hh_info_t* o) {
   for (int d = 0; d < 2; ++d)
     for (int p = 1; p <= 2; ++p) o->blocks_per_sm[2 * d + p - 1] = h->blocks_per_sm[d][p];
   for (int d = 0; d < 2; ++d) o->tc_panel_bytes[d] = h->tc[d].d_img ? h->tc[d].img_bytes : 0;
+  o->tree_step = H.step;
   return HH_OK;
 }
 

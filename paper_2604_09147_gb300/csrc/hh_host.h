@@ -43,7 +43,9 @@ static_assert(sizeof(DenseBlock) == 56, "DenseBlock layout is part of the file f
 
 struct HostMatrix {
   int64_t n = 0;
-  int32_t dim = 0, L = 0, ell = 0, leaf = 0, kernel = 0;
+  // L, ell and block levels are binary levels; step = binary levels per tree
+  // level (1: binary KD tree, dim: the 2^d-tree held as a binary tree)
+  int32_t dim = 0, L = 0, ell = 0, leaf = 0, kernel = 0, step = 1;
   double eta = 0, tol = 0, kparam = 1, norm_ht = 0;
   uint32_t fmt_mask = 1;
   uint64_t seed = 0;
@@ -68,6 +70,7 @@ struct BuildParams {
   uint32_t fmt_mask;
   uint64_t seed;
   int threads;  // <= 0: hardware concurrency
+  int tree;     // 0: binary KD bisection; 1: balanced 2^d-tree (ell in its levels)
 };
 
 // Algorithm 1 + 5 + 3: throws std::runtime_error / std::invalid_argument.

@@ -39,6 +39,8 @@ void rd(FILE* f, void* p, size_t n) {
 void validate(const HostMatrix& h) {
   if (h.n < 1 || h.dim < 1 || h.dim > 3 || h.L < 0 || h.L > 46 || h.ell < 0 || h.ell > h.L)
     throw std::invalid_argument("bad header");
+  if (h.step != 1 && h.step != h.dim) throw std::invalid_argument("bad tree step");
+  if (h.L % h.step || h.ell % h.step) throw std::invalid_argument("levels are not tree levels");
   if ((int64_t)h.perm.size() != h.n || (int64_t)h.points.size() != h.n * h.dim)
     throw std::invalid_argument("bad point / permutation arrays");
   std::vector<char> seen(h.n, 0);
@@ -84,7 +86,7 @@ void save_file(const HostMatrix& h, const std::string& path) {
   const int64_t nn = (int64_t)h.node_off.size();
   int64_t ints[16] = {h.n, h.dim, h.L, h.ell, h.leaf, h.kernel, (int64_t)h.lr.size(),
                       (int64_t)h.dense.size(), (int64_t)h.fmt_mask, (int64_t)h.arena.size(),
-                      (int64_t)h.dense_data.size(), nn, (int64_t)h.seed, 0, 0, 0};
+                      (int64_t)h.dense_data.size(), nn, (int64_t)h.seed, (int64_t)h.step, 0, 0};
   double reals[8] = {h.eta, h.tol, h.kparam, h.norm_ht, 0, 0, 0, 0};
   wr(f.f, kMagic, 8);
   wr(f.f, ints, sizeof(ints));
@@ -124,6 +126,7 @@ void load_file(const std::string& path, HostMatrix& h) {
   h.fmt_mask = (uint32_t)ints[8];
   const int64_t abytes = ints[9], delems = ints[10], nn = ints[11];
   h.seed = (uint64_t)ints[12];
+  h.step = ints[13] > 0 ? (int32_t)ints[13] : 1;  // files without the field hold a binary tree
   h.eta = reals[0];
   h.tol = reals[1];
   h.kparam = reals[2];

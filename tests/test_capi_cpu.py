@@ -88,7 +88,21 @@ def test_corrupt_file_is_rejected(P, tmp_path):
     (2048, 2, W.EXP, 1.0, 64, 5, 1e-2, ALL),                  # H_s special case (ell = L)
 ])
 def test_host_builder_matches_oracle(P, tmp_path, n, dim, kernel, param, leaf, ell, tol, mask):
-    pts = W.points(n, dim, 77)
+    _builder_vs_oracle(P, tmp_path, W.points(n, dim, 77), kernel, param, leaf, ell, tol, mask)
+
+
+@pytest.mark.parametrize("n,dim,kernel,param,leaf,ell,tol,mask", [
+    (2048, 3, W.INV_R, 1.0, 64, 3, 1e-5, ALL),   # the paper's sphere-surface set in 3-D
+    (2048, 2, W.LOG, 1.0, 64, 3, 1e-5, ALL),     # and on the unit circle
+])
+def test_host_builder_matches_oracle_on_sphere(P, tmp_path, n, dim, kernel, param, leaf, ell, tol, mask):
+    pts = W.sphere_points(n, dim, 78)
+    assert np.allclose(np.linalg.norm(pts, axis=1), 1.0)
+    _builder_vs_oracle(P, tmp_path, pts, kernel, param, leaf, ell, tol, mask)
+
+
+def _builder_vs_oracle(P, tmp_path, pts, kernel, param, leaf, ell, tol, mask):
+    n = len(pts)
     H = P.HMatrix.build(pts, kernel, param, leaf, 1.0, ell, tol, mask, device=-1)
     path = str(tmp_path / "h.hhm")
     H.save(path)

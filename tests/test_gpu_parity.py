@@ -93,6 +93,57 @@ def test_adaptive_formats_match_oracle_file(P, tmp_path, n, dim, kernel, param, 
     assert rel(H.matvec(gpu(xs)).cpu().numpy(), M.matvec(O, xs)) <= TOL32
 
 
+@pytest.mark.parametrize("dim,kernel", [(3, W.INV_R), (2, W.LOG)])
+def test_sphere_surface_points(P, tmp_path, dim, kernel):
+    """The paper's second particle set (points on the unit sphere / circle):
+    single, several and 32 columns (the tensor-core path), forward and
+    transposed, against the oracle over the same stored factors."""
+    n = 6144
+    pts = W.sphere_points(n, dim, 15)
+    O, H = oracle_pair(P, tmp_path, pts, kernel, 1.0, 64, 4, 1e-5, ALL)
+    x = W.rhs(n, 1, "uniform", 16)[:, 0]
+    check_against(P, H, O, x, TOL32)
+    xs = W.rhs(n, 4, "normal", 17)
+    assert rel(H.matvec(gpu(xs)).cpu().numpy(), M.matvec(O, xs)) <= TOL32
+    # 32 columns: tensor-core blocks bounded as in tests/test_gpu_tc.py
+    X = W.rhs(n, 32, "normal", 18)
+    Y = H.matvec(torch.from_numpy(np.ascontiguousarray(X.T)).cuda().t()).cpu().numpy()
+    H.sync_status()
+    ref = M.matvec(O, X)
+    xt = np.abs(X[O.perm])
+    ab = np.zeros_like(xt)
+    for b in O.lowrank:
+        if b.k > 0 and b.fmt in (1, 2, 3, 4) and b.row_off % 16 == 0 and b.col_off % 16 == 0:
+            w = 2.0 ** -20 if b.fmt == 1 else 2.0 ** -12
+            ab[b.row_off:b.row_off + b.m] += w * (np.abs(b.Ud()) @ (np.abs(b.Vd()).T @ xt[b.col_off:b.col_off + b.n]))
+    abu = np.empty_like(ab)
+    abu[O.perm] = ab
+    assert np.linalg.norm(Y - ref) <= TOL32 * np.linalg.norm(ref) + np.linalg.norm(abu)
+
+
+@pytest.mark.parametrize("dim,kernel", [(2, W.LOG), (3, W.INV_R)])
+def test_2d_tree_matrices(P, tmp_path, dim, kernel):
+    """Matrices on the balanced 2^d-tree (cells of any size, some empty)
+    through the same kernels: 1, 4 and 32 columns, forward and transposed."""
+    import math
+    n = 5000
+    pts = W.points(n, dim, 19) * 2 - 1
+    O = OB.build(pts, kernel, 1.0, 32, math.sqrt(dim), 1, 1e-5, ALL, tree_kind="2d")
+    path = str(tmp_path / "t2d.hhm")
+    hhfile.write(O, path)
+    H = P.HMatrix.load(path, 0)
+    assert H.info()["tree_step"] == dim
+    check_against(P, H, O, W.rhs(n, 1, "uniform", 20)[:, 0], TOL32)
+    xs = W.rhs(n, 4, "normal", 21)
+    assert rel(H.matvec(gpu(xs)).cpu().numpy(), M.matvec(O, xs)) <= TOL32
+    X = W.rhs(n, 32, "normal", 22)
+    for tr in (False, True):
+        Y = H.matvec(torch.from_numpy(np.ascontiguousarray(X.T)).cuda().t(), transpose=tr).cpu().numpy()
+        H.sync_status()
+        ref = M.matvec_T(O, X) if tr else M.matvec(O, X)
+        assert rel(Y, ref) <= 1e-5
+
+
 @pytest.mark.parametrize("n,dim,leaf,ell,mask", [
     (50, 2, 64, -1, W.F64),            # one dense block (L = 0)
     (5000, 3, 128, 3, ALL),            # ragged cluster sizes

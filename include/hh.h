@@ -186,15 +186,16 @@ int hh_reencode(hh_handle src, uint32_t fmt_mask, int device, hh_handle* out);
  * (gain 0) the algorithm moves to ell - 1 while the gain grows strictly and
  * stops at the first level whose gain does not.
  *   points ... seed   as for hh_build (switch_level is what is searched).
+ *   tree              HH_TREE_KD or HH_TREE_2D (levels are then tree levels).
  *   ell_star          receives ell*.
- *   depth             receives L (may be NULL).
+ *   depth             receives L in tree levels (may be NULL).
  *   gains             NULL or HH_MAX_LEVELS doubles: gains[l] = S_s - S_h(l)
- *                     for each level evaluated, NaN for the others.
+ *                     for each tree level evaluated, NaN for the others.
  * Host-synchronous and host-only: one construction (Algorithm 1, 5, 3) per
  * evaluated level.  HH_EINVAL for bad arguments or a tree deeper than
  * HH_MAX_LEVELS - 1. */
 int hh_optimal_switch_level(const double* points, int64_t n, int dim, int kernel, double kernel_param,
-                            int leaf_size, double eta, double tol, uint32_t fmt_mask, uint64_t seed,
+                            int leaf_size, double eta, double tol, uint32_t fmt_mask, uint64_t seed, int tree,
                             int* ell_star, int* depth, double* gains);
 
 /* hh_save -- write the handle's matrix (points, tree, block tables, factor

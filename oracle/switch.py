@@ -30,26 +30,28 @@ from __future__ import annotations
 import numpy as np
 
 from .build import build
-from .tree import tree_depth
+from .tree import tree_depth, tree_depth_2d
 
 
 def storage_gain(points: np.ndarray, kernel: int, kernel_param: float, leaf_size: int, eta: float, tol: float,
-                 fmt_mask: int, ell: int, storage_s: float) -> float:
-    """S_1(ell) - S_2(ell) = S_s - S_h(ell) for one switching level."""
-    H = build(points, kernel, kernel_param, leaf_size, eta, ell, tol, fmt_mask)
+                 fmt_mask: int, ell: int, storage_s: float, tree_kind: str = "kd") -> float:
+    """S_1(ell) - S_2(ell) = S_s - S_h(ell) for one switching level (tree levels)."""
+    H = build(points, kernel, kernel_param, leaf_size, eta, ell, tol, fmt_mask, tree_kind)
     return storage_s - H.storage()
 
 
 def optimal_switch_level(points: np.ndarray, kernel: int, kernel_param: float, leaf_size: int, eta: float,
-                         tol: float, fmt_mask: int) -> tuple[int, dict]:
-    """Algorithm 2: returns (ell*, {ell: gain} for every level it evaluated)."""
-    L = tree_depth(len(points), leaf_size)
-    Hs = build(points, kernel, kernel_param, leaf_size, eta, L, tol, fmt_mask)
+                         tol: float, fmt_mask: int, tree_kind: str = "kd") -> tuple[int, dict]:
+    """Algorithm 2: returns (ell*, {ell: gain} for every level it evaluated),
+    levels counted in the tree's own levels."""
+    n, dim = np.shape(points)
+    L = tree_depth_2d(n, dim, leaf_size) if tree_kind == "2d" else tree_depth(n, leaf_size)
+    Hs = build(points, kernel, kernel_param, leaf_size, eta, L, tol, fmt_mask, tree_kind)
     ss = Hs.storage()
     ell, s = L, 0.0
     gains = {L: 0.0}
     while ell > 0:
-        s_new = storage_gain(points, kernel, kernel_param, leaf_size, eta, tol, fmt_mask, ell - 1, ss)
+        s_new = storage_gain(points, kernel, kernel_param, leaf_size, eta, tol, fmt_mask, ell - 1, ss, tree_kind)
         gains[ell - 1] = s_new
         if s_new <= s:
             break

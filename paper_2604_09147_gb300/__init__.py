@@ -67,7 +67,7 @@ def _load():
         "hh_build_ex": (I32, [P, I64, I32, I32, D, I32, D, I32, D, U32, U64, I32, I32, c.POINTER(P)]),
         "hh_load": (I32, [c.c_char_p, I32, c.POINTER(P)]),
         "hh_reencode": (I32, [P, U32, I32, c.POINTER(P)]),
-        "hh_optimal_switch_level": (I32, [P, I64, I32, I32, D, I32, D, D, U32, U64, c.POINTER(I32),
+        "hh_optimal_switch_level": (I32, [P, I64, I32, I32, D, I32, D, D, U32, U64, I32, c.POINTER(I32),
                                           c.POINTER(I32), c.POINTER(D)]),
         "hh_save": (I32, [P, c.c_char_p]),
         "hh_info": (I32, [P, c.POINTER(_Info)]),
@@ -312,10 +312,11 @@ class HMatrix:
 
 def optimal_switch_level(points, kernel: int = INV_R, kernel_param: float = 1.0, leaf_size: int = 128,
                          eta: float = 1.0, tol: float = 1e-6, fmt_mask: int = F64 | F32 | F16 | BF16,
-                         seed: int = 0) -> tuple:
+                         seed: int = 0, tree: str = "kd") -> tuple:
     """Algorithm 2 (hh_optimal_switch_level): the switching level with the
     largest storage gain over the H_s matrix.  Returns (ell*, L, {level: gain})
-    with gain = S_s - S_h(level) in fp64 words for every level evaluated."""
+    with gain = S_s - S_h(level) in fp64 words for every level evaluated
+    (tree levels; tree "kd" or "2d")."""
     pts = np.ascontiguousarray(points.cpu().numpy() if isinstance(points, torch.Tensor) else points,
                                dtype=np.float64)
     if pts.ndim != 2:
@@ -323,8 +324,8 @@ def optimal_switch_level(points, kernel: int = INV_R, kernel_param: float = 1.0,
     ell, depth = ctypes.c_int(), ctypes.c_int()
     g = (ctypes.c_double * MAX_LEVELS)()
     _check(_L().hh_optimal_switch_level(pts.ctypes.data, pts.shape[0], pts.shape[1], kernel, kernel_param,
-                                        leaf_size, eta, tol, fmt_mask, seed, ctypes.byref(ell), ctypes.byref(depth),
-                                        g))
+                                        leaf_size, eta, tol, fmt_mask, seed, 1 if tree == "2d" else 0,
+                                        ctypes.byref(ell), ctypes.byref(depth), g))
     gains = {l: float(g[l]) for l in range(depth.value + 1) if not np.isnan(g[l])}
     return ell.value, depth.value, gains
 

@@ -1038,11 +1038,12 @@ int hh_build_ex(const double* points, int64_t n, int dim, int kernel, double ker
 }
 
 int hh_optimal_switch_level(const double* points, int64_t n, int dim, int kernel, double kernel_param,
-                            int leaf_size, double eta, double tol, uint32_t fmt_mask, uint64_t seed,
+                            int leaf_size, double eta, double tol, uint32_t fmt_mask, uint64_t seed, int tree,
                             int* ell_star, int* depth, double* gains) {
   if (!points || !ell_star) return fail(HH_EINVAL, "points or ell_star is NULL");
+  if (tree != HH_TREE_KD && tree != HH_TREE_2D) return fail(HH_EINVAL, "unknown tree kind");
   try {
-    hh::BuildParams p{kernel, kernel_param, leaf_size, eta, 0, tol, fmt_mask, seed, 0};
+    hh::BuildParams p{kernel, kernel_param, leaf_size, eta, 0, tol, fmt_mask, seed, 0, tree};
     if (const char* e = std::getenv("HH_BUILD_THREADS")) p.threads = std::atoi(e);
     std::vector<double> g;
     int L = 0;

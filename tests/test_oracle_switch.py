@@ -9,7 +9,7 @@ from oracle import build as B
 from oracle import formats as F
 from oracle import partition as PT
 from oracle import switch as S
-from oracle.tree import tree_depth
+from oracle.tree import tree_depth, tree_depth_2d
 
 ALL = W.F64 | W.F32 | W.F16 | W.BF16 | W.E4M3
 
@@ -75,16 +75,17 @@ def test_mixed_precision_can_move_the_level():
     assert eall > e64
 
 
-@pytest.mark.parametrize("case", [(4096, 2, W.INV_R, 64, 1e-6, W.F64), (2048, 3, W.EXP, 32, 1e-4, ALL)])
+@pytest.mark.parametrize("case", [(4096, 2, W.INV_R, 64, 1e-6, W.F64, "kd"), (2048, 3, W.EXP, 32, 1e-4, ALL, "kd"),
+                                  (4096, 2, W.LOG, 16, 1e-6, ALL, "2d")])
 def test_library_matches_oracle(case):
     """hh_optimal_switch_level against the oracle: the same tree depth and
     level; gains equal up to the rank differences of the two compressions."""
     P = pytest.importorskip("paper_2604_09147_gb300")
-    n, dim, kern, leaf, tol, mask = case
+    n, dim, kern, leaf, tol, mask, tree = case
     pts = W.points(n, dim, 13)
-    ell, depth, gains = P.optimal_switch_level(pts, kern, 1.0, leaf, 1.0, tol, mask)
-    o_ell, o_gains = S.optimal_switch_level(pts, kern, 1.0, leaf, 1.0, tol, mask)
-    assert depth == tree_depth(n, leaf)
+    ell, depth, gains = P.optimal_switch_level(pts, kern, 1.0, leaf, 1.0, tol, mask, tree=tree)
+    o_ell, o_gains = S.optimal_switch_level(pts, kern, 1.0, leaf, 1.0, tol, mask, tree_kind=tree)
+    assert depth == (tree_depth_2d(n, dim, leaf) if tree == "2d" else tree_depth(n, leaf))
     assert ell == o_ell
     assert set(gains) == set(o_gains)
     scale = max(abs(v) for v in o_gains.values())

@@ -159,3 +159,31 @@ def test_table_2_trend_s1_over_s2_above_one(tmp_path):
         s2 = sum(b.k * (b.m + b.n) for b in Gh.lowrank if b.kind != PT.KIND_STD)
         assert ss - sh == pytest.approx(s1 - s2, rel=1e-9)
         assert s1 / s2 > 1.0
+
+
+@pytest.mark.parametrize("name", ["one_point", "n_equals_leaf", "duplicates", "one_dim", "line_in_3d"])
+def test_degenerate_point_sets(tmp_path, name):
+    """One point, a single leaf, repeated points, d = 1 and a line in 3-D
+    (most cells empty): the library and the oracle agree and the blocks
+    cover N x N once."""
+    P = pytest.importorskip("paper_2604_09147_gb300")
+    pts = {"one_point": np.array([[0.5, 0.5]]),
+           "n_equals_leaf": W.points(32, 2, 1),
+           "duplicates": np.repeat(W.points(40, 3, 2), 5, axis=0),
+           "one_dim": W.points(500, 1, 3),
+           "line_in_3d": np.c_[np.linspace(0, 1, 300), np.zeros(300), np.zeros(300)]}[name]
+    eta = math.sqrt(pts.shape[1])
+    H = P.HMatrix.build(pts, W.EXP, 1.0, 32, eta, -1, 1e-6, ALL, device=-1, tree="2d")
+    path = str(tmp_path / "d.hhm")
+    H.save(path)
+    G = hhfile.read(path)
+    O = OB.build(pts, W.EXP, 1.0, 32, eta, -1, 1e-6, ALL, tree_kind="2d")
+    assert np.array_equal(G.perm, O.perm)
+    assert {(b.level, b.i, b.j) for b in G.lowrank} == {(b.level, b.i, b.j) for b in O.lowrank}
+    n = len(pts)
+    cover = np.zeros((n, n), dtype=np.int32)
+    for b in G.lowrank:
+        cover[b.row_off:b.row_off + b.m, b.col_off:b.col_off + b.n] += 1
+    for d in G.dense:
+        cover[d.row_off:d.row_off + d.m, d.col_off:d.col_off + d.n] += 1
+    assert np.all(cover == 1)

@@ -242,6 +242,24 @@ int hh_matvec(hh_handle h, const double* x, double* y, int nrhs, int64_t ldx, in
 int hh_matvec_T(hh_handle h, const double* ybar, double* xbar, int nrhs, int64_t ldy,
                 int64_t ldx, void* stream);
 
+/* hh_solve_cg -- conjugate gradients (Hestenes-Stiefel) for
+ * (A_h + shift I) x = b: the fast iterative solver the product enables
+ * (Section 5, end).  Meant for symmetric positive definite kernels (exp(-r),
+ * Gaussian), whose A_h is symmetric up to the compression tolerance.
+ *   b       device, n (caller's order); not modified.
+ *   x       device, n: the initial guess on entry, the solution on return.
+ *   shift   added to the diagonal (0 for A_h itself).
+ *   rtol    stop when ||r_k|| <= rtol ||b|| (recursively updated residual).
+ *   max_iter, iters, relres   iteration cap; iterations done and the final
+ *           ||r|| / ||b|| (either pointer may be NULL).
+ * Each iteration is one forward product (the streaming passes, on the
+ * handle's workspace) and two dot products read back to the host (the call
+ * synchronises `stream`); three n-vectors are allocated for the call.
+ * HH_EINVAL if b and x overlap or the iteration breaks down
+ * (p^T (A_h + shift I) p <= 0: not positive definite). */
+int hh_solve_cg(hh_handle h, const double* b, double* x, double shift, double rtol, int max_iter,
+                int* iters, double* relres, void* stream);
+
 /* hh_workspace_bytes -- bytes of device workspace hh_matvec_ws needs. */
 int hh_workspace_bytes(hh_handle h, size_t* bytes);
 

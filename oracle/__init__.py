@@ -22,6 +22,8 @@ no blocking, fusion or reordering beyond what the paper states:
   matvec.py     Algorithm 4 (b = H_hat x), its transpose, dense assembly.
   switch.py     Algorithm 2 (the switching level with the largest storage
                 gain over the H_s matrix).
+  solve.py      conjugate gradients for (H_hat + shift I) x = b on
+                Algorithm 4's product.
   bounds.py     Theorem 4.2 / 4.4 error bounds and Lemma 3.1.
   hhfile.py     reader/writer of the serialized H_h file (the input both the
                 oracle and the CUDA path consume).

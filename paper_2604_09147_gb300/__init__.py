@@ -75,6 +75,7 @@ def _load():
         "hh_matvec": (I32, [P, P, P, I32, I64, I64, P]),
         "hh_matvec_T": (I32, [P, P, P, I32, I64, I64, P]),
         "hh_workspace_bytes": (I32, [P, c.POINTER(c.c_size_t)]),
+        "hh_solve_cg": (I32, [P, P, P, D, D, I32, c.POINTER(I32), c.POINTER(D), P]),
         "hh_matvec_ws": (I32, [P, I32, P, P, I32, I64, I64, P, c.c_size_t, P]),
         "hh_matvec_host": (I32, [P, I32, P, P, I32, P]),
         "hh_matvec_timed": (I32, [P, I32, P, P, I32, I64, I64, P, c.POINTER(c.c_float)]),
@@ -305,6 +306,19 @@ class HMatrix:
         _check(_L().hh_matvec_stages(self._h, 1 if transpose else 0, xv.data_ptr(), y.data_ptr(), nrhs, ldx, ldy,
                                      _stream_ptr(x.device), ms))
         return [float(v) for v in ms]
+
+    def solve_cg(self, b: torch.Tensor, shift: float = 0.0, rtol: float = 1e-8, max_iter: int = 1000,
+                 x0: torch.Tensor | None = None) -> tuple:
+        """hh_solve_cg: conjugate gradients for (A_h + shift I) x = b on the
+        device; returns (x, iterations, final relative residual)."""
+        if b.dim() != 1 or b.shape[0] != self.n or b.dtype != torch.float64 or not b.is_cuda:
+            raise ValueError("b must be a cuda float64 vector of length n")
+        b = b.contiguous()
+        x = torch.zeros_like(b) if x0 is None else x0.detach().clone().contiguous()
+        it, res = ctypes.c_int(), ctypes.c_double()
+        _check(_L().hh_solve_cg(self._h, b.data_ptr(), x.data_ptr(), float(shift), float(rtol), int(max_iter),
+                                ctypes.byref(it), ctypes.byref(res), _stream_ptr(b.device)))
+        return x, it.value, res.value
 
     def sync_status(self) -> None:
         _check(_L().hh_sync_status(self._h, _stream_ptr(self.device)))

@@ -1196,6 +1196,77 @@ int hh_matvec_T(hh_handle h, const double* ybar, double* xbar, int nrhs, int64_t
   return run_product(h, 1, ybar, xbar, nrhs, ldy, ldx, h->d_ws, h->ws_bytes, (cudaStream_t)stream, nullptr, kAuto);
 }
 
+int hh_solve_cg(hh_handle h, const double* b, double* x, double shift, double rtol, int max_iter, int* iters,
+                double* relres, void* stream) {
+  if (!h || !b || !x) return fail(HH_EINVAL, "null argument");
+  if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data (built with device = -1)");
+  if (max_iter < 0 || !(rtol >= 0.0)) return fail(HH_EINVAL, "max_iter < 0 or rtol < 0");
+  const int64_t n = h->H.n;
+  const size_t nb = static_cast<size_t>(n) * sizeof(double);
+  if ((const char*)b < (const char*)x + nb && (const char*)x < (const char*)b + nb)
+    return fail(HH_EINVAL, "b and x overlap");
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  double* scratch = nullptr;  // r, p, q, dot partials
+  if (cudaMalloc(&scratch, 3 * nb + sizeof(double) * hh::dev::kDotBlocks) != cudaSuccess) {
+    if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+    return fail(HH_ENOMEM, "cannot allocate the solver vectors");
+  }
+  double* r = scratch;
+  double* p = r + n;
+  double* q = p + n;
+  double* part = q + n;
+  std::vector<double> hpart(hh::dev::kDotBlocks);
+  int rc = HH_OK;
+  cudaError_t e = cudaSuccess;
+  auto dot = [&](const double* u, const double* v) {
+    double s = 0.0;
+    if (e == cudaSuccess) e = hh::dev::launch_dot(u, v, n, part, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hpart.data(), part, sizeof(double) * hh::dev::kDotBlocks,
+                                              cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (double v2 : hpart) s += v2;  // block order: deterministic
+    return s;
+  };
+  auto apply = [&](const double* in, double* out) {  // out = (A_h + shift I) in
+    if (e != cudaSuccess || rc != HH_OK) return;
+    rc = run_product(h, 0, in, out, 1, n, n, h->d_ws, h->ws_bytes, st);
+    if (rc == HH_OK && shift != 0.0) e = hh::dev::launch_shift(out, in, shift, n, st);
+  };
+  // r = b - (A + shift I) x, p = r
+  apply(x, q);
+  if (e == cudaSuccess && rc == HH_OK) e = cudaMemcpyAsync(r, b, nb, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && rc == HH_OK) e = hh::dev::launch_shift(r, q, -1.0, n, st);
+  if (e == cudaSuccess && rc == HH_OK) e = cudaMemcpyAsync(p, r, nb, cudaMemcpyDeviceToDevice, st);
+  const double bnorm = std::sqrt(dot(b, b));
+  double rr = dot(r, r);
+  int it = 0;
+  while (rc == HH_OK && e == cudaSuccess && it < max_iter && std::sqrt(rr) > rtol * bnorm) {
+    apply(p, q);
+    const double pq = dot(p, q);
+    if (rc != HH_OK || e != cudaSuccess) break;
+    if (!(pq > 0.0)) {
+      rc = fail(HH_EINVAL, "conjugate gradients broke down: p^T (A + shift I) p <= 0");
+      break;
+    }
+    const double alpha = rr / pq;
+    e = hh::dev::launch_cg_step(x, r, p, q, alpha, n, st);
+    const double rr_new = dot(r, r);
+    if (e == cudaSuccess) e = hh::dev::launch_cg_dir(p, r, rr_new / rr, n, st);
+    rr = rr_new;
+    ++it;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(scratch);
+  if (rc == HH_OK && e != cudaSuccess) rc = fail(HH_ECUDA, std::string("solver launch failed: ") + cudaGetErrorString(e));
+  if (iters) *iters = it;
+  if (relres) *relres = bnorm > 0.0 ? std::sqrt(rr) / bnorm : 0.0;
+  if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+  return rc;
+}
+
 int hh_matvec_ws(hh_handle h, int transpose, const double* in, double* out, int nrhs, int64_t ld_in,
                  int64_t ld_out, void* workspace, size_t workspace_bytes, void* stream) {
   if (!h) return fail(HH_EINVAL, "null handle");

@@ -79,6 +79,14 @@ cudaError_t launch_batch_prep(const double* x, const int64_t* xofs, const int32_
 cudaError_t launch_batch_finish(const double* acc, const int64_t* xofs, const int32_t* perm, const int64_t* pofs,
                                 const int64_t* ns, int count, int64_t np, double* y, cudaStream_t st);
 
+// ---- vector kernels of the conjugate-gradient solver (kernels.cu) ----
+constexpr int kDotBlocks = 256;  // a dot product writes kDotBlocks partial sums
+cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* partials, cudaStream_t st);
+cudaError_t launch_shift(double* q, const double* p, double shift, int64_t n, cudaStream_t st);  // q += shift p
+cudaError_t launch_cg_step(double* x, double* r, const double* p, const double* q, double alpha, int64_t n,
+                           cudaStream_t st);  // x += alpha p, r -= alpha q
+cudaError_t launch_cg_dir(double* p, const double* r, double beta, int64_t n, cudaStream_t st);  // p = r + beta p
+
 // ---- tensor-core path for many right-hand sides (tc.cu) ----
 // A piece: ranks [r0, r0 + k) of one low-rank block stored in fp32, fp16, bf16
 // or e4m3.  f1 / f2 point at the piece's first rank column of the phase-1

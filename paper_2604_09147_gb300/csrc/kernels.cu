@@ -171,3 +171,86 @@ cudaError_t launch_batch_finish(const double* acc, const int64_t* xofs, const in
 
 }  // namespace dev
 }  // namespace hh
+
+// ---------------------------------------------------------------------------
+// Vector kernels of the conjugate-gradient solver (capi.cu: hh_solve_cg).
+// Dot products are reduced per block into `partials` (block b writes
+// partials[b]); the caller adds the partials in block order, so the result
+// does not depend on scheduling.
+namespace hh {
+namespace dev {
+namespace {
+
+constexpr int kVecThreads = 256;
+
+__global__ void dot_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                           double* __restrict__ partials) {
+  __shared__ double red[kVecThreads];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    s += a[i] * b[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kVecThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+// q += shift p
+__global__ void shift_kernel(double* __restrict__ q, const double* __restrict__ p, double shift, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    q[i] += shift * p[i];
+}
+
+// x += alpha p, r -= alpha q
+__global__ void cg_step_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                               const double* __restrict__ q, double alpha, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+  }
+}
+
+// p = r + beta p
+__global__ void cg_dir_kernel(double* __restrict__ p, const double* __restrict__ r, double beta, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    p[i] = r[i] + beta * p[i];
+}
+
+int vec_blocks(int64_t n) {
+  int64_t b = (n + kVecThreads - 1) / kVecThreads;
+  if (b > kDotBlocks) b = kDotBlocks;
+  return b < 1 ? 1 : static_cast<int>(b);
+}
+
+}  // namespace
+
+cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* partials, cudaStream_t st) {
+  dot_kernel<<<kDotBlocks, kVecThreads, 0, st>>>(a, b, n, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift(double* q, const double* p, double shift, int64_t n, cudaStream_t st) {
+  shift_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>(q, p, shift, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_step(double* x, double* r, const double* p, const double* q, double alpha, int64_t n,
+                           cudaStream_t st) {
+  cg_step_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>(x, r, p, q, alpha, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_dir(double* p, const double* r, double beta, int64_t n, cudaStream_t st) {
+  cg_dir_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>(p, r, beta, n);
+  return cudaGetLastError();
+}
+
+}  // namespace dev
+}  // namespace hh

@@ -1,0 +1,62 @@
+"""Conjugate gradients on the GPU product (hh_solve_cg) against the oracle's
+conjugate gradients on the same stored factors."""
+import numpy as np
+import pytest
+
+import hh_workloads as W
+from oracle import build as OB
+from oracle import hhfile
+from oracle import matvec as M
+from oracle import solve as S
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+ALL = W.F64 | W.F32 | W.F16 | W.BF16 | W.E4M3
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_09147_gb300 import build as b
+    b.build()
+    import paper_2604_09147_gb300 as pkg
+    return pkg
+
+
+@pytest.mark.parametrize("mask,res_tol", [(W.F64, 1e-9), (ALL, 1e-5)])
+def test_cg_matches_oracle(P, tmp_path, mask, res_tol):
+    """(H_hat + I) x = b, Gaussian kernel: the GPU solver stops at the
+    requested recursive residual within a couple of iterations of the
+    oracle, and its solution satisfies the oracle's operator up to the
+    product's own accuracy (1e-12 fp64 path, 1e-6 adaptive path)."""
+    n = 6000
+    O = OB.build(W.points(n, 3, 53), W.GAUSS, 0.05, 64, 1.0, 2, 1e-8, mask)
+    path = str(tmp_path / "s.hhm")
+    hhfile.write(O, path)
+    H = P.HMatrix.load(path, 0)
+    b = W.rhs(n, 1, "uniform", 54)[:, 0]
+    xo, ito, reso = S.cg(O, b, shift=1.0, rtol=1e-10, max_iter=500)
+    xg, itg, resg = H.solve_cg(torch.from_numpy(b).cuda(), shift=1.0, rtol=1e-10, max_iter=500)
+    H.sync_status()
+    assert resg <= 1e-10 and abs(itg - ito) <= 2
+    x = xg.cpu().numpy()
+    r = b - (M.matvec(O, x) + x)
+    assert np.linalg.norm(r) <= res_tol * np.linalg.norm(b)
+    if mask == W.F64:
+        assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
+    # restarting from the solution takes no iteration
+    _, it2, _ = H.solve_cg(torch.from_numpy(b).cuda(), shift=1.0, rtol=max(resg, 1e-10) * 1.01, x0=xg)
+    assert it2 == 0
+
+
+def test_cg_argument_errors(P, tmp_path):
+    O = OB.build(W.points(500, 2, 55), W.EXP, 1.0, 64, 1.0, 1, 1e-6, W.F64)
+    path = str(tmp_path / "e.hhm")
+    hhfile.write(O, path)
+    H = P.HMatrix.load(path, 0)
+    b = torch.ones(500, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.HHError):
+        H.solve_cg(b, max_iter=-1)
+    x, it, res = H.solve_cg(torch.zeros(500, dtype=torch.float64, device="cuda"))
+    assert it == 0 and res == 0.0 and float(x.abs().max()) == 0.0

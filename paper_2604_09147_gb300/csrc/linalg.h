@@ -1,6 +1,9 @@
 // Small dense linear algebra for the host builder: column-major matrices,
-// Householder QR, column-pivoted QR with a Frobenius stopping rule,
-// one-sided Jacobi SVD and adaptive cross approximation (ACA).
+// a register-blocked matrix product, blocked Householder QR, column-pivoted
+// QR with a Frobenius stopping rule, one-sided Jacobi SVD and adaptive cross
+// approximation (ACA).  Every routine fixes its order of operations and is
+// compiled without floating-point contraction, so results are the same on
+// every host.
 #pragma once
 
 #include <cstdint>
@@ -21,16 +24,28 @@ struct Mat {
   const double* col(int64_t j) const { return a.data() + j * m; }
 };
 
-// C[:, 0:r] = A * B[:, 0:r]  (A m x k, B k x >= r, C m x >= r, preallocated)
-void gemm_nn(const Mat& A, const Mat& B, int64_t r, Mat& C);
+// C (m x n, leading dimension ldc) += alpha * A * B with A(i, q) =
+// A[i * a_rs + q * a_cs] (m x k) and B(q, j) = B[q * b_rs + j * b_cs] (k x n):
+// the strides select plain or transposed operands.
+void gemm(int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t a_rs, int64_t a_cs,
+          const double* B, int64_t b_rs, int64_t b_cs, double* C, int64_t ldc);
 
-// Thin Householder QR of A (m x k, m >= k): A = Q R, Q (m x k) orthonormal,
-// R (k x k) upper triangular.
-void qr_thin(const Mat& A, Mat& Q, Mat& R);
+// Householder QR of A (m x k, m >= k) in place: R in the upper triangle, the
+// reflectors' tails below it (H_j = I - tau_j v_j v_j^T, v_j[j] = 1), so that
+// A_in = H_0 H_1 ... H_{k-1} [R; 0].
+void qr_factor(Mat& A, std::vector<double>& tau);
 
-// One-sided (Hestenes) Jacobi SVD of A (m x n, m >= n): A = U diag(s) V^T,
-// singular values in descending order, U (m x n), V (n x n).
-void svd_jacobi(const Mat& A, Mat& U, std::vector<double>& s, Mat& V);
+// The k x k upper triangular R of a factored matrix.
+Mat qr_r(const Mat& F);
+
+// out (m x r) = Q [X; 0] for X (k x r) with Q = H_0 ... H_{k-1} of a
+// factored m x k matrix: the thin Q times X without forming Q.
+void qr_apply_q(const Mat& F, const std::vector<double>& tau, const Mat& X, Mat& out);
+
+// One-sided (Hestenes) Jacobi SVD of A (m x n, m >= n), left side only:
+// A = W diag(s) Z^T with s descending and W (m x n) orthonormal (columns of
+// zero singular values are zero); Z is not formed (Z S = A^T W).
+void svd_left(const Mat& A, Mat& W, std::vector<double>& s);
 
 // Smallest r with sqrt(sum_{i>=r} s_i^2) <= eps * sqrt(sum_i s_i^2)
 // (s sorted descending); 0 for an all-zero s.

@@ -251,11 +251,16 @@ void svd_left(const Mat& A, Mat& W, std::vector<double>& s) {
   W = A;
   const double tol = 1e-15;
   std::vector<double> nrm(static_cast<size_t>(n));
+  // each sweep visits every pair once, block pair by block pair, so that the
+  // two column blocks of a block pair stay in cache (about 512 KB)
+  const int64_t bs = std::max<int64_t>(8, std::min<int64_t>(128, 32768 / std::max<int64_t>(m, 1)));
   for (int sweep = 0; sweep < 80; ++sweep) {
     bool rotated = false;
     for (int64_t j = 0; j < n; ++j) nrm[j] = dot(W.col(j), W.col(j), m);
-    for (int64_t p = 0; p + 1 < n; ++p) {
-      for (int64_t q = p + 1; q < n; ++q) {
+    for (int64_t b0 = 0; b0 < n; b0 += bs)
+    for (int64_t c0 = b0; c0 < n; c0 += bs)
+    for (int64_t p = b0; p < std::min(n, b0 + bs); ++p) {
+      for (int64_t q = std::max(p + 1, c0); q < std::min(n, c0 + bs); ++q) {
         const double alpha = nrm[p], beta = nrm[q];
         if (alpha == 0.0 || beta == 0.0) continue;
         const double gamma = dot(W.col(p), W.col(q), m);

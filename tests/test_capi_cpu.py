@@ -58,6 +58,10 @@ def test_argument_errors(P):
     with pytest.raises(P.HHError) as e:
         H.matvec_host(np.zeros(300))
     assert e.value.code == P.HH_ENOTSUP
+    # conjugate gradients: null vectors, then a handle without device data
+    b, x = np.ones(300), np.zeros(300)
+    assert P._L().hh_solve_cg(H._h, None, x.ctypes.data, 0.0, 1e-8, 10, None, None, None) == P.HH_EINVAL
+    assert P._L().hh_solve_cg(H._h, b.ctypes.data, x.ctypes.data, 0.0, 1e-8, 10, None, None, None) == P.HH_ENOTSUP
     with pytest.raises(P.HHError) as e:
         P.HMatrix.load("/nonexistent/file.hhm", device=-1)
     assert e.value.code == P.HH_EIO

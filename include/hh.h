@@ -192,8 +192,12 @@ int hh_reencode(hh_handle src, uint32_t fmt_mask, int device, hh_handle* out);
  *   gains             NULL or HH_MAX_LEVELS doubles: gains[l] = S_s - S_h(l)
  *                     for each tree level evaluated, NaN for the others.
  * Host-synchronous and host-only: one construction (Algorithm 1, 5, 3) per
- * evaluated level.  HH_EINVAL for bad arguments or a tree deeper than
- * HH_MAX_LEVELS - 1. */
+ * evaluated level.  A block's compression depends only on its two clusters
+ * and tol, so the evaluated levels share them: each block is compressed once,
+ * and the search holds every compressed block in fp64 in host memory until it
+ * returns (about the fp64 storage of the H_s matrix plus the near-field
+ * blocks of the levels evaluated).  HH_EINVAL for bad arguments or a tree
+ * deeper than HH_MAX_LEVELS - 1. */
 int hh_optimal_switch_level(const double* points, int64_t n, int dim, int kernel, double kernel_param,
                             int leaf_size, double eta, double tol, uint32_t fmt_mask, uint64_t seed, int tree,
                             int* ell_star, int* depth, double* gains);

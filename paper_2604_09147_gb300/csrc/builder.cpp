@@ -7,9 +7,12 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <memory>
 #include <numeric>
 #include <stdexcept>
 #include <thread>
+#include <tuple>
 
 #include "hh_host.h"
 #include "linalg.h"
@@ -258,6 +261,12 @@ struct Compressed {
   la::Mat U, V;
   std::vector<double> s;
 };
+
+// Compressions already computed, keyed by (level, i, j).  A block's
+// compression depends only on its two clusters and tol, so builds of the same
+// points, tree and tol with different switching levels (Algorithm 2) share
+// them.
+using CompressionCache = std::map<std::tuple<int, int, int>, std::shared_ptr<const Compressed>>;
 
 constexpr int64_t kDenseMax = int64_t(1) << 18;
 constexpr double kAcaShare = 0.01;
@@ -541,7 +550,8 @@ void layout_and_store(const std::vector<FactorRef>& refs, int threads, HostMatri
 
 }  // namespace
 
-void build(const double* points, int64_t n, int dim, const BuildParams& p, HostMatrix& h) {
+static void build_impl(const double* points, int64_t n, int dim, const BuildParams& p, HostMatrix& h,
+                       CompressionCache* cache) {
   auto t0 = std::chrono::steady_clock::now();
   if (n < 1 || dim < 1 || dim > 3) throw std::invalid_argument("need n >= 1 and 1 <= dim <= 3");
   if (n > (int64_t(1) << 31) - 64) throw std::invalid_argument("n too large for 32-bit positions");
@@ -599,24 +609,37 @@ void build(const double* points, int64_t n, int dim, const BuildParams& p, HostM
       nbr_idx.push_back(d);
       jobs.push_back(dnp[d]);
     }
-  std::vector<Compressed> comp(jobs.size());
-  std::vector<int64_t> order(jobs.size());
-  std::iota(order.begin(), order.end(), 0);
+  std::vector<std::shared_ptr<const Compressed>> comp(jobs.size());
+  std::vector<std::shared_ptr<Compressed>> fresh(jobs.size());
+  std::vector<int64_t> order;
   std::vector<double> cost(jobs.size());
   for (size_t b = 0; b < jobs.size(); ++b) {
+    if (cache) {
+      auto it = cache->find(std::make_tuple(jobs[b].level, jobs[b].i, jobs[b].j));
+      if (it != cache->end()) {
+        comp[b] = it->second;
+        continue;
+      }
+    }
     int64_t o1, m, o2, nn;
     rng(jobs[b].level, jobs[b].i, o1, m);
     rng(jobs[b].level, jobs[b].j, o2, nn);
     cost[b] = double(m) * double(nn);
+    fresh[b] = std::make_shared<Compressed>();
+    order.push_back(static_cast<int64_t>(b));
   }
   std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
-  parallel_for(static_cast<int64_t>(jobs.size()), p.threads, [&](int64_t t) {
+  parallel_for(static_cast<int64_t>(order.size()), p.threads, [&](int64_t t) {
     const Pair& q = jobs[order[t]];
     int64_t o1, m, o2, nn;
     rng(q.level, q.i, o1, m);
     rng(q.level, q.j, o2, nn);
-    compress_block(g, o1, m, o2, nn, p.tol, comp[order[t]]);
+    compress_block(g, o1, m, o2, nn, p.tol, *fresh[order[t]]);
   });
+  for (int64_t b : order) {
+    comp[b] = fresh[b];
+    if (cache) (*cache)[std::make_tuple(jobs[b].level, jobs[b].i, jobs[b].j)] = fresh[b];
+  }
 
   // dense blocks (diagonal; with ell == L also the leaf neighbours)
   std::vector<std::vector<double>> dvals(dnp.size());
@@ -634,13 +657,13 @@ void build(const double* points, int64_t n, int dim, const BuildParams& p, HostM
   double norm2 = 0.0;
   for (size_t b = 0; b < lrp.size(); ++b) {
     double s2 = 0.0;
-    for (double s : comp[b].s) s2 += s * s;
+    for (double s : comp[b]->s) s2 += s * s;
     bnorm[b] = std::sqrt(s2);
     norm2 += s2;
   }
   for (size_t b = lrp.size(); b < jobs.size(); ++b) {
     double s2 = 0.0;
-    for (double s : comp[b].s) s2 += s * s;
+    for (double s : comp[b]->s) s2 += s * s;
     bnorm[b] = std::sqrt(s2);
   }
   for (size_t d = 0; d < dnp.size(); ++d) {
@@ -665,7 +688,7 @@ void build(const double* points, int64_t n, int dim, const BuildParams& p, HostM
     rng(jobs[b].level, jobs[b].i, o1, m);
     rng(jobs[b].level, jobs[b].j, o2, nn);
     int f = choose_format(block_tau(p.tol, jobs[b].level, bnorm[b], h.norm_ht), h.fmt_mask);
-    const int64_t pk = comp[b].U.n;
+    const int64_t pk = comp[b]->U.n;
     if (double(pk) * double(m + nn) * fmt_bits(f) / 64.0 < double(m) * double(nn)) {
       keep.push_back({b, f});
       dense_keep[nbr_idx[q]] = 0;
@@ -684,10 +707,10 @@ void build(const double* points, int64_t n, int dim, const BuildParams& p, HostM
     B.j = q.j;
     rng(q.level, q.i, B.row_off, B.m);
     rng(q.level, q.j, B.col_off, B.n);
-    B.k = static_cast<int32_t>(comp[c.job].U.n);
+    B.k = static_cast<int32_t>(comp[c.job]->U.n);
     B.fmt = c.fmt;
     B.norm = bnorm[c.job];
-    refs[t] = {B, comp[c.job].U.a.data(), comp[c.job].V.a.data()};
+    refs[t] = {B, comp[c.job]->U.a.data(), comp[c.job]->V.a.data()};
   }
   layout_and_store(refs, p.threads, h);
 
@@ -708,6 +731,10 @@ void build(const double* points, int64_t n, int dim, const BuildParams& p, HostM
   }
   h.build_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+void build(const double* points, int64_t n, int dim, const BuildParams& p, HostMatrix& h) {
+  build_impl(points, n, dim, p, h, nullptr);
 }
 
 void reencode(const HostMatrix& src, uint32_t fmt_mask, int threads, HostMatrix& h) {
@@ -755,11 +782,12 @@ int optimal_switch_level(const double* points, int64_t n, int dim, const BuildPa
   }
   depth = L;
   gains.assign(static_cast<size_t>(L) + 1, std::nan(""));
+  CompressionCache cache;  // the levels share most blocks
   auto storage_at = [&](int ell) {
     BuildParams q = p;
     q.ell = ell;
     HostMatrix h;
-    build(points, n, dim, q, h);
+    build_impl(points, n, dim, q, h, &cache);
     return summarize(h).storage_amp;
   };
   const double ss = storage_at(L);

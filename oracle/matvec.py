@@ -6,11 +6,22 @@ matvec   : b <- 0; for every admissible block b_I += U_hat (V_hat^T x_J);
            back afterwards.  Several right-hand sides are columns of x.
 matvec_T : the transpose product x_bar_J += V_hat (U_hat^T y_bar_I) and
            x_bar_J += H_IJ^T y_bar_I (the backward of b = H_hat x).
+matvec_wp: Algorithm 4 with every arithmetic operation in a working
+           precision u (fp64, fp32 or fp16), the setting of the backward
+           error experiment of Section 5 (the paper varies u to show that it
+           must stay below about eps / N for Theorem 4.4 to hold): inputs
+           and stored factors are rounded to u, each product and each sum of
+           t_b = V^T x_J, of b_I += U t_b and of the dense blocks is rounded
+           to u (NumPy's fp16 arithmetic rounds each operation's fp32 result,
+           so a sum may be rounded twice), accumulated in the order of the
+           loops below.
 dense_hhat / dense_h : the explicit matrices in the user's point order.
 
 Parity: pinned by tests against the explicit dense H_hat (brute force), the
 adjoint identity <y, H x> = <H^T y, x>, and against the exact kernel matrix
-within the paper's bounds.
+within the paper's bounds; matvec_wp against matvec (u = fp64) and the
+standard componentwise bound gamma_c |U||V|^T|x| of a computation with
+paths of c operations in precision u (tests/test_oracle_working_precision.py).
 """
 from __future__ import annotations
 
@@ -55,6 +66,38 @@ def matvec_T(H: HMatrix, y: np.ndarray) -> np.ndarray:
     out = np.empty_like(xt)
     out[H.perm] = xt
     return out[:, 0] if vec else out
+
+
+WORKING_DTYPES = {0: np.float64, 1: np.float32, 2: np.float16}   # format codes FP64, FP32, FP16
+
+
+def matvec_wp(H: HMatrix, x: np.ndarray, wp: int) -> np.ndarray:
+    """b = H_hat x (one right-hand side) computed in working precision wp."""
+    dt = WORKING_DTYPES[wp]
+    xt = np.asarray(x, dtype=np.float64)[H.perm].astype(dt)
+    bt = np.zeros(H.n, dtype=dt)
+    for b in H.lowrank:
+        if b.k == 0:
+            continue
+        U, V = b.Ud().astype(dt), b.Vd().astype(dt)
+        xj = xt[b.col_off:b.col_off + b.n]
+        t = np.zeros(b.k, dtype=dt)
+        for r in range(b.n):                      # t = V^T x_J, one row at a time
+            t = t + V[r] * xj[r]
+        yi = bt[b.row_off:b.row_off + b.m]
+        for c in range(b.k):                      # b_I += U t, one column at a time
+            yi = yi + U[:, c] * t[c]
+        bt[b.row_off:b.row_off + b.m] = yi
+    for d in H.dense:
+        D = d.D.astype(dt)
+        xj = xt[d.col_off:d.col_off + d.n]
+        yi = bt[d.row_off:d.row_off + d.m]
+        for c in range(d.n):
+            yi = yi + D[:, c] * xj[c]
+        bt[d.row_off:d.row_off + d.m] = yi
+    out = np.empty(H.n)
+    out[H.perm] = bt.astype(np.float64)
+    return out
 
 
 def dense_hhat(H: HMatrix) -> np.ndarray:

@@ -200,10 +200,11 @@ def traffic_for(kernel: str, algorithmic_bytes: float):
         return None
 
 
-def oracle_sample(path: str, x: np.ndarray, budget_s: float, fraction: float | None = None):
+def oracle_sample(path: str, x: np.ndarray, budget_s: float, fraction: float | None = None, keep: bool = False):
     """Time the oracle's Algorithm 4 (float64 NumPy) on a bounded sample:
     whole products while they fit the budget, else a slice of the blocks;
-    returns (products per second, description, blocks, seconds)."""
+    returns (products per second, description, seconds), and with keep the
+    oracle's copy of the matrix as a fourth item."""
     from oracle import hhfile
     from oracle import matvec as M
     G = hhfile.read(path)
@@ -228,7 +229,41 @@ def oracle_sample(path: str, x: np.ndarray, budget_s: float, fraction: float | N
     rate = reps * frac_bytes / el
     desc = (f"oracle Algorithm 4 in float64 NumPy over {nb} of {len(blocks)} low-rank blocks "
             f"({100 * frac_bytes:.1f}% of the factor+dense words), {reps} passes, {el:.1f} s")
-    return rate, desc, el
+    return (rate, desc, el, G) if keep else (rate, desc, el)
+
+
+def oracle_rows_check(G, x: np.ndarray, y: np.ndarray, leaves: int = 8, seed: int = 7) -> dict:
+    """The product y (user order) against the oracle's Algorithm 4 in float64
+    over the same stored factors, on the rows of a few seeded leaf clusters:
+    every low-rank and dense block whose row cluster holds them."""
+    L = G.tree.L
+    nleaf = 1 << L
+    pick = sorted(int(v) for v in np.random.default_rng(seed).choice(nleaf, size=min(leaves, nleaf), replace=False))
+    sel = [(int(G.tree.off[nleaf - 1 + v]), int(G.tree.size[nleaf - 1 + v])) for v in pick]
+    sel = [(o, z) for o, z in sel if z > 0]
+    xt = np.asarray(x, dtype=np.float64)[G.perm]
+    yo = [np.zeros(z) for _, z in sel]
+
+    def hits(r0, m):
+        return [q for q, (o, z) in enumerate(sel) if r0 <= o and o + z <= r0 + m]
+    for b in G.lowrank:
+        h = hits(b.row_off, b.m)
+        if not h or not b.k:
+            continue
+        t = b.Vd().T @ xt[b.col_off:b.col_off + b.n]
+        U = b.Ud()
+        for q in h:
+            o, z = sel[q]
+            yo[q] += U[o - b.row_off:o - b.row_off + z] @ t
+    for d in G.dense:
+        for q in hits(d.row_off, d.m):
+            o, z = sel[q]
+            yo[q] += d.D[o - d.row_off:o - d.row_off + z] @ xt[d.col_off:d.col_off + d.n]
+    yu = np.asarray(y, dtype=np.float64)
+    num = sum(float(np.sum((yu[G.perm[o:o + z]] - yo[q]) ** 2)) for q, (o, z) in enumerate(sel))
+    den = sum(float(np.sum(v ** 2)) for v in yo)
+    return {"rel_err": float(np.sqrt(num / den)) if den > 0 else 0.0, "rows": sum(z for _, z in sel),
+            "leaf_clusters": len(sel)}
 
 
 def run_reference(args):
@@ -340,11 +375,21 @@ def run_ours(args):
            "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
 
     cpu = None
+    parity = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        y_amp = Ham.matvec(x).cpu().numpy()
         path = os.path.join(CACHE, "bench_adaptive.hhm")
         Ham.save(path)
-        rate, desc, _ = oracle_sample(path, xh0, args.cpu_seconds)
+        rate, desc, _, G = oracle_sample(path, xh0, args.cpu_seconds, keep=True)
         cpu = {"value": rate, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+        # the product's error against the oracle, beside the paper's bound
+        try:
+            parity = oracle_rows_check(G, xh0, y_amp)
+        except Exception as e:  # a failed check is reported, not fatal to the measurement
+            parity = {"error": f"{type(e).__name__}: {e}"}
+        parity.update({"tol": 1e-6, "bound_thm44": inf["bound_thm44"],
+                       "vs": "oracle Algorithm 4 (float64) over the same stored factors, sampled leaf-cluster rows"})
+        del G
 
     gbs = inf["bytes_per_matvec"] / (ms_amp * 1e-3) / 1e9
     gbs64 = inf64["bytes_per_matvec"] / (ms_64 * 1e-3) / 1e9
@@ -367,7 +412,7 @@ def run_ours(args):
         "blocks_per_fmt": inf["blocks_per_fmt"],
         "bound_thm44": inf["bound_thm44"],
         "build_seconds": build_s,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "parity": parity,
         "gpu_launches": 4 * args.steps, "clocks": clk, "autotune": tuned,
     }
     if rank == 0:

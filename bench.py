@@ -20,7 +20,10 @@ product Y = A_h X of all R columns; the metric is right-hand sides per second.
 
 Multi-GPU (torchrun): every rank runs an independent replica (weak scaling);
 the max time over ranks is reported.  --impl reference times the CPU oracle
-(oracle/, float64 NumPy) on a bounded sample of the same product.
+(oracle/, float64 NumPy) on a bounded sample of the same product.  In the
+single right-hand-side line the CPU-baseline leg also compares the product
+with the oracle's Algorithm 4 on the rows of eight seeded leaf clusters
+("parity": relative error, the 1e-6 tolerance and Theorem 4.4's bound).
 """
 from __future__ import annotations
 

@@ -189,3 +189,19 @@ def test_builder_blocks_meet_eq_2_1_at_high_rank(P, tmp_path):
         U, V = b.Ud(), b.Vd()
         assert np.linalg.norm(A - U @ V.T) <= 1.02 * tol * np.linalg.norm(A), (b.level, b.m, b.n, b.k)
         assert np.abs(U.T @ U - np.eye(b.k)).max() <= 1e-12
+
+
+def test_missing_library_fails_loudly():
+    """No fallback: without libhh.so the first call raises ImportError
+    instead of computing anything another way."""
+    import subprocess
+    import sys
+    code = ("import paper_2604_09147_gb300 as P\n"
+            "P.LIB_PATH = '/nonexistent/libhh.so'\n"
+            "P._LIB = None\n"
+            "try:\n"
+            "    P.HMatrix.build([[0.0, 0.0], [1.0, 1.0]], device=-1)\n"
+            "except ImportError as e:\n"
+            "    print('ImportError', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert "ImportError" in r.stdout and "missing" in r.stdout, r.stdout + r.stderr

@@ -91,3 +91,18 @@ def test_library_matches_oracle(case):
     scale = max(abs(v) for v in o_gains.values())
     for l, g in o_gains.items():
         assert abs(gains[l] - g) <= 0.02 * scale
+
+
+def test_library_search_equals_independent_builds():
+    """The library's search shares block compressions between the levels it
+    evaluates (a block's compression depends only on its clusters and tol):
+    each gain equals, exactly, S_s - S_h(ell) from separate builds."""
+    P = pytest.importorskip("paper_2604_09147_gb300")
+    pts = W.points(3000, 3, 17)
+    args = (W.EXP, 1.0, 32, 1.0)
+    ell, depth, gains = P.optimal_switch_level(pts, *args, 1e-5, ALL)
+    ss = P.HMatrix.build(pts, *args, depth, 1e-5, ALL, device=-1).info()["storage_amp"]
+    assert len(gains) >= 2
+    for l, g in gains.items():
+        sh = P.HMatrix.build(pts, *args, l, 1e-5, ALL, device=-1).info()["storage_amp"]
+        assert g == ss - sh

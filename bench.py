@@ -236,16 +236,17 @@ def oracle_sample(path: str, x: np.ndarray, budget_s: float, fraction: float | N
 
 
 def oracle_rows_check(G, x: np.ndarray, y: np.ndarray, leaves: int = 8, seed: int = 7) -> dict:
-    """The product y (user order) against the oracle's Algorithm 4 in float64
-    over the same stored factors, on the rows of a few seeded leaf clusters:
-    every low-rank and dense block whose row cluster holds them."""
+    """The product y (user order; one column or n x R) against the oracle's
+    Algorithm 4 in float64 over the same stored factors, on the rows of a few
+    seeded leaf clusters: every low-rank and dense block whose row cluster
+    holds them."""
     L = G.tree.L
     nleaf = 1 << L
     pick = sorted(int(v) for v in np.random.default_rng(seed).choice(nleaf, size=min(leaves, nleaf), replace=False))
     sel = [(int(G.tree.off[nleaf - 1 + v]), int(G.tree.size[nleaf - 1 + v])) for v in pick]
     sel = [(o, z) for o, z in sel if z > 0]
     xt = np.asarray(x, dtype=np.float64)[G.perm]
-    yo = [np.zeros(z) for _, z in sel]
+    yo = [np.zeros((z,) + xt.shape[1:]) for _, z in sel]
 
     def hits(r0, m):
         return [q for q, (o, z) in enumerate(sel) if r0 <= o and o + z <= r0 + m]
@@ -549,12 +550,23 @@ def run_many(args):
            "h2d_bytes_per_step": 8 * n * R, "d2h_bytes_per_step": 8 * n * R}
 
     cpu = None
+    parity = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        Y = H.matvec(x).cpu().numpy()
         path = os.path.join(CACHE, f"bench_{args.workload}.hhm")
         H.save(path)
-        rate, desc, _ = oracle_sample(path, X0, args.cpu_seconds)
+        rate, desc, _, G = oracle_sample(path, X0, args.cpu_seconds, keep=True)
         cpu = {"value": rate * R, "unit": "rhs/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": desc + f", {R} columns per pass"}
+        try:
+            parity = oracle_rows_check(G, X0, Y)
+        except Exception as e:  # a failed check is reported, not fatal to the measurement
+            parity = {"error": f"{type(e).__name__}: {e}"}
+        parity.update({"tol": "1e-6 ||Y|| + sum_b w_b |U_b| |V_b|^T |X| over the tensor-core blocks "
+                              "(w_b = 2^-20 fp32, 2^-12 16/8-bit)", "bound_thm44": inf["bound_thm44"],
+                       "vs": "oracle Algorithm 4 (float64) over the same stored factors, sampled leaf-cluster rows, "
+                             "all columns"})
+        del G
     launches = 2 + 6 + 1 + (3 * ((R + 3) // 4) if stages["fp64_streaming"] > 0.002 else 0)
     out = {
         "metric": "H_h matvec right-hand sides/s (adaptive precision, many right-hand sides)",
@@ -572,7 +584,7 @@ def run_many(args):
         "streaming_4col": {"ms_per_step": ms_stream, "speedup": ms_stream / ms},
         "blocks_per_fmt": inf["blocks_per_fmt"], "factor_bytes_per_fmt": inf["factor_bytes_per_fmt"],
         "tc_factor_bytes": inf["tc_factor_bytes"], "bound_thm44": inf["bound_thm44"], "build_seconds": build_s,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "parity": parity,
         "gpu_launches": launches * args.steps, "clocks": clk, "autotune": tuned,
     }
     if rank == 0:

@@ -27,3 +27,17 @@ def test_rows_check_against_full_product(tmp_path):
     yp = y.copy()
     yp[G.perm[int(G.tree.off[leaf]):int(G.tree.off[leaf] + G.tree.size[leaf])]] += 1.0
     assert bench.oracle_rows_check(G, x, yp, leaves=1 << G.tree.L)["rel_err"] > 1e-4
+
+
+def test_rows_check_many_columns(tmp_path):
+    O = OB.build(W.points(2000, 3, 7), W.GAUSS, 0.05, 64, 1.0, 2, 1e-6, W.F64 | W.F32 | W.BF16 | W.E4M3)
+    path = str(tmp_path / "m.hhm")
+    hhfile.write(O, path)
+    G = hhfile.read(path)
+    X = W.rhs(2000, 5, "normal", 8)
+    Y = M.matvec(G, X)
+    assert bench.oracle_rows_check(G, X, Y)["rel_err"] <= 1e-15
+    Yp = Y.copy()
+    Yp[:, 3] *= 1 + 1e-6
+    r = bench.oracle_rows_check(G, X, Yp, leaves=1 << G.tree.L)
+    assert r["rows"] == 2000 and 0 < r["rel_err"] < 1e-6

@@ -672,15 +672,25 @@ def run_batch(args):
     e2e = {"value": ws * e2e_steps * count / max_over_ranks(torch, e2e_s, ws), "unit": "matvec/s",
            "h2d_bytes_per_step": 8 * x.numel(), "d2h_bytes_per_step": 8 * x.numel()}
     cpu = None
+    parity = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         # the oracle on the largest matrix of the batch, scaled by bytes to the whole batch
         big = max(range(count), key=lambda i: infos[i]["bytes_per_matvec"])
+        ybig = y[batch.offsets[big]:batch.offsets[big + 1]].cpu().numpy()  # its part of the last batch product
         path = os.path.join(CACHE, "bench_batch_big.hhm")
         mats[big].save(path)
-        rate, desc, _ = oracle_sample(path, xs_h[big], args.cpu_seconds)
+        rate, desc, _, G = oracle_sample(path, xs_h[big], args.cpu_seconds, keep=True)
         scale = infos[big]["bytes_per_matvec"] / total_bytes
         cpu = {"value": rate * scale * count, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": desc + f"; matrix {big} (N={specs[big]['n']}), scaled by bytes to the batch"}
+        try:
+            parity = oracle_rows_check(G, xs_h[big], ybig)
+        except Exception as e:  # a failed check is reported, not fatal to the measurement
+            parity = {"error": f"{type(e).__name__}: {e}"}
+        parity.update({"tol": 1e-6, "bound_thm44": infos[big]["bound_thm44"], "matrix": big,
+                       "vs": "oracle Algorithm 4 (float64) over the same stored factors, sampled leaf-cluster rows "
+                             "of the largest matrix's part of the batch product"})
+        del G
     out = {
         "metric": "H_h matvecs/s over an uneven batch (one CUDA graph per batch product)",
         "value": value, "unit": "matvec/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -692,7 +702,7 @@ def run_batch(args):
                    "l2": "batch bytes %.2f GB per step" % (total_bytes / 1e9)},
         "one_sequence": {"ms_per_step": t_seq / args.steps},
         "per_matrix_launches": {"ms_per_step": t_each / args.steps, "speedup_graph": t_each / t_graph},
-        "build_seconds": build_s, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "build_seconds": build_s, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "parity": parity,
         "gpu_launches": 4 * args.steps, "clocks": clk,
     }
     if rank == 0:

@@ -23,6 +23,7 @@ import numpy as np
 
 EXP, INV_R, GAUSS, LOG, INV_R2 = 0, 1, 2, 3, 4
 F64, F32, F16, BF16, E4M3 = 1, 2, 4, 8, 16
+RULE_Q43 = 32  # fmt_mask option: the rule uses Table 1's u = 2.5e-1 for the 8-bit format
 
 # Workload presets.  Seeds: points 1234 + id, vectors 42 + id.
 CONFIGS = {

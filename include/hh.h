@@ -68,6 +68,11 @@ enum hh_fmt { HH_FMT_F64 = 0, HH_FMT_F32 = 1, HH_FMT_F16 = 2, HH_FMT_BF16 = 3, H
 #define HH_F16 4u
 #define HH_BF16 8u
 #define HH_E4M3 16u
+/* fmt_mask option: Algorithm 3's rule takes the 8-bit format's unit roundoff
+ * as printed in Table 1 (2.5e-1) instead of e4m3's 2^-4, so it picks the
+ * 8-bit format only where tau_b >= 1/4; storage, decoding and the error
+ * bounds keep 2^-4.  Not a format: combine with HH_E4M3. */
+#define HH_RULE_Q43 32u
 
 typedef struct hh_matrix* hh_handle;
 typedef struct hh_batch_s* hh_batch;
@@ -128,7 +133,8 @@ typedef struct {
  *                matrix, ell = 0 a HODLR matrix.  ell > L -> HH_ENOTSUP.
  *   tol          target accuracy eps of LRcompression (0 < tol < 1).
  *   fmt_mask     HH_F64|HH_F32|... the set U of Algorithm 3; HH_F64 alone
- *                gives uniform fp64 storage.
+ *                gives uniform fp64 storage; | HH_RULE_Q43 for the rule's
+ *                Table 1 reading of the 8-bit format.  Other bits: HH_EINVAL.
  *   seed         recorded in saved files; the build itself is deterministic.
  *   device       CUDA device to upload to, or -1 for a host-only handle
  *                (hh_save / hh_info work; matrix-vector calls return

@@ -127,6 +127,11 @@ class HMatrix:
         return out
 
 
+# fmt_mask bit 5: the rule takes Table 1's printed u = 2.5e-1 for the 8-bit
+# format (formats.choose_format's q43_rule); bits 0-4 select the formats
+RULE_Q43 = 1 << 5
+
+
 def allowed_formats(fmt_mask: int) -> list[int]:
     return [f for f in (F.FP32, F.FP16, F.BF16, F.E4M3) if fmt_mask & (1 << f)]
 
@@ -194,8 +199,9 @@ def build(points: np.ndarray, kernel: int, kernel_param: float, leaf_size: int,
 
     # Algorithm 3: precision of every admissible block
     allowed = allowed_formats(fmt_mask)
+    q43 = bool(fmt_mask & RULE_Q43)
     for b in H.lowrank:
-        b.fmt = F.choose_format(block_tau(tol, b.level, b.norm, H.norm_Ht), allowed)
+        b.fmt = F.choose_format(block_tau(tol, b.level, b.norm, H.norm_Ht), allowed, q43)
 
     # Section 4.3 special case (ell == L): compress a leaf neighbour when it pays off
     if ell == L and nbr_candidates:
@@ -208,7 +214,7 @@ def build(points: np.ndarray, kernel: int, kernel_param: float, leaf_size: int,
             U, V, s = lr_compress(kernel, kernel_param, tp[d.row_off:d.row_off + d.m],
                                   tp[d.col_off:d.col_off + d.n], tol)
             nb = float(np.sqrt(np.sum(s * s)))
-            f = F.choose_format(block_tau(tol, d.level, nb, H.norm_Ht), allowed)
+            f = F.choose_format(block_tau(tol, d.level, nb, H.norm_Ht), allowed, q43)
             if lowrank_pays_off(U.shape[1], d.m, d.n, F.BITS[f]):
                 H.lowrank.append(LRBlock(d.level, KIND_NBR, d.i, d.j, d.row_off, d.m,
                                          d.col_off, d.n, U, V, s, nb, fmt=f))

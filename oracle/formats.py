@@ -4,7 +4,8 @@ Table 1 (Section 1) lists fp64, fp32, fp16, bf16 and an 8-bit "q43" format
 (1 sign, 4 exponent, 3 mantissa bits).  The GPU has fp8 e4m3fn (OCP) instead:
 the same 1-4-3 split and bias 7, no infinities, largest finite 448.  Its unit
 roundoff under round-to-nearest is 2^-4; Table 1 prints 2.5e-1 for q43 (the
-spacing 2^-3 times 2), which is kept here as PAPER_Q43_U for reference only.
+spacing 2^-3 times 2), kept here as PAPER_Q43_U; the rule can be asked to use
+it for the 8-bit format (choose_format's q43_rule, fmt_mask bit RULE_Q43).
 
 Rounding is done in float64 arithmetic on exactly representable quantities:
 with v = f * 2^E (frexp), the quantum at v's binade is 2^(max(E-1, emin) - m)
@@ -151,13 +152,15 @@ def decode_bits(b: np.ndarray, fmt: int) -> np.ndarray:
     raise ValueError(fmt)
 
 
-def choose_format(tau: float, allowed: list[int]) -> int:
+def choose_format(tau: float, allowed: list[int], q43_rule: bool = False) -> int:
     """Algorithm 3's rule: the largest unit roundoff u_bar in {u} U allowed
     with u_bar <= tau (inclusive); fp64 (the working precision) if none fits.
-    Among formats of equal u the first in `allowed` order wins."""
+    Among formats of equal u the first in `allowed` order wins.  With
+    q43_rule the 8-bit format enters the rule with Table 1's printed
+    u = 2.5e-1 instead of its unit roundoff 2^-4 (its storage is unchanged)."""
     best, best_u = FP64, UNIT_ROUNDOFF[FP64]
     for f in allowed:
-        u = UNIT_ROUNDOFF[f]
+        u = PAPER_Q43_U if (q43_rule and f == E4M3) else UNIT_ROUNDOFF[f]
         if u <= tau and u > best_u:
             best, best_u = f, u
     return best

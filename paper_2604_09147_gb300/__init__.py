@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libhh.so")
 
 EXP, INV_R, GAUSS, LOG, INV_R2 = 0, 1, 2, 3, 4
 F64, F32, F16, BF16, E4M3 = 1, 2, 4, 8, 16
+RULE_Q43 = 32  # fmt_mask option: the rule uses Table 1's u = 2.5e-1 for the 8-bit format
 FMT_NAMES = ("fp64", "fp32", "fp16", "bf16", "e4m3")
 HH_OK, HH_EINVAL, HH_ENOMEM, HH_ECUDA, HH_ETIMEOUT, HH_ENOTSUP, HH_EIO, HH_EDEVICE = 0, -1, -2, -3, -4, -5, -6, -7
 MAX_LEVELS = 48

@@ -449,12 +449,16 @@ void store_value(uint8_t* dst, double r, int fmt) {
   }
 }
 
+// fmt_mask bit 5: the rule takes Table 1's printed unit roundoff of the
+// 8-bit format (2.5e-1) instead of e4m3's 2^-4; storage and bounds keep 2^-4
+constexpr uint32_t kRuleQ43 = 1u << 5;
+
 int choose_format(double tau, uint32_t mask) {
   int best = F64;
   double bu = unit_roundoff(F64);
   for (int f = F32; f <= E4M3; ++f) {
     if (!(mask & (1u << f))) continue;
-    double u = unit_roundoff(f);
+    double u = (f == E4M3 && (mask & kRuleQ43)) ? 0.25 : unit_roundoff(f);
     if (u <= tau && u > bu) {
       best = f;
       bu = u;
@@ -560,7 +564,7 @@ static void build_impl(const double* points, int64_t n, int dim, const BuildPara
   if (!(p.tol > 0 && p.tol < 1)) throw std::invalid_argument("tol must be in (0, 1)");
   if (p.kernel < 0 || p.kernel > 4) throw std::invalid_argument("unknown kernel");
   if (!(p.kparam > 0)) throw std::invalid_argument("kernel_param must be > 0");
-  if (p.fmt_mask & ~31u) throw std::invalid_argument("unknown format bits in fmt_mask");
+  if (p.fmt_mask & ~63u) throw std::invalid_argument("unknown bits in fmt_mask");
   for (int64_t i = 0; i < n * dim; ++i)
     if (!std::isfinite(points[i])) throw std::invalid_argument("points must be finite");
   h = HostMatrix();
@@ -738,7 +742,7 @@ void build(const double* points, int64_t n, int dim, const BuildParams& p, HostM
 }
 
 void reencode(const HostMatrix& src, uint32_t fmt_mask, int threads, HostMatrix& h) {
-  if (fmt_mask & ~31u) throw std::invalid_argument("unknown format bits in fmt_mask");
+  if (fmt_mask & ~63u) throw std::invalid_argument("unknown bits in fmt_mask");
   if (src.ell == src.L && src.L > 0)
     throw std::domain_error("re-encoding needs ell < L (with ell == L the dense/low-rank choice depends on the format)");
   for (const LRBlock& b : src.lr)

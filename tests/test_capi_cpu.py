@@ -54,6 +54,9 @@ def test_argument_errors(P):
     with pytest.raises(P.HHError) as e:
         P.HMatrix.build(pts, kernel=7, device=-1)
     assert e.value.code == P.HH_EINVAL
+    with pytest.raises(P.HHError) as e:
+        P.HMatrix.build(pts, fmt_mask=ALL | 64, device=-1)                   # not a format or option bit
+    assert e.value.code == P.HH_EINVAL
     H = P.HMatrix.build(pts, leaf_size=32, device=-1)
     with pytest.raises(P.HHError) as e:
         H.matvec_host(np.zeros(300))
@@ -93,6 +96,23 @@ def test_corrupt_file_is_rejected(P, tmp_path):
 ])
 def test_host_builder_matches_oracle(P, tmp_path, n, dim, kernel, param, leaf, ell, tol, mask):
     _builder_vs_oracle(P, tmp_path, W.points(n, dim, 77), kernel, param, leaf, ell, tol, mask)
+
+
+def test_host_builder_matches_oracle_with_table1_q43_rule(P, tmp_path):
+    """fmt_mask | RULE_Q43: both builders apply the rule with Table 1's u for
+    the 8-bit format, so at eps = 1e-2 no block with tau_b < 1/4 is 8-bit;
+    the option travels in the file's fmt_mask."""
+    pts = W.points(3000, 3, 79)
+    _builder_vs_oracle(P, tmp_path, pts, W.EXP, 1.0, 64, 2, 1e-2, ALL | W.RULE_Q43)
+    H = P.HMatrix.build(pts, W.EXP, 1.0, 64, 1.0, 2, 1e-2, ALL | W.RULE_Q43, device=-1)
+    path = str(tmp_path / "q.hhm")
+    H.save(path)
+    G = hhfile.read(path)
+    assert G.fmt_mask & W.RULE_Q43
+    lvl = lambda l: 2.0 ** (l / 2)  # noqa: E731
+    for b in G.lowrank:
+        if b.fmt == 4:
+            assert 1e-2 / (lvl(b.level) * b.norm / G.norm_Ht) >= 0.25
 
 
 @pytest.mark.parametrize("n,dim,kernel,param,leaf,ell,tol,mask", [

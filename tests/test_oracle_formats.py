@@ -125,3 +125,14 @@ def test_choose_format_rule():
     us = [U[F.choose_format(t, allowed)] for t in taus]
     assert all(a <= b for a, b in zip(us, us[1:]))
     assert all(u <= t for u, t in zip(us, taus) if u != U[F.FP64])
+
+
+def test_rule_with_table1_q43_unit_roundoff():
+    """With the Table 1 reading (fmt_mask bit RULE_Q43) the 8-bit format enters
+    the rule with u = 2.5e-1: tau in [2^-4, 1/4) now picks bf16, tau >= 1/4
+    still the 8-bit format; the other formats are unaffected."""
+    allowed = [F.FP32, F.FP16, F.BF16, F.E4M3]
+    assert F.choose_format(0.2, allowed) == F.E4M3
+    assert F.choose_format(0.2, allowed, q43_rule=True) == F.BF16
+    assert F.choose_format(0.25, allowed, q43_rule=True) == F.E4M3
+    assert F.choose_format(1e-3, allowed, q43_rule=True) == F.choose_format(1e-3, allowed)

@@ -187,3 +187,19 @@ def test_degenerate_point_sets(tmp_path, name):
     for d in G.dense:
         cover[d.row_off:d.row_off + d.m, d.col_off:d.col_off + d.n] += 1
     assert np.all(cover == 1)
+
+
+@pytest.mark.parametrize("kernel,param", [(W.INV_R, 1.0), (W.GAUSS, 2.0)])
+def test_library_global_error_follows_eps(tmp_path, kernel, param):
+    """Section 5.1's experiment on the library's builder (2^d-tree, eta = sqrt(3),
+    ell = L - 1, all five formats): ||H - H_hat||_F / ||H||_F stays within
+    Theorem 4.2's bound and follows eps (not far below it either)."""
+    P = pytest.importorskip("paper_2604_09147_gb300")
+    pts = W.points(2500, 3, 9) * 2 - 1
+    Hd = M.dense_h(pts, kernel, param)
+    for eps in (1e-2, 1e-6):
+        H = P.HMatrix.build(pts, kernel, param, 64, math.sqrt(3), 1, eps, ALL, device=-1, tree="2d")
+        path = str(tmp_path / "g.hhm")
+        H.save(path)
+        err = np.linalg.norm(Hd - M.dense_hhat(hhfile.read(path))) / np.linalg.norm(Hd)
+        assert 0.1 * eps <= err <= H.info()["bound_thm42"]

@@ -27,9 +27,10 @@ def P():
 @pytest.mark.parametrize("mask,res_tol", [(W.F64, 1e-9), (ALL, 1e-5)])
 def test_cg_matches_oracle(P, tmp_path, mask, res_tol):
     """(H_hat + I) x = b, Gaussian kernel: the GPU solver stops at the
-    requested recursive residual within a couple of iterations of the
-    oracle, and its solution satisfies the oracle's operator up to the
-    product's own accuracy (1e-12 fp64 path, 1e-6 adaptive path)."""
+    requested recursive residual within two iterations of the oracle (fp64
+    path) or 15% of its iterations (adaptive path), and its solution
+    satisfies the oracle's operator up to the product's own accuracy (1e-12
+    fp64 path, 1e-6 adaptive path)."""
     n = 6000
     O = OB.build(W.points(n, 3, 53), W.GAUSS, 0.05, 64, 1.0, 2, 1e-8, mask)
     path = str(tmp_path / "s.hhm")

@@ -234,6 +234,29 @@ def test_autograd_backward_is_transpose(P, tmp_path):
         assert abs(lhs - rhs) <= 1e-6 * abs(lhs) + 1e-12
 
 
+def test_autograd_matches_central_differences(P, tmp_path):
+    """The product is linear, so a central difference of L(x) = <ybar, A_h x>
+    with any step is <ybar, A_h d> up to rounding.  On a uniform-fp64 matrix
+    (fp64-class arithmetic, within 1e-12 of the oracle) with h = 1e-3 the
+    rounding is about 1e-12 ||ybar|| ||y|| / h; the hand-written backward
+    <A_h^T ybar, d> must agree to 1e-7 ||ybar|| ||y|| on 8 directions (about
+    6e-6 of the derivative itself for these random vectors)."""
+    pts = W.points(4000, 3, 13)
+    _, H = oracle_pair(P, tmp_path, pts, W.EXP, 1.0, 64, 3, 1e-8, W.F64)
+    x = gpu(W.rhs(4000, 1, "uniform", 3)[:, 0]).requires_grad_(True)
+    ybar = gpu(W.rhs(4000, 1, "normal", 4)[:, 0])
+    torch.dot(ybar, P.hh_apply(H, x)).backward()
+    g = x.grad.detach()
+    x0 = x.detach()
+    scale = float(ybar.norm()) * float(H.matvec(x0).norm())
+    h = 1e-3
+    for k in range(8):
+        d = gpu(W.rhs(4000, 1, "uniform", 60 + k)[:, 0])
+        lp = float(torch.dot(ybar, H.matvec(x0 + h * d)))
+        lm = float(torch.dot(ybar, H.matvec(x0 - h * d)))
+        assert abs((lp - lm) / (2 * h) - float(torch.dot(g, d))) <= 1e-7 * scale
+
+
 def test_host_api_and_batched(P, tmp_path):
     mats, xs, oracles = [], [], []
     for i, n in enumerate((2100, 3333, 1500)):

@@ -203,3 +203,28 @@ def test_library_global_error_follows_eps(tmp_path, kernel, param):
         H.save(path)
         err = np.linalg.norm(Hd - M.dense_hhat(hhfile.read(path))) / np.linalg.norm(Hd)
         assert 0.1 * eps <= err <= H.info()["bound_thm42"]
+
+
+def test_hodlr_h_s_and_h_h_storage(tmp_path):
+    """Section 3's comparison (1/r in 2-D, uniform fp64, library builder):
+    weak admissibility admits near-field blocks whose ranks grow with the
+    cluster size, so HODLR's low-rank storage exceeds H_s's (far field only)
+    at both tolerances, and H_h stores less than H_s with its leaf neighbours
+    dense (standard admissibility alone)."""
+    P = pytest.importorskip("paper_2604_09147_gb300")
+    pts = W.points(16384, 2, 21) * 2 - 1
+    store = {}
+    for eps in (1e-2, 1e-8):
+        for name, ell in (("s", 4), ("h", 3), ("hodlr", 0)):
+            H = P.HMatrix.build(pts, W.INV_R, 1.0, 64, math.sqrt(2), ell, eps, W.F64, device=-1, tree="2d")
+            assert H.info()["L"] == 2 * 4
+            path = str(tmp_path / "s.hhm")
+            H.save(path)
+            G = hhfile.read(path)
+            nbr = name == "s"
+            lr = sum(b.k * (b.m + b.n) for b in G.lowrank if not (nbr and b.kind == PT.KIND_NBR))
+            dn = sum(d.m * d.n for d in G.dense) + sum(b.m * b.n for b in G.lowrank if nbr and b.kind == PT.KIND_NBR)
+            store[name, eps] = (lr, dn)
+    for eps in (1e-2, 1e-8):
+        assert store["hodlr", eps][0] > store["s", eps][0]
+        assert sum(store["h", eps]) < sum(store["s", eps])

@@ -37,3 +37,11 @@ def test_cg_on_hh_matches_direct_solve(mask):
     xd = np.linalg.solve(A, b)
     assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
     assert np.linalg.norm(A @ x - b) <= 1e-8 * np.linalg.norm(b)
+
+
+def test_cg_reports_breakdown_on_indefinite_operator():
+    """p^T A p <= 0 (an indefinite operator) stops the iteration with an error
+    instead of returning a meaningless iterate, as the library's solver does."""
+    A = np.diag([1.0, -1.0])
+    with pytest.raises(ValueError):
+        S.cg(None, np.array([1.0, 1.0]), rtol=1e-12, max_iter=10, apply=lambda v: A @ v)

@@ -355,12 +355,13 @@ void hh_batch_free(hh_batch b);
  * owns all device memory, or a loop that must not pay cudaMalloc's implicit
  * synchronisation).  The paper has no counterpart: this is a deployment
  * variant of hh_matvec.
- *   Scratch: a fixed 32 MiB file-scope device array inside the library,
- *   which every GPU that loads the library holds until the process exits;
- *   matrices whose scratch (about 40 bytes per point plus 16 to 32 bytes per
+ *   Scratch: a fixed 32 MiB file-scope device array inside the library.
+ *   A GPU holds it from the first matrix built or loaded on it (hh_build,
+ *   hh_build_ex, hh_load or hh_reencode with that device), where its device
+ *   address is looked up once (cudaGetSymbolAddress), until the process
+ *   exits; so this call itself neither allocates nor loads anything.
+ *   Matrices whose scratch (about 40 bytes per point plus 16 to 32 bytes per
  *   unit of rank) exceeds it are rejected with HH_EINVAL and a message.
- *   The first call on a device looks up the array's device address (one
- *   cudaGetSymbolAddress); make that first call before any stream capture.
  *   All calls share the one array: calls that overlap on the GPU (other
  *   streams, other handles) race and give wrong results; order them on one
  *   stream.  Everything the product needs zeroed is cleared by each call.

@@ -173,7 +173,7 @@ T* upload(const std::vector<T>& v) {
 
 // Dense blocks with an even leading dimension (16-byte aligned columns), each
 // scaled by a power of two so that its largest magnitude lies in (1/2, 1]
-// (exact; the kernels split fp64 values into fp32 halves).
+// (exact; upload_matrix then turns every value into a pair of fp32 halves).
 void upload_dense(hh_matrix* h, std::vector<int64_t>& doff, std::vector<int32_t>& dexp) {
   const hh::HostMatrix& H = h->H;
   doff.assign(H.dense.size(), 0);
@@ -632,11 +632,54 @@ void build_mr_set(hh_matrix* h, int dir, const std::vector<int64_t>& doff, const
   out.n_dtiles = (int)dt.size();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free product (hh_matvec_noalloc, see include/hh.h).
+//
+// Some callers cannot allocate device memory at call time: a host framework
+// that owns every device allocation (a serving runtime with a fixed memory
+// budget, a plugin host), or a latency-critical loop in which cudaMalloc's
+// implicit device synchronisation is not acceptable.  For them the product's
+// scratch (shifted input copies, output accumulator, t arenas for one
+// right-hand side) lives in one fixed file-scope device array.  A GPU holds
+// it from the first matrix built or loaded on it (upload_matrix resolves its
+// address, which loads this file's device module) until the process exits,
+// so that no hh_matvec_noalloc call loads a module or reserves memory.
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB per device
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};  // device address of g_noalloc_scratch per device
+
+// Device address of the scratch array on the current device (looked up once
+// per device; host code must not use the symbol itself as an address).
+int noalloc_scratch(int device, void** ptr) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return fail(HH_ENOTSUP, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(HH_ECUDA, std::string("cudaGetSymbolAddress(scratch) failed: ") + cudaGetErrorString(e));
+    g_noalloc_addr[device] = p;
+  }
+  *ptr = g_noalloc_addr[device];
+  return HH_OK;
+}
+
 void upload_matrix(hh_matrix* h, int device) {
   const hh::HostMatrix& H = h->H;
   ck(cudaSetDevice(device), "cudaSetDevice");
   h->device = device;
   ck(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device), "device attribute");
+  {
+    // the allocation-free product's scratch array: resolved here, once per
+    // device, so that hh_matvec_noalloc never loads a module (a failure is
+    // reported by that call instead)
+    void* scratch = nullptr;
+    if (noalloc_scratch(device, &scratch) != HH_OK) g_last_error.clear();
+  }
   h->d_arena = upload(H.arena);
   h->d_perm = upload(H.perm);
   {
@@ -656,6 +699,27 @@ void upload_matrix(hh_matrix* h, int device) {
   std::vector<int64_t>& doff = h->doff;
   std::vector<int32_t>& dexp = h->dexp;
   upload_dense(h, doff, dexp);
+  // the device form of fp64 data: every fp64 factor and dense block becomes
+  // float2 pairs (hi, lo) in place, once (the host arena keeps fp64)
+  {
+    std::vector<int64_t> spans;
+    for (const hh::LRBlock& B : H.lr)
+      if (B.fmt == hh::F64 && B.k > 0) {
+        spans.insert(spans.end(), {B.u_off, B.ldu * B.k});
+        spans.insert(spans.end(), {B.v_off, B.ldv * B.k});
+      }
+    int64_t* d_spans = upload(spans);
+    cudaError_t e = hh::dev::launch_presplit_f64(h->d_arena, d_spans, (int)(spans.size() / 2), 0);
+    const int64_t dtot = H.dense.empty() ? 0 : doff.back() + (H.dense.back().m + 1) / 2 * 2 * H.dense.back().n;
+    std::vector<int64_t> dspan = {0, dtot};
+    int64_t* d_dspan = upload(dspan);
+    if (e == cudaSuccess)
+      e = hh::dev::launch_presplit_f64(reinterpret_cast<uint8_t*>(h->d_dense_pad), d_dspan, dtot > 0 ? 1 : 0, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_spans);
+    cudaFree(d_dspan);
+    ck(e, "fp64 device form");
+  }
   // with many right-hand sides the streaming passes keep only the fp64
   // low-rank blocks; the tensor cores and mr.cu take the rest
   // positions of one many-column phase-1 item (HH_TC_SPLIT_POSITIONS, a
@@ -690,8 +754,10 @@ struct WsView {
   int* counters;
 };
 
-size_t ws_layout(const hh_matrix* h, WsView* v, char* base) {
-  const int R = hh::dev::kMaxNR;
+// Workspace of the streaming passes for up to R right-hand sides per launch
+// sequence: shifted input copies and output accumulator for R columns; the t
+// arenas always for kMaxNR (the descriptors' t offsets are laid out for it).
+size_t ws_layout(const hh_matrix* h, WsView* v, char* base, int R = hh::dev::kMaxNR) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -701,8 +767,8 @@ size_t ws_layout(const hh_matrix* h, WsView* v, char* base) {
   float* xs = (float*)take(sizeof(float) * 4 * R * h->npad);
   float* xs_lo = (float*)take(sizeof(float) * 4 * R * h->npad);
   double* acc = (double*)take(sizeof(double) * R * h->npad);
-  float* t32 = (float*)take(sizeof(float) * std::max<int64_t>(1, h->t32_elems * R));
-  float2* t64 = (float2*)take(sizeof(float2) * std::max<int64_t>(1, h->t64_elems * R));
+  float* t32 = (float*)take(sizeof(float) * std::max<int64_t>(1, h->t32_elems * hh::dev::kMaxNR));
+  float2* t64 = (float2*)take(sizeof(float2) * std::max<int64_t>(1, h->t64_elems * hh::dev::kMaxNR));
   int* counters = (int*)take(256);
   if (v) *v = {xs, xs_lo, acc, t32, t64, counters};
   return off;
@@ -1738,58 +1804,15 @@ void hh_batch_free(hh_batch b) {
 
 }  // extern "C"
 
-// ---------------------------------------------------------------------------
-// Allocation-free product (hh_matvec_noalloc, see include/hh.h).
-//
-// Some callers cannot allocate device memory at call time: a host framework
-// that owns every device allocation (a serving runtime with a fixed memory
-// budget, a plugin host), or a latency-critical loop in which cudaMalloc's
-// implicit device synchronisation is not acceptable.  For them the product's
-// scratch (shifted input copies, output accumulator, t arenas for one
-// right-hand side) lives in one fixed file-scope device array that every GPU
-// holds from the moment it loads this library until the process exits.
-namespace {
-
-constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB per device
-__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kNoAllocMaxDevices] = {};  // device address of g_noalloc_scratch per device
-
-// Device address of the scratch array on the current device (looked up once
-// per device; host code must not use the symbol itself as an address).
-int noalloc_scratch(int device, void** ptr) {
-  if (device < 0 || device >= kNoAllocMaxDevices) return fail(HH_ENOTSUP, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(HH_ECUDA, std::string("cudaGetSymbolAddress(scratch) failed: ") + cudaGetErrorString(e));
-    g_noalloc_addr[device] = p;
-  }
-  *ptr = g_noalloc_addr[device];
-  return HH_OK;
-}
-
-}  // namespace
-
 extern "C" int hh_matvec_noalloc(hh_handle h, int transpose, const double* in, double* out, void* stream) {
   if (!h || !in || !out) return fail(HH_EINVAL, "null argument");
+  if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data (built with device = -1)");
   // scratch for one right-hand side, in the layout of the handle workspace
-  const int64_t npad = (h->H.n + 32 + 3) / 4 * 4;
-  int64_t t32 = 0, t64 = 0;
-  for (const hh::LRBlock& b : h->H.lr) (b.fmt == hh::F64 ? t64 : t32) += b.k;
-  const size_t need = align256(sizeof(float) * 4 * npad) + align256(sizeof(float) * 4 * npad) +
-                      align256(sizeof(double) * npad) +
-                      align256(sizeof(float) * std::max<int64_t>(1, t32 * hh::dev::kMaxNR)) +
-                      align256(sizeof(float2) * std::max<int64_t>(1, t64 * hh::dev::kMaxNR)) + 256;
+  const size_t need = ws_layout(h, nullptr, nullptr, 1);
   if (need > kNoAllocScratchBytes)
     return fail(HH_EINVAL, "hh_matvec_noalloc: this matrix needs " + std::to_string(need) +
                                " bytes of scratch, more than the fixed " +
                                std::to_string(kNoAllocScratchBytes) + " bytes; use hh_matvec or hh_matvec_ws");
-  if (h->device < 0) return fail(HH_ENOTSUP, "handle has no device data (built with device = -1)");
   const char* a0 = (const char*)in;
   const char* b0 = (const char*)out;
   const size_t span = (size_t)h->H.n * sizeof(double);
@@ -1800,41 +1823,13 @@ extern "C" int hh_matvec_noalloc(hh_handle h, int transpose, const double* in, d
   void* base = nullptr;
   int rc = noalloc_scratch(h->device, &base);
   if (rc == HH_OK) {
-    char* p = (char*)base;
-    float* xs = (float*)p;
-    p += align256(sizeof(float) * 4 * npad);
-    float* xs_lo = (float*)p;
-    p += align256(sizeof(float) * 4 * npad);
-    double* acc = (double*)p;
-    p += align256(sizeof(double) * npad);
-    float* tt32 = (float*)p;
-    p += align256(sizeof(float) * std::max<int64_t>(1, t32 * hh::dev::kMaxNR));
-    float2* tt64 = (float2*)p;
+    WsView w;
+    ws_layout(h, &w, (char*)base, 1);
     const int dir = transpose ? 1 : 0;
     cudaStream_t st = (cudaStream_t)stream;
-    int* counters = (int*)(p + align256(sizeof(float2) * std::max<int64_t>(1, t64 * hh::dev::kMaxNR)));
-    cudaError_t e = hh::dev::launch_prep(in, h->H.n, 1, h->d_perm, h->H.n, npad, xs, xs_lo, acc, st, counters);
-    bool p1 = false;
-    for (int phase = 1; phase <= 2 && e == cudaSuccess; ++phase) {
-      hh::dev::StreamArgs s;
-      std::memset(&s, 0, sizeof(s));
-      s.desc = h->ss[dir].d_desc[phase - 1];
-      s.items = h->ss[dir].d_items[phase - 1];
-      s.n_items = h->ss[dir].n_items[phase - 1];
-      s.nr = 1;
-      s.npad = npad;
-      s.xs = xs;
-      s.xs_lo = xs_lo;
-      s.t32 = tt32;
-      s.t64 = tt64;
-      s.acc = acc;  // cleared by the prep launch on every call
-      s.status = h->d_status;
-      s.counter = counters + (phase - 1);
-      int grid = std::max(1, std::min(h->ss[dir].grid[phase][1], s.n_items));
-      e = hh::dev::launch_stream(phase, h->ss[dir].fset, s, grid, st, p1);
-      p1 = phase == 1 && s.n_items > 0;
-    }
-    if (e == cudaSuccess) e = hh::dev::launch_finish(acc, 1, h->d_iperm, h->H.n, npad, out, h->H.n, st);
+    // prep clears the accumulator and the work counters on every call
+    cudaError_t e = run_stream(h, h->ss[dir], in, h->H.n, 1, w.acc, w, st, nullptr);
+    if (e == cudaSuccess) e = hh::dev::launch_finish(w.acc, 1, h->d_iperm, h->H.n, h->npad, out, h->H.n, st);
     if (e != cudaSuccess) rc = fail(HH_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
   }
   if (cur >= 0 && cur != h->device) cudaSetDevice(cur);

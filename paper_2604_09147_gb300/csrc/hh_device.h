@@ -14,7 +14,8 @@ struct Item {
   int32_t kind, idx, lo, hi;
 };
 
-// One factor (or dense block) as seen by a streaming pass.
+// One factor (or dense block) as seen by a streaming pass.  fp64 data is
+// held as float2 pairs (hi, lo) in the same 8 bytes (launch_presplit_f64).
 //   phase 1: columns j of f (rows x cols, column-major, ld elements) dotted
 //            with in[in_off + i]; mode 0: t[toff + j*nr + r] = sum (scaled
 //            units), mode 1: acc[out_off + j] += sum (dense block, A^T).
@@ -63,6 +64,10 @@ constexpr unsigned kSetF32 = 1u | 2u;    // fp64 + fp32
 constexpr unsigned kSetAll = 31u;        // every format
 unsigned pass_set_for(unsigned fmts_present);
 
+// fp64 values at the spans {byte offset, count} (device array of 2 nspans
+// int64) of base rewritten in place as float2 (fl32(v), fl32(v - fl32(v))):
+// the form in which every kernel reads fp64 factors and dense blocks
+cudaError_t launch_presplit_f64(uint8_t* base, const int64_t* spans, int nspans, cudaStream_t st);
 // out[u + r ld] = acc[r npad + iperm[u]] (iperm: caller position -> tree position)
 cudaError_t launch_finish(const double* acc, int nr, const int32_t* iperm, int64_t n, int64_t npad,
                           double* out, int64_t ld, cudaStream_t st);

@@ -8,6 +8,8 @@
 //            work counters of the two passes.
 //   finish : output accumulator (tree order) -> the caller's order, through
 //            the inverse permutation (caller position -> tree position).
+//   presplit: fp64 factors and dense blocks -> pairs of fp32 values, once
+//            when a matrix is uploaded.
 // The two streaming passes between them live in stream.cu.
 #include "hh_device.h"
 
@@ -42,6 +44,22 @@ __global__ void prep_kernel(const double* __restrict__ in, int64_t ld, int nr,
   }
 }
 
+// fp64 values -> (hi, lo) = (fl32(v), fl32(v - hi)) in place, over spans
+// {byte offset, count} of base: the device form of fp64 factors and dense
+// blocks that the streaming and dense kernels read (run once per upload)
+__global__ void presplit_kernel(uint8_t* __restrict__ base, const int64_t* __restrict__ spans, int nspans) {
+  for (int s = blockIdx.x; s < nspans; s += gridDim.x) {
+    double* p = reinterpret_cast<double*>(base + spans[2 * s]);
+    float2* q = reinterpret_cast<float2*>(p);
+    const int64_t n = spans[2 * s + 1];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const double v = p[i];
+      const float hi = __double2float_rn(v);
+      q[i] = make_float2(hi, __double2float_rn(v - static_cast<double>(hi)));
+    }
+  }
+}
+
 // out[u + r ld] = acc[r npad + iperm[u]]: a thread owns caller position u
 // and walks the columns, so the writes of a warp are coalesced and the
 // gathered reads of the threads in flight stay in a few accumulator columns
@@ -63,6 +81,12 @@ cudaError_t launch_prep(const double* in, int64_t ld, int nr, const int32_t* per
   int64_t blocks = (npad + 3 + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   prep_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(in, ld, nr, perm, n, npad, xs, xs_lo, acc, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_presplit_f64(uint8_t* base, const int64_t* spans, int nspans, cudaStream_t st) {
+  if (nspans <= 0) return cudaSuccess;
+  presplit_kernel<<<nspans < 4096 ? nspans : 4096, 256, 0, st>>>(base, spans, nspans);
   return cudaGetLastError();
 }
 

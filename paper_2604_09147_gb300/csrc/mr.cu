@@ -322,9 +322,19 @@ __global__ void __launch_bounds__(kThreads, 2) mr_phase2(MrArgs a) {
 }
 
 // ------------------------------------------------------------------ dense blocks
-__device__ __forceinline__ void split_d(double d, float& hi, float& lo) {
-  hi = __double2float_rn(d);
-  lo = __double2float_rn(d - static_cast<double>(hi));
+// a dense entry held as an fp32 pair (hi, lo) of its value times 2^-e, times
+// 2^e: exact scaling in fp32 when 2^e is a normal fp32 number (the builder's
+// scales are), else through fp64
+__device__ __forceinline__ void pair_scaled(float2 v, int e, float& hi, float& lo) {
+  if (e >= -126 && e <= 127) {
+    const float sc = __int_as_float((127 + e) << 23);
+    hi = v.x * sc;
+    lo = v.y * sc;
+  } else {
+    const double d = ldexp(static_cast<double>(v.x) + static_cast<double>(v.y), e);
+    hi = __double2float_rn(d);
+    lo = __double2float_rn(d - static_cast<double>(hi));
+  }
 }
 
 // S + C += (ah + al)(bh + bl): the leading product exactly (fma error term),
@@ -361,18 +371,18 @@ __global__ void __launch_bounds__(kThreads, 2) mr_dense(MrArgs a) {
   auto load = [&]() {
     const TcEntry en = a.entries[tl.first + lc.e];
     const TcPiece& q = a.pieces[en.piece];
-    const double* D = reinterpret_cast<const double*>(q.f2);
+    const float2* D = reinterpret_cast<const float2*>(q.f2);  // fp64 entries as fp32 pairs
     const int k = kK2 * lc.chunk + dk;
     const bool trans = q.pad != 0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int m = 4 * dm + t;
-      double d = 0.0;
+      float2 d = make_float2(0.f, 0.f);
       if (k < q.k && m >= en.dst && m < en.dst + en.nrows) {
         const int64_t row = en.src + (m - en.dst);
-        d = ldexp(__ldg(D + (trans ? row * q.ld2 + k : static_cast<int64_t>(k) * q.ld2 + row)), q.e);
+        d = __ldg(D + (trans ? row * q.ld2 + k : static_cast<int64_t>(k) * q.ld2 + row));
       }
-      split_d(d, dh[t], dl[t]);
+      pair_scaled(d, q.e, dh[t], dl[t]);
     }
 #pragma unroll
     for (int h = 0; h < XU; ++h) {

@@ -10,8 +10,8 @@
 //     RC * sizeof(fmt) = 2 KB per column.  Consumers compute
 //     sum_i f[i, j] in[in_off + i]; mode 0 stores it to t (low-rank phase 1),
 //     mode 1 adds it to out[out_off + j] (dense block, transposed product).
-// fp64 factors and dense blocks are computed in double-float arithmetic on
-// the fp32 pipe (split_f64 / dd_acc below).
+// fp64 factors and dense blocks (held as fp32 pairs) are computed in
+// double-float arithmetic on the fp32 pipe (dd_acc below).
 //
 //   phase 2 item: rows [lo, hi) (at most RT, RT * sizeof(fmt) = 1 KB) of a
 //     factor f with `cols` columns; stage s holds columns [s*16, s*16+16) of
@@ -173,26 +173,17 @@ __device__ __forceinline__ void dec8(uint2 w, float* v) {
 }
 
 // ------------------------------------------------- fp64 on the fp32 pipe
-// An fp64 factor value v (scaled so |v| <= 1) is split with integer
-// operations into fp32 halves v ~= hi + lo: hi keeps the leading 24
-// significant bits, lo the next 23 (47 bits, truncated; values below 2^-103
-// keep only hi, below 2^-126 flush to 0, both negligible against the
-// block's largest entry).  Products of such pairs with the fp32 halves of
-// the input are summed as unevaluated pairs S + C (two-sum of the leading
-// products, the small cross terms gathered in C): about 2^-46 relative per
-// product, without the device's low-rate fp64 units.
-__device__ __forceinline__ void split_f64(double v, float& hi, float& lo) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
-  const uint32_t h = static_cast<uint32_t>(b >> 32), l = static_cast<uint32_t>(b);
-  const uint32_t e = (h >> 20) & 0x7ffu;
-  const uint32_t sign = h & 0x80000000u;
-  const uint32_t hb = sign | ((e - 896u) << 23) | ((h & 0xfffffu) << 3) | (l >> 29);
-  const uint32_t el = e - 919u;  // fp32 biased exponent of 2^(e - 1023 - 23)
-  const float a = __uint_as_float(sign | (el << 23) | ((l >> 6) & 0x7fffffu));
-  const float c = __uint_as_float(sign | (el << 23));
-  hi = (e >= 897u) ? __uint_as_float(hb) : 0.f;
-  lo = (e >= 920u) ? a - c : 0.f;
-}
+// fp64 factors and dense blocks are held on the device as pairs of fp32
+// values in the same 8 bytes (v ~= hi + lo, hi = fl32(v), lo = fl32(v - hi),
+// written once when the matrix is uploaded; about 2^-48 relative, values
+// below 2^-126 of the block's largest entry flushed).  Products of such
+// pairs with the fp32 halves of the input are summed as unevaluated pairs
+// S + C (two-sum of the leading products, the small cross terms gathered in
+// C): about 2^-46 relative per product, without the device's low-rate fp64
+// units.  Reductions of pairs and the conversion of the result to fp64 stay
+// off those units too (dd_add, f2d_scaled): on this device a single fp64
+// instruction per output costs as much issue time as the whole fp32 pipeline
+// of a stage.
 
 // (S, C) += (vh + vl) * (xh + xl), dropping vl * xl
 __device__ __forceinline__ void dd_acc(float& S, float& C, float vh, float vl, float xh, float xl) {
@@ -204,6 +195,30 @@ __device__ __forceinline__ void dd_acc(float& S, float& C, float vh, float vl, f
   const float err = (S - (t - bp)) + (p - bp);
   S = t;
   C += err + cr;
+}
+
+// (S, C) += (s2, c2): leading parts by two-sum, trailing parts in fp32
+__device__ __forceinline__ void dd_add(float& S, float& C, float s2, float c2) {
+  const float t = S + s2;
+  const float bp = t - S;
+  const float err = (S - (t - bp)) + (s2 - bp);
+  S = t;
+  C += err + c2;
+}
+
+// v * 2^e as an fp64 value, built from v's bits with integer operations
+// (exact); zero, subnormal, non-finite or out-of-range results take the
+// fp64 units (rare)
+__device__ __forceinline__ double f2d_scaled(float v, int e) {
+  const uint32_t b = __float_as_uint(v);
+  const int ex = static_cast<int>((b >> 23) & 0xffu);
+  if ((b & 0x7fffffffu) == 0u) return 0.0;
+  const int de = ex - 127 + 1023 + e;
+  if (ex == 0 || ex == 255 || de < 1 || de > 2046) return ldexp(static_cast<double>(v), e);
+  const unsigned long long bits = (static_cast<unsigned long long>(b & 0x80000000u) << 32) |
+                                  (static_cast<unsigned long long>(de) << 52) |
+                                  (static_cast<unsigned long long>(b & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(bits));
 }
 
 // ---------------------------------------------------------------- producer
@@ -384,10 +399,8 @@ __device__ __forceinline__ void p1_consume_stage(const uint8_t* data, const floa
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         if (!(c ? c1 : c0)) continue;
-        const double2 f = *reinterpret_cast<const double2*>(data + (wc + c * kConsumers) * kP1ColBytes + r * 8);
-        float h0, l0, h1, l1;
-        split_f64(f.x, h0, l0);
-        split_f64(f.y, h1, l1);
+        const float4 f = *reinterpret_cast<const float4*>(data + (wc + c * kConsumers) * kP1ColBytes + r * 8);
+        const float h0 = f.x, l0 = f.y, h1 = f.z, l1 = f.w;
 #pragma unroll
         for (int rr = 0; rr < NR; ++rr) {
           dd_acc(acd[c][rr][q0 + 0], acd[c][rr][q0 + 1], h0, l0, xh[rr][0], xl[rr][0]);
@@ -447,19 +460,24 @@ __device__ __forceinline__ void p1_flush(const Meta& m, const StreamArgs& a, int
 #pragma unroll
     for (int rr = 0; rr < NR; ++rr) {
       if (m.fmt == 0) {
-        double s = 0.0;
+        float S = acd[c][rr][0], C = acd[c][rr][1];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) s += static_cast<double>(acd[c][rr][q]);
+        for (int q = 1; q < 8; ++q) dd_add(S, C, acd[c][rr][2 * q], acd[c][rr][2 * q + 1]);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        for (int off = 16; off > 0; off >>= 1) {
+          const float s2 = __shfl_xor_sync(0xffffffffu, S, off), c2 = __shfl_xor_sync(0xffffffffu, C, off);
+          dd_add(S, C, s2, c2);
+        }
+        float th = S, tl = 0.f;  // renormalised: th = fl32(S + C), tl the rest
+        dd_add(th, tl, C, 0.f);
         if (lane == 0 && col < ncols) {
           const int j = m.lo + col;
           if (m.mode == 0) {  // t of an fp64 block, kept as its two fp32 halves
-            const float th = __double2float_rn(s);
-            a.t64[m.toff + static_cast<int64_t>(j) * NR + rr] =
-                make_float2(th, __double2float_rn(s - static_cast<double>(th)));
+            a.t64[m.toff + static_cast<int64_t>(j) * NR + rr] = make_float2(th, tl);
           } else {
-            atomicAdd(a.acc + static_cast<size_t>(rr) * a.npad + m.out_off + j, ldexp(s, m.e));
+            double* o = a.acc + static_cast<size_t>(rr) * a.npad + m.out_off + j;
+            atomicAdd(o, f2d_scaled(th, m.e));
+            if (tl != 0.f) atomicAdd(o, f2d_scaled(tl, m.e));
           }
         }
       } else {
@@ -486,9 +504,8 @@ __device__ __forceinline__ void p2_consume_stage(const uint8_t* data, const Meta
     // one row per thread; column c feeds the double-float chain c % 8:
     // (accd[rr][2q], accd[rr][2q+1]), q = c % 8
     auto column = [&](int c, float& S, float& C, int rr0) {
-      const double f = *reinterpret_cast<const double*>(data + c * kP2RowBytes + ct * 8);
-      float fh, fl;
-      split_f64(f, fh, fl);
+      const float2 f = *reinterpret_cast<const float2*>(data + c * kP2RowBytes + ct * 8);
+      const float fh = f.x, fl = f.y;
       const int j = col0 + c;
       float th, tl;
       if (m.mode == 0) {
@@ -548,10 +565,12 @@ __device__ __forceinline__ void p2_flush(const Meta& m, const StreamArgs& a, int
     if (row0 < m.hi)
 #pragma unroll
       for (int rr = 0; rr < NR; ++rr) {
-        double v = 0.0;
+        float S = accd[rr][0], C = accd[rr][1];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v += static_cast<double>(accd[rr][q]);
-        atomicAdd(a.acc + static_cast<size_t>(rr) * a.npad + m.out_off + row0, ldexp(v, m.e));
+        for (int q = 1; q < 8; ++q) dd_add(S, C, accd[rr][2 * q], accd[rr][2 * q + 1]);
+        double* o = a.acc + static_cast<size_t>(rr) * a.npad + m.out_off + row0;
+        atomicAdd(o, f2d_scaled(S, m.e));
+        if (C != 0.f) atomicAdd(o, f2d_scaled(C, m.e));
       }
     return;
   }
@@ -562,8 +581,7 @@ __device__ __forceinline__ void p2_flush(const Meta& m, const StreamArgs& a, int
     if (row < m.hi)
 #pragma unroll
       for (int rr = 0; rr < NR; ++rr)
-        atomicAdd(a.acc + static_cast<size_t>(rr) * a.npad + m.out_off + row,
-                  ldexp(static_cast<double>(acc[e][rr]), m.e));
+        atomicAdd(a.acc + static_cast<size_t>(rr) * a.npad + m.out_off + row, f2d_scaled(acc[e][rr], m.e));
   }
 }
 

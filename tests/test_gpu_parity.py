@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 
 import hh_workloads as W
+from rowparity import assert_clusters
 from oracle import build as OB
 from oracle.compress import kernel_entries
 from oracle import hhfile
@@ -55,10 +56,16 @@ def oracle_pair(P, tmp_path, pts, kernel, param, leaf, ell, tol, mask):
 
 
 def check_against(P, H, O, x, tol):
+    """Forward and transposed product against the oracle: the whole vector
+    and every leaf cluster's rows at the same relative tolerance."""
     y = H.matvec(gpu(x)).cpu().numpy()
-    assert rel(y, M.matvec(O, x)) <= tol
+    ref = M.matvec(O, x)
+    assert rel(y, ref) <= tol
+    assert_clusters(y, ref, O, tol)
     z = H.matvec(gpu(x), transpose=True).cpu().numpy()
-    assert rel(z, M.matvec_T(O, x)) <= tol
+    ref = M.matvec_T(O, x)
+    assert rel(z, ref) <= tol
+    assert_clusters(z, ref, O, tol)
     H.sync_status()
 
 
@@ -77,6 +84,7 @@ def test_fp64_path_matches_oracle_file(P, tmp_path):
         assert xv.stride(1) == len(pts) + 7
         y = H.matvec(xv).cpu().numpy()
         assert rel(y, M.matvec(O, xs)) <= TOL64
+        assert_clusters(y, M.matvec(O, xs), O, TOL64)
 
 
 @pytest.mark.parametrize("n,dim,kernel,param,ell,tol,nfmt", [(8192, 3, W.GAUSS, 0.01, 4, 1e-3, 3),
@@ -90,7 +98,9 @@ def test_adaptive_formats_match_oracle_file(P, tmp_path, n, dim, kernel, param, 
     x = W.rhs(n, 1, "uniform", 6)[:, 0]
     check_against(P, H, O, x, TOL32)
     xs = W.rhs(n, 4, "normal", 7)
-    assert rel(H.matvec(gpu(xs)).cpu().numpy(), M.matvec(O, xs)) <= TOL32
+    y4 = H.matvec(gpu(xs)).cpu().numpy()
+    assert rel(y4, M.matvec(O, xs)) <= TOL32
+    assert_clusters(y4, M.matvec(O, xs), O, TOL32)
 
 
 @pytest.mark.parametrize("dim,kernel", [(3, W.INV_R), (2, W.LOG)])
@@ -201,8 +211,11 @@ def test_full_size_adaptive_65k(P, adaptive_65k, tmp_path):
         y = H.matvec(gpu(x)).cpu().numpy()
         yo = M.matvec(G, x)
         assert rel(y, yo) <= tol
+        assert_clusters(y, yo, G, tol)
         z = H.matvec(gpu(x), transpose=True).cpu().numpy()
-        assert rel(z, M.matvec_T(G, x)) <= tol
+        zo = M.matvec_T(G, x)
+        assert rel(z, zo) <= tol
+        assert_clusters(z, zo, G, tol)
         del G
     # backward error against the exact kernel on 1024 sampled rows
     rows = np.random.default_rng(0).choice(len(pts), 1024, replace=False)
@@ -301,6 +314,7 @@ def test_batch_one_launch_sequence_and_graph(P, tmp_path):
             a, b = B.offsets[i], B.offsets[i + 1]
             ref = M.matvec_T(O, xs[i]) if tr else M.matvec(O, xs[i])
             assert rel(y1[a:b], ref) <= TOL32
+            assert_clusters(y1[a:b], ref, O, TOL32)
         # replays agree up to the order of the fp64 atomic additions
         assert rel(y3, y2) <= 1e-12
         assert rel(y2, y1) <= 1e-12
@@ -322,6 +336,7 @@ def test_batch_fp64_matrices_match_at_1e12(P, tmp_path):
     for i, O in enumerate(oracles):
         a, b = B.offsets[i], B.offsets[i + 1]
         assert rel(y[a:b], M.matvec(O, xs[i])) <= TOL64
+        assert_clusters(y[a:b], M.matvec(O, xs[i]), O, TOL64)
     B.close()
 
 

@@ -26,6 +26,7 @@ import numpy as np
 import pytest
 
 import hh_workloads as W
+from rowparity import assert_clusters
 from oracle import hhfile
 from oracle import matvec as M
 from oracle.compress import kernel_entries
@@ -108,6 +109,7 @@ def check(H, O, nrhs, transpose, seed):
     ab = abs_product(O, x, transpose)
     d = y - ref
     assert np.linalg.norm(d) <= TOL * np.linalg.norm(ref) + np.linalg.norm(ab)
+    assert_clusters(y, ref, O, TOL, extra=ab)          # the same bound per leaf cluster
     for c in range(nrhs):
         assert np.linalg.norm(d[:, c]) <= TOL * np.linalg.norm(ref[:, c]) + np.linalg.norm(ab[:, c])
     return x, y

@@ -58,6 +58,11 @@ MANY_N = {"multirhs_65k": 65536, "multirhs_262k": 262144}
 for _k, _n in MANY_N.items():
     WORKLOADS[_k] = (f"N={_n:,} points U[0,1]^3, Gaussian exp(-r^2/0.01), leaf 128, eta 1, switch level 5, "
                      "tol 1e-6, adaptive {fp64,fp32,bf16,e4m3}, R right-hand sides N(0,1) per product")
+# the 16/8-bit single-column field alone (its own line; for captures)
+LOWBIT_N = {"lowbit_65k": 65536, "lowbit_16k": 16384}
+for _k, _n in LOWBIT_N.items():
+    WORKLOADS[_k] = (f"N={_n:,} points U[0,1]^3, Gaussian exp(-r^2/0.01), leaf 128, eta 1, switch level 5, "
+                     "tol 1e-6, adaptive {fp64,fp32,bf16,e4m3}, 1 RHS N(0,1)")
 WORKLOADS["uneven_batch"] = ("64 independent matrices, N log-uniform in [nmin, nmax] (preset [2,048, 131,072]); "
                              "even index 2-D exp(-r) leaf 64, odd index 3-D 1/r leaf 128; eta 1, switch level "
                              "floor(L/2), tol 1e-6, adaptive {fp64,fp32,fp16,bf16}; one RHS U(-1,1) each")
@@ -276,18 +281,24 @@ def run_reference(args):
         return 0
     import paper_2604_09147_gb300 as P
     per_step = max(0.5, 120.0 / max(1, args.steps + args.warmup))
-    if args.workload in MANY_N:
+    if args.workload in MANY_N or args.workload in LOWBIT_N:
+        nr = 1 if args.workload in LOWBIT_N else args.nrhs
         c = W.CONFIGS["multirhs_262k"]
-        pts = W.config_points("multirhs_262k", MANY_N[args.workload])
+        pts = W.config_points("multirhs_262k", {**MANY_N, **LOWBIT_N}[args.workload])
         H = P.HMatrix.build_cached(pts, CACHE, c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"],
                                    c["tol"], c["fmts"], device=-1)
         path = os.path.join(CACHE, f"bench_{args.workload}_ref.hhm")
         H.save(path)
-        x = W.config_rhs("multirhs_262k", nrhs=args.nrhs, n=len(pts))
+        x = W.config_rhs("multirhs_262k", nrhs=nr, n=len(pts))
+        if nr == 1:
+            x = x[:, 0]
         rate, desc, el = oracle_sample(path, x, per_step * args.steps)
-        rate, unit = rate * args.nrhs, "rhs/s"
-        metric = "H_h matvec right-hand sides/s (adaptive precision, many right-hand sides)"
-        desc += f", {args.nrhs} columns per pass"
+        if args.workload in LOWBIT_N:
+            unit, metric = "matvec/s", "H_h matvecs/s (adaptive precision), HBM GB/s and fraction of peak"
+        else:
+            rate, unit = rate * nr, "rhs/s"
+            metric = "H_h matvec right-hand sides/s (adaptive precision, many right-hand sides)"
+            desc += f", {nr} columns per pass"
     else:
         c = W.CONFIGS["adaptive_65k"]
         pts = W.config_points("adaptive_65k", WORKLOAD_N[args.workload])
@@ -309,6 +320,91 @@ def run_reference(args):
                             "sample": desc},
            "e2e": {"value": rate, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+    return 0
+
+
+def low_bit_field(args, P, torch, rank, ws, dev, clocks=None):
+    """Single right-hand side on a matrix with 16- and 8-bit factors:
+    N = 65,536 (--low-bit-n) points U[0,1]^3, Gaussian exp(-r^2/0.01), leaf 128,
+    eta 1, switch level 5, tol 1e-6, {fp64, fp32, bf16, e4m3} (the
+    many-right-hand-side workload's family), one N(0,1) right-hand side.
+    Times the streaming passes with their bf16 / e4m3 decoding; reports the
+    blocks and bytes per format, GB/s, the HBM fraction per phase and the
+    error against the oracle on sampled leaf-cluster rows."""
+    c = W.CONFIGS["multirhs_262k"]
+    pts = W.config_points("multirhs_262k", args.low_bit_n)
+    t0 = time.time()
+    H = P.HMatrix.build_cached(pts, CACHE, c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"], c["tol"],
+                               c["fmts"], device=dev)
+    build_s = time.time() - t0
+    n = len(pts)
+    x0 = W.config_rhs("multirhs_262k", nrhs=1, n=n)[:, 0]
+    x = torch.from_numpy(x0.copy()).cuda()
+    y = torch.empty_like(x)
+    tuned = None if args.no_autotune else H.autotune(0)
+    inf = H.info()
+    for _ in range(max(3, args.warmup)):
+        H.matvec(x, out=y)
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+    t = timed_loop(torch, H, x, y, args.steps, ws)
+    clk = clocks.stop() if clocks is not None else None
+    t = max_over_ranks(torch, t, ws)
+    ms = t / args.steps
+    hbm, peak_kind = peaks()
+    phases = np.mean([H.matvec_timed(x, y) for _ in range(min(args.steps, 100))], axis=0)
+    b1, b2 = inf["v_bytes"], inf["u_bytes"] + inf["dense_bytes"]
+    out = {"workload": f"N={n:,} points U[0,1]^3, Gaussian exp(-r^2/0.01), leaf 128, eta 1, switch level 5, "
+                       "tol 1e-6, adaptive {fp64,fp32,bf16,e4m3}, 1 RHS N(0,1)",
+           "ms_per_step": ms, "value": 1e3 / ms, "unit": "matvec/s",
+           "gbs": inf["bytes_per_matvec"] / (ms * 1e-3) / 1e9,
+           "hbm_frac": inf["bytes_per_matvec"] / (ms * 1e-3) / 1e9 / hbm, "peak_kind": f"of {peak_kind}",
+           "blocks_per_fmt": inf["blocks_per_fmt"], "factor_bytes_per_fmt": inf["factor_bytes_per_fmt"],
+           "phase_ms": {"prep": phases[0], "phase1": phases[1], "phase2": phases[2], "finish": phases[3]},
+           "phase1_hbm_frac": b1 / (phases[1] * 1e-3) / 1e9 / hbm,
+           "phase2_hbm_frac": b2 / (phases[2] * 1e-3) / 1e9 / hbm,
+           "build_seconds": build_s, "autotune": tuned, "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        try:
+            from oracle import hhfile
+            ya = H.matvec(x).cpu().numpy()
+            path = os.path.join(CACHE, "bench_low_bit.hhm")
+            H.save(path)
+            G = hhfile.read(path)
+            out["parity"] = oracle_rows_check(G, x0, ya)
+            out["parity"].update({"tol": 1e-6, "bound_thm44": inf["bound_thm44"]})
+            del G
+        except Exception as e:  # reported, not fatal to the measurement
+            out["parity"] = {"error": f"{type(e).__name__}: {e}"}
+    return out
+
+
+def run_low_bit(args):
+    """The 16/8-bit single-column matrix as the line's own workload."""
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", init_method="env://")
+    dev = torch.cuda.current_device()
+    import paper_2604_09147_gb300 as P
+    from paper_2604_09147_gb300 import build as B
+    B.build()
+    args.low_bit_n = LOWBIT_N[args.workload]
+    f = low_bit_field(args, P, torch, rank, ws, dev, clocks=ClockSampler(dev))
+    clk = f.pop("clocks")
+    out = {"metric": "H_h matvecs/s (adaptive precision), HBM GB/s and fraction of peak",
+           "value": ws * f["value"], "unit": "matvec/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": f["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOADS[args.workload], "n": args.low_bit_n, "nrhs": 1,
+                      "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2"},
+           "gpu_launches": 4 * args.steps, "clocks": clk, "detail": f}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -395,6 +491,8 @@ def run_ours(args):
                        "vs": "oracle Algorithm 4 (float64) over the same stored factors, sampled leaf-cluster rows"})
         del G
 
+    low_bit = None if args.no_low_bit else low_bit_field(args, P, torch, rank, ws, dev)
+
     gbs = inf["bytes_per_matvec"] / (ms_amp * 1e-3) / 1e9
     gbs64 = inf64["bytes_per_matvec"] / (ms_64 * 1e-3) / 1e9
     out = {
@@ -418,6 +516,7 @@ def run_ours(args):
         "build_seconds": build_s,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "parity": parity,
         "gpu_launches": 4 * args.steps, "clocks": clk, "autotune": tuned,
+        "low_bit_1rhs": low_bit,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -722,6 +821,10 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="adaptive_65k")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU oracle baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-low-bit", action="store_true",
+                    help="skip the 16/8-bit single-column field of the default line")
+    ap.add_argument("--low-bit-n", type=int, default=65536,
+                    help="points of that field's matrix (16,384 for ncu captures)")
     ap.add_argument("--nrhs", type=int, default=128, help="right-hand sides per product (multirhs workloads)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch parameters (for profiling runs with a fixed launch sequence)")
@@ -737,6 +840,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload in MANY_N:
         return run_many(args)
+    if args.workload in LOWBIT_N:
+        return run_low_bit(args)
     if args.workload == "uneven_batch":
         return run_batch(args)
     return run_ours(args)

@@ -216,9 +216,15 @@ void build_stream_set(hh_matrix* h, int dir, const std::vector<int64_t>& toff, c
     double cost;
   };
   std::vector<Costed> items[2];
+  // phase-1 items: whole groups of cols1 columns, as many groups (at most 8)
+  // as make about 64 KB of factor bytes, so that short columns do not pay the
+  // per-item scheduling latency every stage
   auto add_cols = [&](int phase, int di, int64_t rows, int64_t cols, int sz) {
-    for (int64_t j = 0; j < cols; j += cols1) {
-      int64_t hi = std::min<int64_t>(cols, j + cols1);
+    const int64_t group_bytes = std::max<int64_t>(1, int64_t(cols1) * rows * sz);
+    const int64_t groups = std::max<int64_t>(1, std::min<int64_t>(8, ((int64_t(64) << 10) + group_bytes - 1) / group_bytes));
+    const int64_t per = cols1 * groups;
+    for (int64_t j = 0; j < cols; j += per) {
+      int64_t hi = std::min<int64_t>(cols, j + per);
       items[phase].push_back({{0, di, (int32_t)j, (int32_t)hi}, double(hi - j) * double(rows * sz)});
     }
   };

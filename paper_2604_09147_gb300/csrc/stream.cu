@@ -235,11 +235,14 @@ __device__ void produce(Smem<PHASE, FSET>& sm, const StreamArgs& a) {
   bool ok = true;
   int issued_mask = 0;  // stages whose copies may be in flight after a timeout
   uint32_t issued_par[kStages] = {};  // full-barrier phase parity of the last issue per stage
+  // the next item's number is taken from the counter while the current
+  // item's stages are issued, so that the atomic's round trip overlaps them
+  int next = 0;
+  if (lane == 0) next = atomicAdd(a.counter, 1);
   while (ok) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(a.counter, 1);
-    item = __shfl_sync(0xffffffffu, item, 0);
+    const int item = __shfl_sync(0xffffffffu, next, 0);
     if (item >= a.n_items) break;
+    if (lane == 0) next = atomicAdd(a.counter, 1);
     const Item it = a.items[item];
     const StreamDesc d = a.desc[it.idx];
     const int sz = fmt_size(d.fmt);
@@ -253,7 +256,14 @@ __device__ void produce(Smem<PHASE, FSET>& sm, const StreamArgs& a) {
       nparts = (d.cols + per - 1) / per;
       if (nparts == 0) nparts = 1;
     }
-    for (int p = 0; p < nparts; ++p) {
+    // phase 1: an item of short columns spans several groups of kP1Cols
+    // columns, streamed group after group (each group is a run of stages the
+    // consumers reduce and flush on its own)
+    const int ngroups = PHASE == 1 ? (it.hi - it.lo + kP1Cols - 1) / kP1Cols : 1;
+    for (int q = 0; q < ngroups * nparts; ++q) {
+      const int p = q % nparts;
+      const int glo = PHASE == 1 ? it.lo + (q / nparts) * kP1Cols : it.lo;
+      const int ghi = PHASE == 1 ? min(glo + kP1Cols, it.hi) : it.hi;
       if (!mbar_wait(&sm.empty[stage], par, a.status)) {
         ok = false;
         break;
@@ -265,8 +275,8 @@ __device__ void produce(Smem<PHASE, FSET>& sm, const StreamArgs& a) {
         count = min(per, d.rows - p * per);
         if (count < 0) count = 0;
         bytes_each = ((count * sz) + 15) & ~15;
-        nseg = it.hi - it.lo;
-        src0 = d.f + (static_cast<size_t>(it.lo) * d.ld + static_cast<size_t>(p) * per) * sz;
+        nseg = ghi - glo;
+        src0 = d.f + (static_cast<size_t>(glo) * d.ld + static_cast<size_t>(p) * per) * sz;
         seg_stride = static_cast<size_t>(d.ld) * sz;
       } else {
         count = min(per, d.cols - p * per);
@@ -300,8 +310,8 @@ __device__ void produce(Smem<PHASE, FSET>& sm, const StreamArgs& a) {
         m.fmt = d.fmt;
         m.mode = d.mode;
         m.e = d.e;
-        m.lo = it.lo;
-        m.hi = it.hi;
+        m.lo = glo;
+        m.hi = ghi;
         m.in_off = d.in_off;
         m.out_off = d.out_off;
         m.xs = xbytes > 0;
@@ -410,17 +420,26 @@ __device__ __forceinline__ void p1_consume_stage(const uint8_t* data, const floa
     }
   } else {
     constexpr int EPV = 16 / SZ;  // elements per 16-byte vector
+    constexpr int NCH = EPV / 4;  // float4 chunks of input per vector (1, 2 or 4)
+    // A lane's input rows are EPV * 4 bytes apart from its neighbour's: with
+    // 16- and 8-bit factors the warp's 16-byte input reads would fall on 2 or 4
+    // times fewer shared-memory bank groups than lanes need.  Each lane
+    // therefore visits its chunks in an order rotated by rot (and rotates the
+    // factor words alike), which spreads every read over all bank groups.
+    const int rot = NCH == 4 ? ((lane >> 1) & 3) : (NCH == 2 ? ((lane >> 2) & 1) : 0);
 #pragma unroll
     for (int g = 0; g < RC / (32 * EPV); ++g) {
       const int r = g * 32 * EPV + lane * EPV;
       if (r >= m.count) break;
       // the input of these EPV rows, NR right-hand sides
+      // chunk j of the lane's registers holds input chunk (j + rot) mod NCH
       float xv[NR][EPV];
       if (NR == 1 && m.xs) {
 #pragma unroll
-        for (int e4 = 0; e4 < EPV; e4 += 4) {
+        for (int j = 0; j < NCH; ++j) {
+          const int e4 = 4 * ((j + rot) & (NCH - 1));
           const float4 v = *reinterpret_cast<const float4*>(xsm + r + e4);
-          xv[0][e4] = v.x; xv[0][e4 + 1] = v.y; xv[0][e4 + 2] = v.z; xv[0][e4 + 3] = v.w;
+          xv[0][4 * j] = v.x; xv[0][4 * j + 1] = v.y; xv[0][4 * j + 2] = v.z; xv[0][4 * j + 3] = v.w;
         }
       } else {
         const int q = m.in_off + row_base + r, s = q & 3;
@@ -428,9 +447,10 @@ __device__ __forceinline__ void p1_consume_stage(const uint8_t* data, const floa
         for (int rr = 0; rr < NR; ++rr) {
           const float* xp = a.xs + static_cast<size_t>(s * NR + rr) * a.npad + (q - s);
 #pragma unroll
-          for (int e4 = 0; e4 < EPV; e4 += 4) {
+          for (int j = 0; j < NCH; ++j) {
+            const int e4 = 4 * ((j + rot) & (NCH - 1));
             const float4 v = __ldg(reinterpret_cast<const float4*>(xp + e4));
-            xv[rr][e4] = v.x; xv[rr][e4 + 1] = v.y; xv[rr][e4 + 2] = v.z; xv[rr][e4 + 3] = v.w;
+            xv[rr][4 * j] = v.x; xv[rr][4 * j + 1] = v.y; xv[rr][4 * j + 2] = v.z; xv[rr][4 * j + 3] = v.w;
           }
         }
       }
@@ -438,9 +458,17 @@ __device__ __forceinline__ void p1_consume_stage(const uint8_t* data, const floa
       for (int c = 0; c < 2; ++c) {
         if (!(c ? c1 : c0)) continue;
         const uint4 raw = *reinterpret_cast<const uint4*>(data + (wc + c * kConsumers) * kP1ColBytes + r * SZ);
+        // the factor's 32-bit words in the same rotated chunk order
+        uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+        if constexpr (NCH == 4) {
+          if (rot & 1) { const uint32_t t = w[0]; w[0] = w[1]; w[1] = w[2]; w[2] = w[3]; w[3] = t; }
+          if (rot & 2) { uint32_t t = w[0]; w[0] = w[2]; w[2] = t; t = w[1]; w[1] = w[3]; w[3] = t; }
+        } else if constexpr (NCH == 2) {
+          if (rot) { uint32_t t = w[0]; w[0] = w[2]; w[2] = t; t = w[1]; w[1] = w[3]; w[3] = t; }
+        }
         float f[EPV];
-        dec8<FMT>(make_uint2(raw.x, raw.y), f);
-        dec8<FMT>(make_uint2(raw.z, raw.w), f + EPV / 2);
+        dec8<FMT>(make_uint2(w[0], w[1]), f);
+        dec8<FMT>(make_uint2(w[2], w[3]), f + EPV / 2);
 #pragma unroll
         for (int rr = 0; rr < NR; ++rr)
 #pragma unroll

@@ -208,6 +208,31 @@ int hh_optimal_switch_level(const double* points, int64_t n, int dim, int kernel
                             int leaf_size, double eta, double tol, uint32_t fmt_mask, uint64_t seed, int tree,
                             int* ell_star, int* depth, double* gains);
 
+/* hh_shard_plan -- ownership of the product's block rows by nranks ranks
+ * (one GPU each).  In Algorithm 4 (Section 4.4) every block row
+ * b_I = sum_J H_IJ x_J is independent of the others, so the rows split into
+ * contiguous ranges of tree positions: bounds[0] = 0 <= bounds[1] <= ... <=
+ * bounds[nranks] = n (nranks + 1 int64, caller-owned, host), rank r owning
+ * [bounds[r], bounds[r+1]).  The ranges are unions of consecutive clusters of
+ * tree level min(L, ceil(log2 nranks) + 3), balanced by the factor and dense
+ * bytes their rows stream (a block cut by a boundary counts its U rows to
+ * their owner and a row share of its V to each).  Host-only, deterministic;
+ * HH_EINVAL for a null handle or bounds, or nranks < 1. */
+int hh_shard_plan(hh_handle h, int nranks, int64_t* bounds);
+
+/* hh_shard -- the matrix of block rows [p0, p1) (tree positions, p0 and p1
+ * from hh_shard_plan or any cluster boundaries) as a handle of its own on
+ * `device` (-1: host only): every low-rank block whose row cluster meets the
+ * range, cut to those rows (U's rows, V whole, factors copied into a compact
+ * arena, formats and scales unchanged), and the dense blocks inside the
+ * range.  Its point order IS the tree order (identity permutation): hh_matvec
+ * on it takes all of x in tree order and returns y in tree order, exact in
+ * [p0, p1) and zero elsewhere; hh_matvec_T reads only rows [p0, p1) of
+ * y_bar and returns this range's contribution to all of x_bar (the sum over
+ * the ranks' shards is A_h^T y_bar).  The shard is independent of h.
+ * HH_EINVAL if the range lies outside [0, n] or cuts a dense block. */
+int hh_shard(hh_handle h, int64_t p0, int64_t p1, int device, hh_handle* out);
+
 /* hh_save -- write the handle's matrix (points, tree, block tables, factor
  * arena in stored formats, dense blocks) to `path`. */
 int hh_save(hh_handle h, const char* path);

@@ -71,6 +71,8 @@ def _load():
         "hh_optimal_switch_level": (I32, [P, I64, I32, I32, D, I32, D, D, U32, U64, I32, c.POINTER(I32),
                                           c.POINTER(I32), c.POINTER(D)]),
         "hh_save": (I32, [P, c.c_char_p]),
+        "hh_shard_plan": (I32, [P, I32, c.POINTER(I64)]),
+        "hh_shard": (I32, [P, I64, I64, I32, c.POINTER(P)]),
         "hh_info": (I32, [P, c.POINTER(_Info)]),
         "hh_perm": (I32, [P, P]),
         "hh_matvec": (I32, [P, P, P, I32, I64, I64, P]),
@@ -206,6 +208,22 @@ class HMatrix:
 
     def save(self, path: str) -> None:
         _check(_L().hh_save(self._h, os.fsencode(path)))
+
+    # -- several GPUs ------------------------------------------------------
+    def shard_plan(self, nranks: int) -> list[int]:
+        """hh_shard_plan: tree-position bounds of the block rows of nranks ranks."""
+        b = (ctypes.c_int64 * (nranks + 1))()
+        _check(_L().hh_shard_plan(self._h, int(nranks), b))
+        return [int(v) for v in b]
+
+    def shard(self, p0: int, p1: int, device: int | None = None) -> "HMatrix":
+        """hh_shard: the block rows [p0, p1) as a matrix whose vectors are in
+        tree order (see paper_2604_09147_gb300.dist for the collectives)."""
+        if device is None:
+            device = self.device
+        out = ctypes.c_void_p()
+        _check(_L().hh_shard(self._h, int(p0), int(p1), device, ctypes.byref(out)))
+        return HMatrix(out.value, device)
 
     def close(self) -> None:
         if self._h is not None and self._h.value:

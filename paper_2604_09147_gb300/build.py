@@ -25,7 +25,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libhh.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-HOST_SRCS = ["builder.cpp", "linalg.cpp", "hhio.cpp"]
+HOST_SRCS = ["builder.cpp", "linalg.cpp", "hhio.cpp", "shard.cpp"]
 CUDA_SRCS = ["kernels.cu", "stream.cu", "tc.cu", "mr.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

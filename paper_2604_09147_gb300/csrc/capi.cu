@@ -1178,6 +1178,37 @@ int hh_reencode(hh_handle src, uint32_t fmt_mask, int device, hh_handle* out) {
   return finish_construction(h, device, out);
 }
 
+int hh_shard_plan(hh_handle h, int nranks, int64_t* bounds) {
+  if (!h || nranks < 1 || !bounds) return fail(HH_EINVAL, "null handle or bounds, or nranks < 1");
+  try {
+    std::vector<int64_t> b;
+    hh::shard_plan(h->H, nranks, b);
+    std::copy(b.begin(), b.end(), bounds);
+  } catch (const std::bad_alloc&) {
+    return fail(HH_ENOMEM, "out of host memory");
+  } catch (const std::exception& e) {
+    return fail(HH_EINVAL, e.what());
+  }
+  return HH_OK;
+}
+
+int hh_shard(hh_handle h, int64_t p0, int64_t p1, int device, hh_handle* out) {
+  if (!h || !out) return fail(HH_EINVAL, "null handle or output");
+  if (p0 < 0 || p1 < p0 || p1 > h->H.n) return fail(HH_EINVAL, "shard range outside [0, n]");
+  hh_matrix* s = make_handle();
+  if (!s) return fail(HH_ENOMEM, "out of host memory");
+  try {
+    hh::make_shard(h->H, p0, p1, s->H);
+  } catch (const std::bad_alloc&) {
+    delete s;
+    return fail(HH_ENOMEM, "out of host memory");
+  } catch (const std::exception& e) {
+    delete s;
+    return fail(HH_EINVAL, e.what());
+  }
+  return finish_construction(s, device, out);
+}
+
 int hh_save(hh_handle h, const char* path) {
   if (!h || !path) return fail(HH_EINVAL, "null argument");
   try {

@@ -93,6 +93,14 @@ void validate(const HostMatrix& h);
 int optimal_switch_level(const double* points, int64_t n, int dim, const BuildParams& p, std::vector<double>& gains,
                          int& depth);
 
+// Several GPUs (shard.cpp): contiguous ranges of tree positions, one per
+// rank, balanced by the factor and dense bytes of their block rows
+// (bounds[0] = 0 <= ... <= bounds[nranks] = n); and the matrix of the block
+// rows [p0, p1): blocks cut to those rows, points in tree order, identity
+// permutation (its vectors are in tree order).
+void shard_plan(const HostMatrix& h, int nranks, std::vector<int64_t>& bounds);
+void make_shard(const HostMatrix& src, int64_t p0, int64_t p1, HostMatrix& out);
+
 // Derived quantities for hh_info.
 struct Summary {
   int64_t blocks_per_fmt[NFMT] = {0, 0, 0, 0, 0};

@@ -119,6 +119,10 @@ typedef struct {
   int32_t tree_step;              /* binary levels per tree level: 1 for the KD tree,
                                      d for the 2^d-tree (L, ell, csp are binary)   */
   int32_t pad_;
+  int32_t build_device;           /* GPU that compressed the blocks (hh_build_dev), -1: the host */
+  int32_t pad2_;
+  int64_t build_fallback;         /* blocks of a device build that the host compressed        */
+  double build_device_seconds;    /* wall time of the device compression                       */
 } hh_info_t;
 
 /*
@@ -168,6 +172,22 @@ int hh_build_ex(const double* points, int64_t n, int dim, int kernel, double ker
                 int leaf_size, double eta, int switch_level, double tol, uint32_t fmt_mask,
                 uint64_t seed, int tree, int device, hh_handle* out);
 
+/* hh_build_dev -- hh_build_ex with Algorithm 1's LRcompression (Eq. 2.1) of
+ * every admissible block run on GPU `device` (>= 0), which also receives the
+ * matrix.  Per block, in fp64: ACA with partial pivoting to eps / 100 (the
+ * entries of Eq. 5.1 generated from the points on the device), CholeskyQR2
+ * of both cross factors, the one-sided Jacobi SVD of the k x k core and the
+ * truncation of the Frobenius tail at 0.99 eps (U orthonormal, V = Z Sigma,
+ * as the host path).  Blocks whose rank would exceed 2,048 columns, or whose
+ * factorization fails, are compressed on the host (hh_info.build_fallback).
+ * The tree, the partition, Algorithm 5's norms, Algorithm 3's rule and the
+ * arena are as in hh_build_ex, so the result differs from it only by the
+ * compression's rounding (ranks within a few units, formats alike).
+ * Host-synchronous; errors as hh_build_ex, HH_ECUDA for a device failure. */
+int hh_build_dev(const double* points, int64_t n, int dim, int kernel, double kernel_param, int leaf_size,
+                 double eta, int switch_level, double tol, uint32_t fmt_mask, uint64_t seed, int tree, int device,
+                 hh_handle* out);
+
 /* hh_load -- read a file written by hh_save (or by any writer of the same
  * documented layout) and upload it to `device` (-1: host only).  The layout
  * is validated (offsets, alignment, bounds); a bad file gives HH_EINVAL. */
@@ -207,6 +227,12 @@ int hh_reencode(hh_handle src, uint32_t fmt_mask, int device, hh_handle* out);
 int hh_optimal_switch_level(const double* points, int64_t n, int dim, int kernel, double kernel_param,
                             int leaf_size, double eta, double tol, uint32_t fmt_mask, uint64_t seed, int tree,
                             int* ell_star, int* depth, double* gains);
+
+/* hh_optimal_switch_level_dev -- hh_optimal_switch_level with the
+ * compressions of every evaluated level on GPU `device` (as hh_build_dev). */
+int hh_optimal_switch_level_dev(const double* points, int64_t n, int dim, int kernel, double kernel_param,
+                                int leaf_size, double eta, double tol, uint32_t fmt_mask, uint64_t seed, int tree,
+                                int device, int* ell_star, int* depth, double* gains);
 
 /* hh_shard_plan -- ownership of the product's block rows by nranks ranks
  * (one GPU each).  In Algorithm 4 (Section 4.4) every block row

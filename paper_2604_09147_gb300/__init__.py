@@ -54,6 +54,8 @@ class _Info(ctypes.Structure):
         ("mr_u_elems", ctypes.c_int64), ("mr_v_elems", ctypes.c_int64), ("dense_elems", ctypes.c_int64),
         ("tuned", ctypes.c_int32), ("split_positions", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32 * 4),
         ("tc_panel_bytes", ctypes.c_int64 * 2), ("tree_step", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("build_device", ctypes.c_int32), ("pad2_", ctypes.c_int32), ("build_fallback", ctypes.c_int64),
+        ("build_device_seconds", ctypes.c_double),
     ]
 
 
@@ -66,6 +68,9 @@ def _load():
     sig = {
         "hh_build": (I32, [P, I64, I32, I32, D, I32, D, I32, D, U32, U64, I32, c.POINTER(P)]),
         "hh_build_ex": (I32, [P, I64, I32, I32, D, I32, D, I32, D, U32, U64, I32, I32, c.POINTER(P)]),
+        "hh_build_dev": (I32, [P, I64, I32, I32, D, I32, D, I32, D, U32, U64, I32, I32, c.POINTER(P)]),
+        "hh_optimal_switch_level_dev": (I32, [P, I64, I32, I32, D, I32, D, D, U32, U64, I32, I32, c.POINTER(I32),
+                                              c.POINTER(I32), c.POINTER(D)]),
         "hh_load": (I32, [c.c_char_p, I32, c.POINTER(P)]),
         "hh_reencode": (I32, [P, U32, I32, c.POINTER(P)]),
         "hh_optimal_switch_level": (I32, [P, I64, I32, I32, D, I32, D, D, U32, U64, I32, c.POINTER(I32),
@@ -151,9 +156,11 @@ class HMatrix:
     @classmethod
     def build(cls, points, kernel: int = INV_R, kernel_param: float = 1.0, leaf_size: int = 128,
               eta: float = 1.0, switch_level: int = -1, tol: float = 1e-6, fmt_mask: int = F64 | F32 | F16 | BF16,
-              seed: int = 0, device: int | None = None, tree: str = "kd") -> "HMatrix":
+              seed: int = 0, device: int | None = None, tree: str = "kd",
+              construct_on_device: bool = False) -> "HMatrix":
         """hh_build_ex; tree "kd" (binary KD bisection) or "2d" (the balanced
-        2^d-tree, switch_level in its levels)."""
+        2^d-tree, switch_level in its levels).  construct_on_device: the
+        blocks' compression runs on `device` (hh_build_dev)."""
         pts = np.ascontiguousarray(points.cpu().numpy() if isinstance(points, torch.Tensor) else points,
                                    dtype=np.float64)
         if pts.ndim != 2:
@@ -163,9 +170,9 @@ class HMatrix:
         if device is None:
             device = torch.cuda.current_device() if torch.cuda.is_available() else -1
         out = ctypes.c_void_p()
-        _check(_L().hh_build_ex(pts.ctypes.data, pts.shape[0], pts.shape[1], kernel, kernel_param, leaf_size,
-                                eta, switch_level, tol, fmt_mask, seed, 1 if tree == "2d" else 0, device,
-                                ctypes.byref(out)))
+        fn = _L().hh_build_dev if construct_on_device else _L().hh_build_ex
+        _check(fn(pts.ctypes.data, pts.shape[0], pts.shape[1], kernel, kernel_param, leaf_size,
+                  eta, switch_level, tol, fmt_mask, seed, 1 if tree == "2d" else 0, device, ctypes.byref(out)))
         return cls(out.value, device)
 
     @classmethod
@@ -345,20 +352,21 @@ class HMatrix:
 
 def optimal_switch_level(points, kernel: int = INV_R, kernel_param: float = 1.0, leaf_size: int = 128,
                          eta: float = 1.0, tol: float = 1e-6, fmt_mask: int = F64 | F32 | F16 | BF16,
-                         seed: int = 0, tree: str = "kd") -> tuple:
+                         seed: int = 0, tree: str = "kd", device: int = -1) -> tuple:
     """Algorithm 2 (hh_optimal_switch_level): the switching level with the
     largest storage gain over the H_s matrix.  Returns (ell*, L, {level: gain})
     with gain = S_s - S_h(level) in fp64 words for every level evaluated
-    (tree levels; tree "kd" or "2d")."""
+    (tree levels; tree "kd" or "2d").  device >= 0: the compressions of the
+    evaluated levels run on that GPU (hh_optimal_switch_level_dev)."""
     pts = np.ascontiguousarray(points.cpu().numpy() if isinstance(points, torch.Tensor) else points,
                                dtype=np.float64)
     if pts.ndim != 2:
         raise ValueError("points must be (n, dim)")
     ell, depth = ctypes.c_int(), ctypes.c_int()
     g = (ctypes.c_double * MAX_LEVELS)()
-    _check(_L().hh_optimal_switch_level(pts.ctypes.data, pts.shape[0], pts.shape[1], kernel, kernel_param,
-                                        leaf_size, eta, tol, fmt_mask, seed, 1 if tree == "2d" else 0,
-                                        ctypes.byref(ell), ctypes.byref(depth), g))
+    _check(_L().hh_optimal_switch_level_dev(pts.ctypes.data, pts.shape[0], pts.shape[1], kernel, kernel_param,
+                                            leaf_size, eta, tol, fmt_mask, seed, 1 if tree == "2d" else 0,
+                                            int(device), ctypes.byref(ell), ctypes.byref(depth), g))
     gains = {l: float(g[l]) for l in range(depth.value + 1) if not np.isnan(g[l])}
     return ell.value, depth.value, gains
 

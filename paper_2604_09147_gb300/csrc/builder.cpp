@@ -14,6 +14,7 @@
 #include <thread>
 #include <tuple>
 
+#include "construct.h"
 #include "hh_host.h"
 #include "linalg.h"
 
@@ -633,12 +634,42 @@ static void build_impl(const double* points, int64_t n, int dim, const BuildPara
     order.push_back(static_cast<int64_t>(b));
   }
   std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
-  parallel_for(static_cast<int64_t>(order.size()), p.threads, [&](int64_t t) {
-    const Pair& q = jobs[order[t]];
+  std::vector<int64_t> host_jobs = order;
+  if (p.device >= 0 && !order.empty()) {
+    // LRcompression on the GPU; blocks it leaves (rank capacity, failed
+    // factorization) are compressed here
+    std::vector<DeviceJob> dj(order.size());
+    for (size_t t = 0; t < order.size(); ++t) {
+      const Pair& q = jobs[order[t]];
+      rng(q.level, q.i, dj[t].r0, dj[t].m);
+      rng(q.level, q.j, dj[t].c0, dj[t].n);
+    }
+    std::vector<la::Mat> du, dv;
+    std::vector<std::vector<double>> ds;
+    std::vector<char> dok;
+    DeviceStats st;
+    compress_on_device(p.device, tp.data(), n, dim, p.kernel, p.kparam, p.tol, dj, du, dv, ds, dok, &st);
+    host_jobs.clear();
+    for (size_t t = 0; t < order.size(); ++t) {
+      if (!dok[t]) {
+        host_jobs.push_back(order[t]);
+        continue;
+      }
+      Compressed& c = *fresh[order[t]];
+      c.U = std::move(du[t]);
+      c.V = std::move(dv[t]);
+      c.s = std::move(ds[t]);
+    }
+    h.build_device = p.device;
+    h.build_fallback += static_cast<int64_t>(host_jobs.size());
+    h.build_device_seconds += st.seconds;
+  }
+  parallel_for(static_cast<int64_t>(host_jobs.size()), p.threads, [&](int64_t t) {
+    const Pair& q = jobs[host_jobs[t]];
     int64_t o1, m, o2, nn;
     rng(q.level, q.i, o1, m);
     rng(q.level, q.j, o2, nn);
-    compress_block(g, o1, m, o2, nn, p.tol, *fresh[order[t]]);
+    compress_block(g, o1, m, o2, nn, p.tol, *fresh[host_jobs[t]]);
   });
   for (int64_t b : order) {
     comp[b] = fresh[b];

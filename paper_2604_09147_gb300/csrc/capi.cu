@@ -1079,9 +1079,28 @@ int hh_build(const double* points, int64_t n, int dim, int kernel, double kernel
                      HH_TREE_KD, device, out);
 }
 
+static int build_common(const double* points, int64_t n, int dim, int kernel, double kernel_param, int leaf_size,
+                        double eta, int switch_level, double tol, uint32_t fmt_mask, uint64_t seed, int tree,
+                        int compress_device, int device, hh_handle* out);
+
 int hh_build_ex(const double* points, int64_t n, int dim, int kernel, double kernel_param, int leaf_size,
                 double eta, int switch_level, double tol, uint32_t fmt_mask, uint64_t seed, int tree, int device,
                 hh_handle* out) {
+  return build_common(points, n, dim, kernel, kernel_param, leaf_size, eta, switch_level, tol, fmt_mask, seed, tree,
+                      -1, device, out);
+}
+
+int hh_build_dev(const double* points, int64_t n, int dim, int kernel, double kernel_param, int leaf_size,
+                 double eta, int switch_level, double tol, uint32_t fmt_mask, uint64_t seed, int tree, int device,
+                 hh_handle* out) {
+  if (device < 0) return fail(HH_EINVAL, "hh_build_dev needs a device >= 0");
+  return build_common(points, n, dim, kernel, kernel_param, leaf_size, eta, switch_level, tol, fmt_mask, seed, tree,
+                      device, device, out);
+}
+
+static int build_common(const double* points, int64_t n, int dim, int kernel, double kernel_param, int leaf_size,
+                        double eta, int switch_level, double tol, uint32_t fmt_mask, uint64_t seed, int tree,
+                        int compress_device, int device, hh_handle* out) {
   if (!out) return fail(HH_EINVAL, "out is NULL");
   if (tree != HH_TREE_KD && tree != HH_TREE_2D) return fail(HH_EINVAL, "unknown tree kind");
   *out = nullptr;
@@ -1091,6 +1110,7 @@ int hh_build_ex(const double* points, int64_t n, int dim, int kernel, double ker
   if (!h) return fail(HH_ENOMEM, "out of host memory");
   try {
     hh::BuildParams p{kernel, kernel_param, leaf_size, eta, switch_level, tol, fmt_mask, seed, 0, tree};
+    p.device = compress_device;
     if (const char* t = std::getenv("HH_BUILD_THREADS")) p.threads = std::atoi(t);
     hh::build(points, n, dim, p, h->H);
   } catch (const std::domain_error& e) {
@@ -1102,6 +1122,10 @@ int hh_build_ex(const double* points, int64_t n, int dim, int kernel, double ker
   } catch (const std::bad_alloc&) {
     delete h;
     return fail(HH_ENOMEM, "out of host memory during build");
+  } catch (const std::runtime_error& e) {
+    delete h;
+    const bool dev = std::string(e.what()).rfind("device compression", 0) == 0;
+    return fail(dev ? HH_ECUDA : HH_EINVAL, e.what());
   } catch (const std::exception& e) {
     delete h;
     return fail(HH_EINVAL, e.what());
@@ -1112,10 +1136,19 @@ int hh_build_ex(const double* points, int64_t n, int dim, int kernel, double ker
 int hh_optimal_switch_level(const double* points, int64_t n, int dim, int kernel, double kernel_param,
                             int leaf_size, double eta, double tol, uint32_t fmt_mask, uint64_t seed, int tree,
                             int* ell_star, int* depth, double* gains) {
+  return hh_optimal_switch_level_dev(points, n, dim, kernel, kernel_param, leaf_size, eta, tol, fmt_mask, seed, tree,
+                                     -1, ell_star, depth, gains);
+}
+
+int hh_optimal_switch_level_dev(const double* points, int64_t n, int dim, int kernel, double kernel_param,
+                                int leaf_size, double eta, double tol, uint32_t fmt_mask, uint64_t seed, int tree,
+                                int device, int* ell_star, int* depth, double* gains) {
   if (!points || !ell_star) return fail(HH_EINVAL, "points or ell_star is NULL");
   if (tree != HH_TREE_KD && tree != HH_TREE_2D) return fail(HH_EINVAL, "unknown tree kind");
+  if (device < -1) return fail(HH_EINVAL, "device must be >= -1");
   try {
     hh::BuildParams p{kernel, kernel_param, leaf_size, eta, 0, tol, fmt_mask, seed, 0, tree};
+    p.device = device;
     if (const char* e = std::getenv("HH_BUILD_THREADS")) p.threads = std::atoi(e);
     std::vector<double> g;
     int L = 0;
@@ -1273,6 +1306,9 @@ int hh_info(hh_handle h, hh_info_t* o) {
     for (int p = 1; p <= 2; ++p) o->blocks_per_sm[2 * d + p - 1] = h->blocks_per_sm[d][p];
   for (int d = 0; d < 2; ++d) o->tc_panel_bytes[d] = h->tc[d].d_img ? h->tc[d].img_bytes : 0;
   o->tree_step = H.step;
+  o->build_device = H.build_device;
+  o->build_fallback = H.build_fallback;
+  o->build_device_seconds = H.build_device_seconds;
   return HH_OK;
 }
 

@@ -50,6 +50,9 @@ struct HostMatrix {
   uint32_t fmt_mask = 1;
   uint64_t seed = 0;
   double build_seconds = 0;
+  int32_t build_device = -1;       // GPU that compressed the blocks (-1: the host)
+  int64_t build_fallback = 0;      // blocks the host compressed in a device build
+  double build_device_seconds = 0; // wall time of the device compression
   std::vector<double> points;        // n x dim, user order
   std::vector<int32_t> perm;         // perm[p] = user index at tree position p
   std::vector<int64_t> node_off, node_size;
@@ -71,6 +74,7 @@ struct BuildParams {
   uint64_t seed;
   int threads;  // <= 0: hardware concurrency
   int tree;     // 0: binary KD bisection; 1: balanced 2^d-tree (ell in its levels)
+  int device = -1;  // >= 0: LRcompression of the admissible blocks on this GPU (construct.cu)
 };
 
 // Algorithm 1 + 5 + 3: throws std::runtime_error / std::invalid_argument.

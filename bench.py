@@ -477,6 +477,58 @@ def run_sharded(args):
     return 0
 
 
+def run_construct(args):
+    """Construction time: the adaptive workload's matrix (or the
+    differentiation workload's family at --construct-n points, exp(-r),
+    {fp64, fp32, bf16}) built with the compression on the GPU (hh_build_dev)
+    and, unless --no-host-build, by the host builder; reports both times, the
+    device compression's share, blocks left to the host, and the agreement of
+    ranks and formats."""
+    import torch
+    import paper_2604_09147_gb300 as P
+    from paper_2604_09147_gb300 import build as B
+    B.build()
+    dev = torch.cuda.current_device()
+    if args.construct_n:
+        c = W.CONFIGS["autograd_1m"]
+        pts = W.points(args.construct_n, 3, 1234 + c["id"])
+        fmts, ell, desc = c["fmts"], -1, (f"N={args.construct_n:,} points U[0,1]^3, exp(-r), leaf 128, eta 1, "
+                                           "switch level floor(L/2), tol 1e-6, adaptive {fp64,fp32,bf16}")
+    else:
+        c = W.CONFIGS["adaptive_65k"]
+        pts = W.config_points("adaptive_65k")
+        fmts, ell, desc = c["fmts"], c["ell"], WORKLOADS["adaptive_65k"]
+    args_b = (c["kernel"], c["kernel_param"], c["leaf"], c["eta"], ell, c["tol"], fmts)
+    t0 = time.time()
+    Hd = P.HMatrix.build(pts, *args_b, device=dev, construct_on_device=True)
+    t_dev = time.time() - t0
+    inf = Hd.info()
+    out = {"metric": "H_h construction seconds (compression on the GPU vs the host builder)",
+           "value": t_dev, "unit": "s", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": desc, "n": len(pts), "host_cores": os.cpu_count()},
+           "device_build_seconds": t_dev, "device_compression_seconds": inf["build_device_seconds"],
+           "fallback_blocks": inf["build_fallback"], "blocks": inf["n_lowrank"],
+           "blocks_per_fmt": inf["blocks_per_fmt"], "bytes_per_matvec": inf["bytes_per_matvec"]}
+    if not args.no_host_build:
+        t0 = time.time()
+        Hh = P.HMatrix.build(pts, *args_b, device=-1)
+        out["host_build_seconds"] = time.time() - t0
+        out["speedup"] = out["host_build_seconds"] / t_dev
+        with tempfile.TemporaryDirectory() as d:
+            from oracle import hhfile
+            Hh.save(os.path.join(d, "h.hhm"))
+            Hd.save(os.path.join(d, "d.hhm"))
+            gh, gd = hhfile.read(os.path.join(d, "h.hhm")), hhfile.read(os.path.join(d, "d.hhm"))
+        kh = {(b.level, b.i, b.j): (b.k, b.fmt) for b in gh.lowrank}
+        dk = np.array([abs(b.k - kh[(b.level, b.i, b.j)][0]) for b in gd.lowrank])
+        out["ranks_within_2"] = float(np.mean(dk <= 2))
+        out["max_rank_difference"] = int(dk.max()) if len(dk) else 0
+        out["formats_equal"] = float(np.mean([b.fmt == kh[(b.level, b.i, b.j)][1] for b in gd.lowrank]))
+        out["sum_rank_device_over_host"] = float(sum(b.k for b in gd.lowrank) / max(1, sum(b.k for b in gh.lowrank)))
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -890,9 +942,13 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="adaptive_65k")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU oracle baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["replicas", "sharded"], default="replicas",
+    ap.add_argument("--mode", choices=["replicas", "sharded", "construct"], default="replicas",
                     help="replicas: independent products per rank (weak scaling); sharded: the "
-                         "adaptive workload's block rows split over the ranks (strong scaling)")
+                         "adaptive workload's block rows split over the ranks (strong scaling); construct: "
+                         "construction time on the GPU against the host builder")
+    ap.add_argument("--construct-n", type=int, default=0,
+                    help="construct mode: points of the exp(-r) family (0: the adaptive 65k workload)")
+    ap.add_argument("--no-host-build", action="store_true", help="construct mode: skip the host builder")
     ap.add_argument("--no-low-bit", action="store_true",
                     help="skip the 16/8-bit single-column field of the default line")
     ap.add_argument("--low-bit-n", type=int, default=65536,
@@ -912,6 +968,8 @@ def main(argv=None):
         return run_reference(args)
     if args.mode == "sharded":
         return run_sharded(args)
+    if args.mode == "construct":
+        return run_construct(args)
     if args.workload in MANY_N:
         return run_many(args)
     if args.workload in LOWBIT_N:

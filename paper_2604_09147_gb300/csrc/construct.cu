@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <stdexcept>
@@ -426,34 +428,156 @@ __global__ void __launch_bounds__(256) chol_kernel(const CholJob* jobs) {
   }
 }
 
-// -------------------------------------------------- 3. one-sided Jacobi SVD
-// One CTA per job: the columns of T (k x k) are rotated pairwise until they
-// are mutually orthogonal (Hestenes), J accumulates the rotations (T_in J =
-// T_out).  A sweep visits every pair once in k' - 1 rounds of k' / 2
-// disjoint pairs (round-robin; k' = k rounded up to even, index k a dummy);
-// a warp takes a pair.  Converged when a sweep rotates no pair with
-// |t_p . t_q| > 1e-15 sqrt(|t_p|^2 |t_q|^2); at most kJacobiSweeps sweeps,
-// else *status = 3 (the block goes to the host).
+// ------------------------------------- 3. SVD of the core, QR-preconditioned
+// The left singular vectors of T (k x k) as the host builder takes them:
+// T P = Q1 R1 (Householder QR with column pivoting), R1^T = Q2 R2, so that
+// T = Q1 R2^T Q2^T P^T and the left singular vectors of T are Q1 times those
+// of X = R2^T, whose columns are nearly orthogonal; a one-sided (Hestenes)
+// Jacobi iteration on X's columns then converges in a few sweeps.
+
+// Householder QR of A (k x k, ld k) in place, one CTA per job: R in the upper
+// triangle, reflector tails below it (v_j[j] = 1), tau[j]; with pivot the
+// column of largest remaining norm goes first (norms kept in nrm, downdated
+// and recomputed when cancellation eats them).
+struct QrJob {
+  double* A;
+  double* tau;
+  double* nrm;  // k scratch
+  int k, pivot;
+  int* status;
+};
+
+__global__ void __launch_bounds__(512) qr_kernel(const QrJob* jobs) {
+  const QrJob jb = jobs[blockIdx.x];
+  const int k = jb.k;
+  if (k == 0 || *jb.status != 0) return;
+  double* A = jb.A;
+  __shared__ double redv[32];
+  __shared__ int64_t redi[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  auto col = [&](int c) { return A + static_cast<int64_t>(c) * k; };
+  if (jb.pivot) {
+    for (int c = warp; c < k; c += nw) {
+      const double* a = col(c);
+      double s = 0.0;
+      for (int e = lane; e < k; e += 32) s += a[e] * a[e];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) jb.nrm[c] = s;
+    }
+    __syncthreads();
+  }
+  for (int j = 0; j < k; ++j) {
+    if (jb.pivot) {
+      double a = -1.0, best;
+      int64_t at = j, p;
+      for (int c = j + threadIdx.x; c < k; c += blockDim.x)
+        if (jb.nrm[c] > a) {
+          a = jb.nrm[c];
+          at = c;
+        }
+      cta_argmax(a, at, redv, redi, best, p);
+      if (p != j) {
+        for (int e = threadIdx.x; e < k; e += blockDim.x) {
+          const double t = col(j)[e];
+          col(j)[e] = col(static_cast<int>(p))[e];
+          col(static_cast<int>(p))[e] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          const double t = jb.nrm[j];
+          jb.nrm[j] = jb.nrm[p];
+          jb.nrm[p] = t;
+        }
+      }
+    }
+    double* v = col(j);
+    double s = 0.0;
+    for (int e = j + 1 + threadIdx.x; e < k; e += blockDim.x) s += v[e] * v[e];
+    const double sigma = cta_sum(s, redv);
+    const double alpha = v[j];
+    double tau = 0.0, beta = alpha;
+    if (sigma > 0.0) {
+      beta = (alpha >= 0.0 ? -1.0 : 1.0) * sqrt(alpha * alpha + sigma);
+      tau = (beta - alpha) / beta;
+      const double sc = 1.0 / (alpha - beta);
+      for (int e = j + 1 + threadIdx.x; e < k; e += blockDim.x) v[e] *= sc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      v[j] = beta;
+      jb.tau[j] = tau;
+    }
+    // apply H_j to the columns c > j (a warp per column)
+    if (tau != 0.0)
+      for (int c = j + 1 + warp; c < k; c += nw) {
+        double* a = col(c);
+        double w = lane == 0 ? a[j] : 0.0;
+        for (int e = j + 1 + lane; e < k; e += 32) w += v[e] * a[e];
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        w *= tau;
+        if (lane == 0) a[j] -= w;
+        for (int e = j + 1 + lane; e < k; e += 32) a[e] -= w * v[e];
+      }
+    __syncthreads();
+    if (jb.pivot)
+      for (int c = j + 1 + warp; c < k; c += nw) {
+        const double* a = col(c);
+        const double r = a[j];
+        double nv = jb.nrm[c] - r * r;
+        if (!(nv > 1e-2 * jb.nrm[c])) {  // cancellation: recompute the trailing norm
+          double t = 0.0;
+          for (int e = j + 1 + lane; e < k; e += 32) t += a[e] * a[e];
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          nv = t;
+        }
+        __syncwarp();
+        if (lane == 0) jb.nrm[c] = nv;
+      }
+    __syncthreads();
+  }
+}
+
+// out (k x k) = R^T of the upper triangle of in (zero above the diagonal)
+__global__ void rt_kernel(const double* const* in, double* const* out, const int* ks, const int* const* status) {
+  const int k = ks[blockIdx.x];
+  if (k == 0 || *status[blockIdx.x] != 0) return;
+  const double* a = in[blockIdx.x];
+  double* b = out[blockIdx.x];
+  for (int64_t e = threadIdx.x; e < static_cast<int64_t>(k) * k; e += blockDim.x) {
+    const int i = static_cast<int>(e % k), c = static_cast<int>(e / k);
+    b[e] = i >= c ? a[c + static_cast<int64_t>(i) * k] : 0.0;
+  }
+}
+
+// One-sided Jacobi on the columns of X (k x k) until every pair is
+// orthogonal to 1e-15 relative (at most kJacobiSweeps sweeps, else *status =
+// 3); pairs in k' - 1 round-robin rounds of k' / 2 disjoint pairs per sweep
+// (k' = k rounded up to even, index k a dummy), a warp per pair.
 struct JacJob {
-  double* T;
-  double* J;
+  double* X;
   int k, pad;
   int* status;
+  int* sweeps;  // out: sweeps taken
 };
 
 __global__ void __launch_bounds__(512) jacobi_kernel(const JacJob* jobs) {
   const JacJob jb = jobs[blockIdx.x];
   const int k = jb.k;
   if (k == 0 || *jb.status != 0) return;
-  double* T = jb.T;
-  double* J = jb.J;
-  for (int64_t e = threadIdx.x; e < static_cast<int64_t>(k) * k; e += blockDim.x)
-    J[e] = (e % k == e / k) ? 1.0 : 0.0;
+  double* X = jb.X;
+  extern __shared__ double nrm[];  // squared column norms, updated by each rotation
   const int kk = (k + 1) & ~1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   __shared__ int rotated;
   int sweep = 0;
   for (; sweep < kJacobiSweeps; ++sweep) {
+    for (int c = warp; c < k; c += nw) {  // exact norms at the start of every sweep
+      const double* x = X + static_cast<int64_t>(c) * k;
+      double t = 0.0;
+      for (int e = lane; e < k; e += 32) t += x[e] * x[e];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) nrm[c] = t;
+    }
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int r = 0; r + 1 < kk; ++r) {
@@ -462,35 +586,40 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacJob* jobs) {
         const int pb = 1 + (kk - 2 - a + r) % (kk - 1);
         const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
         if (q >= k) continue;
-        double* tp = T + static_cast<int64_t>(p) * k;
-        double* tq = T + static_cast<int64_t>(q) * k;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int e = lane; e < k; e += 32) {
-          const double x = tp[e], y = tq[e];
-          al += x * x;
-          be += y * y;
-          ga += x * y;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        }
-        if (!(fabs(ga) > 1e-15 * sqrt(al * be)) || ga == 0.0) continue;
+        double* xp = X + static_cast<int64_t>(p) * k;
+        double* xq = X + static_cast<int64_t>(q) * k;
+        const double al = nrm[p], be = nrm[q];
+        if (al == 0.0 || be == 0.0) continue;
+        double ga = 0.0;
+        for (int e = lane; e < k; e += 32) ga += xp[e] * xq[e];
+        for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        if (!(fabs(ga) > 1e-15 * sqrt(al) * sqrt(be))) continue;
         const double zeta = (be - al) / (2.0 * ga);
         const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-        double* jp = J + static_cast<int64_t>(p) * k;
-        double* jq = J + static_cast<int64_t>(q) * k;
+        double np = 0.0, nq = 0.0;
         for (int e = lane; e < k; e += 32) {
-          const double x = tp[e], y = tq[e];
-          tp[e] = c * x - s * y;
-          tq[e] = s * x + c * y;
-          const double u = jp[e], v = jq[e];
-          jp[e] = c * u - s * v;
-          jq[e] = s * u + c * v;
+          const double x = xp[e], y = xq[e];
+          const double u = c * x - s * y, v = s * x + c * y;
+          xp[e] = u;
+          xq[e] = v;
+          np += u * u;
+          nq += v * v;
         }
-        if (lane == 0) rotated = 1;
+        // the rotation moves t gamma of squared norm from p to q; where that
+        // update would mostly cancel, take the norm just accumulated
+        const double up = al - t * ga, uq = be + t * ga;
+        if (!(up > 0.25 * al) || !(uq > 0.25 * be)) {
+          for (int o = 16; o > 0; o >>= 1) {
+            np += __shfl_xor_sync(0xffffffffu, np, o);
+            nq += __shfl_xor_sync(0xffffffffu, nq, o);
+          }
+        }
+        if (lane == 0) {
+          nrm[p] = up > 0.25 * al ? up : np;
+          nrm[q] = uq > 0.25 * be ? uq : nq;
+          rotated = 1;
+        }
       }
       __syncthreads();
     }
@@ -498,20 +627,20 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacJob* jobs) {
     __syncthreads();
     if (!any) break;
   }
-  if (sweep == kJacobiSweeps && threadIdx.x == 0) *jb.status = 3;
+  if (threadIdx.x == 0) {
+    *jb.sweeps = sweep;
+    if (sweep == kJacobiSweeps) *jb.status = 3;
+  }
 }
 
 // ------------------------------------------------------------ 4. truncation
-// One CTA per job: sigma_i = |T[:, i]| (T rotated), sorted descending
-// (ties by column); r = smallest rank whose Frobenius tail is <= teps times
-// the whole; W[:, t] = T[:, i_t] / sigma_t and Jr[:, t] = J[:, i_t] sigma_t
-// for t < r; sig[t] = sigma_t; *r_out = r.
+// One CTA per job: sigma_i = |X[:, i]| (X rotated), sorted descending (ties
+// by column); r = smallest rank whose Frobenius tail is <= teps times the
+// whole; W[:, t] = X[:, i_t] / sigma_t for t < r; sig[t] = sigma_t; *r_out = r.
 struct FinJob {
-  const double* T;
-  const double* J;
+  const double* X;
   double* W;
-  double* Jr;
-  double* sig;   // k (scratch for the unsorted norms at sig + k: 2k doubles)
+  double* sig;   // 2k doubles (the unsorted norms at sig + k)
   int* order;    // k
   int k, pad;
   int* r_out;
@@ -528,7 +657,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinJob* jobs, doubl
   double* nrm = jb.sig + k;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int c = warp; c < k; c += nw) {
-    const double* t = jb.T + static_cast<int64_t>(c) * k;
+    const double* t = jb.X + static_cast<int64_t>(c) * k;
     double s = 0.0;
     for (int e = lane; e < k; e += 32) s += t[e] * t[e];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -554,7 +683,6 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinJob* jobs, doubl
     } else {
       const double lim = teps * sqrt(total);
       double tail = 0.0;  // sum of sig[t..k)^2, from the end
-      r = k;
       for (int t = k - 1; t >= 0; --t) {
         const double nt = tail + jb.sig[t] * jb.sig[t];
         if (sqrt(nt) <= lim) {
@@ -572,10 +700,40 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinJob* jobs, doubl
   const int r = rr;
   for (int64_t e = threadIdx.x; e < static_cast<int64_t>(k) * r; e += blockDim.x) {
     const int row = static_cast<int>(e % k), t = static_cast<int>(e / k);
-    const int i = jb.order[t];
-    const double sg = jb.sig[t];
-    jb.W[row + static_cast<int64_t>(t) * k] = jb.T[row + static_cast<int64_t>(i) * k] / sg;
-    jb.Jr[row + static_cast<int64_t>(t) * k] = jb.J[row + static_cast<int64_t>(i) * k] * sg;
+    jb.W[row + static_cast<int64_t>(t) * k] = jb.X[row + static_cast<int64_t>(jb.order[t]) * k] / jb.sig[t];
+  }
+}
+
+// W (k x r, ld k) <- Q1 W with Q1 = H_0 ... H_{k-1} held as reflector tails
+// below the diagonal of F (k x k) and tau: the reflectors applied last to
+// first, a warp per column of W
+struct ApplyQJob {
+  const double* F;
+  const double* tau;
+  double* W;
+  int k, r;
+  int* status;
+};
+
+__global__ void __launch_bounds__(512) applyq_kernel(const ApplyQJob* jobs) {
+  const ApplyQJob jb = jobs[blockIdx.x];
+  const int k = jb.k, r = jb.r;
+  if (k == 0 || r == 0 || *jb.status != 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < r; c += nw) {
+    double* w = jb.W + static_cast<int64_t>(c) * k;
+    for (int j = k - 1; j >= 0; --j) {
+      const double tau = jb.tau[j];
+      if (tau == 0.0) continue;
+      const double* v = jb.F + static_cast<int64_t>(j) * k;
+      double d = lane == 0 ? w[j] : 0.0;
+      for (int e = j + 1 + lane; e < k; e += 32) d += v[e] * w[e];
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      d *= tau;
+      if (lane == 0) w[j] -= d;
+      for (int e = j + 1 + lane; e < k; e += 32) w[e] -= d * v[e];
+      __syncwarp();
+    }
   }
 }
 
@@ -638,13 +796,32 @@ GemmJob gj(const double* A, int64_t a_rs, int64_t a_cs, const double* B, int64_t
   return g;
 }
 
+// wall time per stage, printed to stderr when HH_CONSTRUCT_TIMING is set
+struct StageClock {
+  bool on = std::getenv("HH_CONSTRUCT_TIMING") != nullptr;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  double acc[8] = {};
+  void mark(int stage) {
+    if (!on) return;
+    cudaDeviceSynchronize();
+    const auto now = std::chrono::steady_clock::now();
+    acc[stage] += std::chrono::duration<double>(now - t).count();
+    t = now;
+  }
+  void report() const {
+    if (!on) return;
+    std::fprintf(stderr, "device compression stages (s): aca %.3f qr %.3f core %.3f jacobi %.3f final %.3f copy %.3f\n",
+                 acc[0], acc[1], acc[2], acc[3], acc[4], acc[5]);
+  }
+};
+
 // per job of a wave: where its buffers live (byte offsets)
 struct Slot {
   size_t u, v, used;                 // ACA: U (m x cap), V (n x cap), flags
   size_t q1u, q1v;                   // recompression: Q1 of U / V, later the final factors
   size_t gu, ru1, riu1, ru2, riu2;   // k x k each
   size_t gv, rv1, riv1, rv2, riv2;
-  size_t t, j, w, jr, sig, order, st;
+  size_t t, j, w, jr, sig, order, st, tau1, tau2;
 };
 
 }  // namespace
@@ -678,6 +855,7 @@ void compress_on_device(int device, const double* tp, int64_t n_pts, int dim, in
   });
   auto cap_of = [](const DeviceJob& j) { return static_cast<int>(std::min<int64_t>({j.m, j.n, kMaxRankCap})); };
   int64_t fallback = 0, waves = 0;
+  StageClock clk;
   size_t next = 0;
   while (next < nj) {
     // ---- a wave: as many jobs as fit the budget with their ACA workspace
@@ -715,6 +893,7 @@ void compress_on_device(int device, const double* tp, int64_t n_pts, int dim, in
     ck(cudaGetLastError(), "aca launch");
     ck(cudaDeviceSynchronize(), "aca");
     ck(cudaMemcpy(aj.data(), daj.p, nw * sizeof(AcaJob), cudaMemcpyDeviceToHost), "aca results");
+    clk.mark(0);
     // ---- recompression of the jobs ACA finished (buffers sized by rank)
     std::vector<size_t> live;  // wave positions
     std::vector<Slot> rs;
@@ -744,6 +923,8 @@ void compress_on_device(int device, const double* tp, int64_t n_pts, int dim, in
                       &sl.t, &sl.j, &sl.w, &sl.jr};
       for (size_t* p : kk) *p = take(8 * k * k);
       sl.sig = take(16 * k);
+      sl.tau1 = take(8 * k);
+      sl.tau2 = take(8 * k);
       sl.order = take(4 * k);
       sl.st = take(8);
       live.push_back(q);
@@ -815,6 +996,7 @@ void compress_on_device(int device, const double* tp, int64_t n_pts, int dim, in
         g.push_back(gj(D(rs[i].rv2), 1, k, D(rs[i].rv1), 1, k, D(rs[i].gv), k, k, k, k));
       }
       run_gemms(g);
+      clk.mark(1);
       g.clear();  // T = R_u R_v^T
       for (size_t i = 0; i < nl; ++i) {
         int m, n, k;
@@ -822,23 +1004,87 @@ void compress_on_device(int device, const double* tp, int64_t n_pts, int dim, in
         g.push_back(gj(D(rs[i].gu), 1, k, D(rs[i].gv), k, 1, D(rs[i].t), k, k, k, k));
       }
       run_gemms(g);
+      clk.mark(2);
+      // SVD of T, QR-preconditioned: F = copy of T, F P = Q1 R1; X = R1^T = Q2 R2;
+      // Jacobi on X2 = R2^T (in jr); W = Q1 (left singular vectors of X2)_r
+      for (size_t i = 0; i < nl; ++i) {
+        int m, n, k;
+        dims(i, m, n, k);
+        ck(cudaMemcpy(D(rs[i].j), D(rs[i].t), 8 * size_t(k) * k, cudaMemcpyDeviceToDevice), "copy T");
+      }
+      auto launch_qr = [&](bool first) {
+        std::vector<QrJob> qj;
+        for (size_t i = 0; i < nl; ++i) {
+          int m, n, k;
+          dims(i, m, n, k);
+          qj.push_back(QrJob{D(first ? rs[i].j : rs[i].w), D(first ? rs[i].tau1 : rs[i].tau2), D(rs[i].sig) + k, k,
+                             first ? 1 : 0, rb.as<int>(rs[i].st)});
+        }
+        DevBuf dq(qj.size() * sizeof(QrJob));
+        upload_vec(qj, dq);
+        qr_kernel<<<static_cast<unsigned>(nl), 512>>>(dq.as<QrJob>());
+        ck(cudaGetLastError(), "qr launch");
+        ck(cudaDeviceSynchronize(), "qr");
+      };
+      auto launch_rt = [&](bool first) {  // first: w = R1^T from j; else jr = R2^T from w
+        std::vector<const double*> in(nl);
+        std::vector<double*> out(nl);
+        std::vector<int> ks(nl);
+        std::vector<const int*> sts(nl);
+        for (size_t i = 0; i < nl; ++i) {
+          int m, n, k;
+          dims(i, m, n, k);
+          in[i] = D(first ? rs[i].j : rs[i].w);
+          out[i] = D(first ? rs[i].w : rs[i].jr);
+          ks[i] = k;
+          sts[i] = rb.as<int>(rs[i].st);
+        }
+        DevBuf di(nl * sizeof(void*)), dout(nl * sizeof(void*)), dk(nl * sizeof(int)), ds(nl * sizeof(void*));
+        upload_vec(in, di);
+        upload_vec(out, dout);
+        upload_vec(ks, dk);
+        upload_vec(sts, ds);
+        rt_kernel<<<static_cast<unsigned>(nl), 256>>>(di.as<const double*>(), dout.as<double*>(), dk.as<int>(),
+                                                      ds.as<const int*>());
+        ck(cudaGetLastError(), "transpose launch");
+        ck(cudaDeviceSynchronize(), "transpose");
+      };
+      launch_qr(true);
+      launch_rt(true);
+      launch_qr(false);
+      launch_rt(false);
       std::vector<JacJob> jj;
       std::vector<FinJob> fj;
-      DevBuf rout(nl * sizeof(int));
+      DevBuf rout(nl * sizeof(int)), dsw(nl * sizeof(int));
       for (size_t i = 0; i < nl; ++i) {
         int m, n, k;
         dims(i, m, n, k);
         int* st = rb.as<int>(rs[i].st);
-        jj.push_back(JacJob{D(rs[i].t), D(rs[i].j), k, 0, st});
-        fj.push_back(FinJob{D(rs[i].t), D(rs[i].j), D(rs[i].w), D(rs[i].jr), D(rs[i].sig), rb.as<int>(rs[i].order),
-                            k, 0, rout.as<int>(i * sizeof(int)), st});
+        jj.push_back(JacJob{D(rs[i].jr), k, 0, st, dsw.as<int>(i * sizeof(int))});
+        fj.push_back(FinJob{D(rs[i].jr), D(rs[i].w), D(rs[i].sig), rb.as<int>(rs[i].order), k, 0,
+                            rout.as<int>(i * sizeof(int)), st});
       }
       DevBuf djj(jj.size() * sizeof(JacJob)), dfj(fj.size() * sizeof(FinJob));
       upload_vec(jj, djj);
       upload_vec(fj, dfj);
-      jacobi_kernel<<<static_cast<unsigned>(nl), 512>>>(djj.as<JacJob>());
+      jacobi_kernel<<<static_cast<unsigned>(nl), 512, kMaxRankCap * 8>>>(djj.as<JacJob>());
       ck(cudaGetLastError(), "jacobi launch");
       ck(cudaDeviceSynchronize(), "jacobi");
+      clk.mark(3);
+      if (clk.on) {
+        std::vector<int> sw(nl);
+        ck(cudaMemcpy(sw.data(), dsw.p, nl * sizeof(int), cudaMemcpyDeviceToHost), "sweeps");
+        int kmx = 0, smx = 0;
+        double sm = 0.0;
+        for (size_t i = 0; i < nl; ++i) {
+          int m, n, k;
+          dims(i, m, n, k);
+          kmx = std::max(kmx, k);
+          smx = std::max(smx, sw[i]);
+          sm += sw[i];
+        }
+        std::fprintf(stderr, "jacobi: %zu cores, largest k %d, sweeps max %d mean %.1f\n", nl, kmx, smx, sm / nl);
+      }
       finalize_kernel<<<static_cast<unsigned>(nl), 256>>>(dfj.as<FinJob>(), (1.0 - kAcaShare) * eps);
       ck(cudaGetLastError(), "truncation launch");
       ck(cudaDeviceSynchronize(), "truncation");
@@ -846,7 +1092,29 @@ void compress_on_device(int device, const double* tp, int64_t n_pts, int dim, in
       ck(cudaMemcpy(rr.data(), rout.p, nl * sizeof(int), cudaMemcpyDeviceToHost), "ranks");
       for (size_t i = 0; i < nl; ++i)
         ck(cudaMemcpy(&stv[i], rb.as<int>(rs[i].st), sizeof(int), cudaMemcpyDeviceToHost), "status");
-      g.clear();  // U_b = Q_u W_r, V_b = Q_v J_r Sigma_r (into the Q1 buffers)
+      {  // W <- Q1 W
+        std::vector<ApplyQJob> aq;
+        for (size_t i = 0; i < nl; ++i) {
+          int m, n, k;
+          dims(i, m, n, k);
+          aq.push_back(ApplyQJob{D(rs[i].j), D(rs[i].tau1), D(rs[i].w), k, stv[i] == 0 ? rr[i] : 0,
+                                 rb.as<int>(rs[i].st)});
+        }
+        DevBuf da(aq.size() * sizeof(ApplyQJob));
+        upload_vec(aq, da);
+        applyq_kernel<<<static_cast<unsigned>(nl), 512>>>(da.as<ApplyQJob>());
+        ck(cudaGetLastError(), "apply Q launch");
+        ck(cudaDeviceSynchronize(), "apply Q");
+      }
+      g.clear();  // Y = T^T W (= Z_r Sigma_r) into jr
+      for (size_t i = 0; i < nl; ++i) {
+        int m, n, k;
+        dims(i, m, n, k);
+        if (stv[i] != 0 || rr[i] == 0) continue;
+        g.push_back(gj(D(rs[i].t), k, 1, D(rs[i].w), 1, k, D(rs[i].jr), k, k, rr[i], k));
+      }
+      run_gemms(g);
+      g.clear();  // U_b = Q_u W_r, V_b = Q_v Y (into the Q1 buffers)
       for (size_t i = 0; i < nl; ++i) {
         int m, n, k;
         dims(i, m, n, k);
@@ -855,6 +1123,7 @@ void compress_on_device(int device, const double* tp, int64_t n_pts, int dim, in
         g.push_back(gj(Vq(i), 1, n, D(rs[i].jr), 1, k, D(rs[i].q1v), n, n, rr[i], k));
       }
       run_gemms(g);
+      clk.mark(4);
       for (size_t i = 0; i < nl; ++i) {
         const size_t job = wave[live[i]];
         const DeviceJob& J = jobs[job];
@@ -873,8 +1142,10 @@ void compress_on_device(int device, const double* tp, int64_t n_pts, int dim, in
         }
         ok[job] = 1;
       }
+      clk.mark(5);
     }
   }
+  clk.report();
   if (stats) {
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     stats->fallback = fallback;

@@ -123,6 +123,9 @@ typedef struct {
   int32_t pad2_;
   int64_t build_fallback;         /* blocks of a device build that the host compressed        */
   double build_device_seconds;    /* wall time of the device compression                       */
+  int32_t stream_depth[4];        /* pipeline depth (stages per CTA) of one-column streaming
+                                     launches per [direction][phase] (hh_autotune; default 4)  */
+  int64_t item_bytes;             /* factor bytes of a streaming phase-1 item (hh_autotune)     */
 } hh_info_t;
 
 /*
@@ -279,9 +282,11 @@ int hh_perm(hh_handle h, int32_t* perm);
  * accumulated in fp32 (the input split into fp32 leading and trailing
  * halves); fp64 low-rank blocks and the dense blocks are computed as pairs
  * of fp32 halves (about 2^-48 relative, the fp64 path's 1e-12 parity); the
- * output is accumulated in fp64.  With nrhs <= 31 the columns go through the
- * streaming passes in chunks of up to 4.  With nrhs >= 32 (HH_TC_MIN_NRHS in
- * the environment overrides; 0 disables) the columns go in chunks of up to
+ * output is accumulated in fp64.  With nrhs <= 4 the columns go through the
+ * streaming passes (one launch sequence for 1, 2 or 4 columns).  With
+ * nrhs >= 5 (measured crossover: the many-column sequence costs about the
+ * same for 5 to 32 columns as the streaming passes for 5; HH_TC_MIN_NRHS in
+ * the environment overrides, 0 disables) the columns go in chunks of up to
  * 128 through one pass over the blocks: the fp32, fp16, bf16 and e4m3 blocks
  * whose clusters start at multiples of 16 on the tensor cores (exact bf16
  * slices of the factors and of the fp32 input; products kept down to about

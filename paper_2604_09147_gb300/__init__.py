@@ -55,7 +55,8 @@ class _Info(ctypes.Structure):
         ("tuned", ctypes.c_int32), ("split_positions", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32 * 4),
         ("tc_panel_bytes", ctypes.c_int64 * 2), ("tree_step", ctypes.c_int32), ("pad_", ctypes.c_int32),
         ("build_device", ctypes.c_int32), ("pad2_", ctypes.c_int32), ("build_fallback", ctypes.c_int64),
-        ("build_device_seconds", ctypes.c_double),
+        ("build_device_seconds", ctypes.c_double), ("stream_depth", ctypes.c_int32 * 4),
+        ("item_bytes", ctypes.c_int64),
     ]
 
 
@@ -253,6 +254,7 @@ class HMatrix:
         d["csp"] = [int(s.csp[i]) for i in range(s.L + 1)]
         d["blocks_per_sm"] = [int(v) for v in s.blocks_per_sm]
         d["tc_panel_bytes"] = [int(v) for v in s.tc_panel_bytes]
+        d["stream_depth"] = [int(v) for v in s.stream_depth]
         return d
 
     def autotune(self, nrhs_many: int = 0) -> dict:
@@ -260,7 +262,8 @@ class HMatrix:
         (streaming CTAs per SM; with nrhs_many > 0 the many-column item split)."""
         _check(_L().hh_autotune(self._h, int(nrhs_many)))
         i = self.info()
-        return {"blocks_per_sm": i["blocks_per_sm"], "split_positions": i["split_positions"]}
+        return {"blocks_per_sm": i["blocks_per_sm"], "stream_depth": i["stream_depth"],
+                "item_bytes": i["item_bytes"], "split_positions": i["split_positions"]}
 
     def perm(self) -> np.ndarray:
         p = np.empty(self.n, dtype=np.int32)

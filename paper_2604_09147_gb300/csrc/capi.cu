@@ -48,6 +48,7 @@ struct StreamSet {
   unsigned fset = hh::dev::kSetAll;
   unsigned present = 0;  // formats of the low-rank blocks in the set (bit f)
   int grid[3][5] = {};   // [phase][nr]
+  int depth[3] = {4, 4, 4};  // [phase] pipeline depth of one-column launches (hh_autotune's choice)
   // host copies (batches concatenate them)
   std::vector<hh::dev::StreamDesc> h_desc[2];
   std::vector<Item> h_items[2];
@@ -111,6 +112,7 @@ struct hh_matrix {
   std::vector<int64_t> doff;   // dense block offsets in d_dense_pad
   std::vector<int32_t> dexp;   // and their scale exponents
   int split_len = hh::dev::kTcSplitPositions;  // positions of a many-column phase-1 item
+  int64_t item_bytes = int64_t(64) << 10;      // factor bytes of a streaming phase-1 item (hh_autotune)
   int blocks_per_sm[2][3] = {};                // streaming grid per [direction][phase] (0: occupancy)
   int tuned = 0;
 };
@@ -217,11 +219,12 @@ void build_stream_set(hh_matrix* h, int dir, const std::vector<int64_t>& toff, c
   };
   std::vector<Costed> items[2];
   // phase-1 items: whole groups of cols1 columns, as many groups (at most 8)
-  // as make about 64 KB of factor bytes, so that short columns do not pay the
-  // per-item scheduling latency every stage
+  // as make about h->item_bytes of factor bytes (64 KB unless hh_autotune
+  // chose otherwise), so that short columns do not pay the per-item
+  // scheduling latency every stage
   auto add_cols = [&](int phase, int di, int64_t rows, int64_t cols, int sz) {
     const int64_t group_bytes = std::max<int64_t>(1, int64_t(cols1) * rows * sz);
-    const int64_t groups = std::max<int64_t>(1, std::min<int64_t>(8, ((int64_t(64) << 10) + group_bytes - 1) / group_bytes));
+    const int64_t groups = std::max<int64_t>(1, std::min<int64_t>(8, (h->item_bytes + group_bytes - 1) / group_bytes));
     const int64_t per = cols1 * groups;
     for (int64_t j = 0; j < cols; j += per) {
       int64_t hi = std::min<int64_t>(cols, j + per);
@@ -307,7 +310,8 @@ void build_stream_set(hh_matrix* h, int dir, const std::vector<int64_t>& toff, c
   out.present = present;
   out.fset = hh::dev::pass_set_for(present);
   for (int phase = 1; phase <= 2; ++phase)
-    for (int nr : {1, 2, 4}) out.grid[phase][nr] = h->sms * hh::dev::stream_blocks_per_sm(phase, out.fset, nr);
+    for (int nr : {1, 2, 4})
+      out.grid[phase][nr] = h->sms * hh::dev::stream_blocks_per_sm(phase, out.fset, nr, nr == 1 ? out.depth[phase] : 4);
 }
 
 // Formats the tensor-core path takes and the most ranks of one piece.
@@ -674,6 +678,9 @@ int noalloc_scratch(int device, void** ptr) {
   return HH_OK;
 }
 
+// streaming grid of one direction and phase (defined below)
+void set_stream_grid(hh_matrix* h, int dir, int phase, int c, int depth = 4);
+
 void upload_matrix(hh_matrix* h, int device) {
   const hh::HostMatrix& H = h->H;
   ck(cudaSetDevice(device), "cudaSetDevice");
@@ -734,6 +741,13 @@ void upload_matrix(hh_matrix* h, int device) {
     const int v = std::atoi(e);
     if (v >= 16 && v % 16 == 0) h->split_len = v;
   }
+  // the streaming launch shape hh_autotune would choose, fixed from the
+  // environment (for profiling runs): HH_STREAM_ITEM_BYTES (phase-1 item
+  // size), HH_STREAM_DEPTH (3, 4 or 6 stages) and HH_STREAM_CTAS (per SM)
+  if (const char* e = std::getenv("HH_STREAM_ITEM_BYTES")) {
+    const long long v = std::atoll(e);
+    if (v >= 1024) h->item_bytes = v;
+  }
   std::vector<char> all(H.lr.size(), 1), rest(H.lr.size(), 0);
   for (size_t b = 0; b < H.lr.size(); ++b) rest[b] = H.lr[b].fmt == hh::F64;
   for (int dir = 0; dir < 2; ++dir) {
@@ -741,6 +755,15 @@ void upload_matrix(hh_matrix* h, int device) {
     build_stream_set(h, dir, toff, doff, dexp, rest, false, h->ss_rest[dir]);
     build_tc_set(h, dir, h->tc[dir]);
     build_mr_set(h, dir, doff, dexp, h->mr[dir]);
+  }
+  {
+    const char* ed = std::getenv("HH_STREAM_DEPTH");
+    const char* ec = std::getenv("HH_STREAM_CTAS");
+    if (ed || ec) {
+      const int depth = ed ? std::atoi(ed) : 4, ctas = ec ? std::atoi(ec) : 16;
+      for (int dir = 0; dir < 2; ++dir)
+        for (int phase = 1; phase <= 2; ++phase) set_stream_grid(h, dir, phase, std::max(1, ctas), depth);
+    }
   }
   ck(cudaMalloc(&h->d_status, 256), "cudaMalloc");
   ck(cudaMemset(h->d_status, 0, 256), "cudaMemset");
@@ -806,18 +829,20 @@ cudaError_t run_stream(hh_matrix* h, const StreamSet& set, const double* in, int
     s.counter = w.counters + (phase - 1);
     if (s.n_items == 0) continue;
     int grid = std::max(1, std::min(set.grid[phase][nr], s.n_items));
-    e = hh::dev::launch_stream(phase, set.fset, s, grid, st, p1 && !ev);
+    e = hh::dev::launch_stream(phase, set.fset, s, grid, st, p1 && !ev, set.depth[phase]);
     p1 = phase == 1;
   }
   return e;
 }
 
 // Right-hand-side count from which hh_matvec / hh_matvec_T use the tensor
-// cores (HH_TC_MIN_NRHS overrides; 0 disables the path).
+// cores (HH_TC_MIN_NRHS overrides; 0 disables the path): the many-column
+// sequence costs about the same for 5 to 32 columns, the streaming passes
+// one pass per 4 columns.
 int tc_min_nrhs() {
   static const int v = [] {
     const char* s = std::getenv("HH_TC_MIN_NRHS");
-    return s ? std::atoi(s) : 32;
+    return s ? std::atoi(s) : 5;
   }();
   return v;
 }
@@ -1038,13 +1063,44 @@ void rebuild_many(hh_matrix* h) {
 
 // Streaming grid of one direction and phase: c CTAs per SM (clamped to the
 // occupancy of each column count).
-void set_stream_grid(hh_matrix* h, int dir, int phase, int c) {
+void set_stream_grid(hh_matrix* h, int dir, int phase, int c, int depth) {
   StreamSet& ss = h->ss[dir];
+  ss.depth[phase] = depth;
   for (int nr : {1, 2, 4}) {
-    const int occ = hh::dev::stream_blocks_per_sm(phase, ss.fset, nr);
+    const int occ = hh::dev::stream_blocks_per_sm(phase, ss.fset, nr, nr == 1 ? depth : 4);
     ss.grid[phase][nr] = h->sms * std::max(1, std::min(c, occ));
   }
   h->blocks_per_sm[dir][phase] = c;
+}
+
+// the streaming tables of both directions again (after h->item_bytes changed);
+// the launch choices of the previous tables are kept
+void rebuild_stream_sets(hh_matrix* h) {
+  const hh::HostMatrix& H = h->H;
+  std::vector<int64_t> toff(H.lr.size(), 0);
+  int64_t t32 = 0, t64 = 0;
+  for (size_t b = 0; b < H.lr.size(); ++b) {
+    int64_t& tot = H.lr[b].fmt == hh::F64 ? t64 : t32;
+    toff[b] = tot * hh::dev::kMaxNR;
+    tot += H.lr[b].k;
+  }
+  std::vector<char> all(H.lr.size(), 1), rest(H.lr.size(), 0);
+  for (size_t b = 0; b < H.lr.size(); ++b) rest[b] = H.lr[b].fmt == hh::F64;
+  for (int dir = 0; dir < 2; ++dir) {
+    StreamSet old = h->ss[dir];
+    for (int p = 0; p < 2; ++p) {
+      cudaFree(h->ss[dir].d_desc[p]);
+      cudaFree(h->ss[dir].d_items[p]);
+      cudaFree(h->ss_rest[dir].d_desc[p]);
+      cudaFree(h->ss_rest[dir].d_items[p]);
+    }
+    h->ss[dir] = StreamSet();
+    h->ss_rest[dir] = StreamSet();
+    build_stream_set(h, dir, toff, h->doff, h->dexp, all, true, h->ss[dir]);
+    build_stream_set(h, dir, toff, h->doff, h->dexp, rest, false, h->ss_rest[dir]);
+    for (int phase = 1; phase <= 2; ++phase)
+      if (h->blocks_per_sm[dir][phase] > 0) set_stream_grid(h, dir, phase, h->blocks_per_sm[dir][phase], old.depth[phase]);
+  }
 }
 
 hh_matrix* make_handle() { return new (std::nothrow) hh_matrix(); }
@@ -1309,6 +1365,9 @@ int hh_info(hh_handle h, hh_info_t* o) {
   o->build_device = H.build_device;
   o->build_fallback = H.build_fallback;
   o->build_device_seconds = H.build_device_seconds;
+  for (int d = 0; d < 2; ++d)
+    for (int p = 1; p <= 2; ++p) o->stream_depth[2 * d + p - 1] = h->ss[d].depth[p];
+  o->item_bytes = h->item_bytes;
   return HH_OK;
 }
 
@@ -1472,25 +1531,66 @@ int hh_autotune(hh_handle h, int nrhs_many) {
   if (rc == HH_OK && cudaMemsetAsync(x, 0x3f, sizeof(double) * n * cols, st) != cudaSuccess)  // entries ~4.8e-4
     rc = fail(HH_ECUDA, "cudaMemsetAsync failed");
   float ms[8];
-  // streaming passes: CTAs per SM for each direction and phase, one column
+  // streaming passes, one column: (1) the factor bytes of a phase-1 item
+  // (the work decomposition; both directions' whole products timed);
+  // (2) per direction and phase, the pipeline depth and the CTAs per SM
+  auto product_ms = [&](int reps) {
+    float t = 1e30f;
+    for (int rep = 0; rep < reps && rc == HH_OK; ++rep) {
+      float sum = 0.f;
+      for (int dir = 0; dir < 2 && rc == HH_OK; ++dir) {
+        rc = timed_product(h, dir, x, y, 1, n, n, st, ms, 5, false);
+        for (int q = 0; q < 4; ++q) sum += ms[q];
+      }
+      if (rep >= 1) t = std::min(t, sum);
+    }
+    return t;
+  };
+  if (rc == HH_OK) {
+    int64_t best_b = h->item_bytes;
+    float best = 1e30f;
+    for (int64_t ib : {int64_t(16) << 10, int64_t(64) << 10, int64_t(256) << 10}) {
+      h->item_bytes = ib;
+      try {
+        rebuild_stream_sets(h);
+      } catch (const std::exception& e) {
+        rc = fail(HH_ECUDA, e.what());
+        break;
+      }
+      const float t = product_ms(4);
+      if (rc == HH_OK && t < best) {
+        best = t;
+        best_b = ib;
+      }
+    }
+    h->item_bytes = best_b;
+    try {
+      rebuild_stream_sets(h);
+    } catch (const std::exception& e) {
+      if (rc == HH_OK) rc = fail(HH_ECUDA, e.what());
+    }
+  }
   for (int dir = 0; dir < 2 && rc == HH_OK; ++dir)
     for (int phase = 1; phase <= 2 && rc == HH_OK; ++phase) {
-      const int occ = hh::dev::stream_blocks_per_sm(phase, h->ss[dir].fset, 1);
-      int best_c = occ;
+      int best_c = 0, best_d = 4;
       float best = 1e30f;
-      for (int c = 1; c <= occ && rc == HH_OK; ++c) {
-        set_stream_grid(h, dir, phase, c);
-        float t = 1e30f;
-        for (int rep = 0; rep < 6 && rc == HH_OK; ++rep) {
-          rc = timed_product(h, dir, x, y, 1, n, n, st, ms, 5, false);
-          if (rep >= 1) t = std::min(t, ms[phase]);
-        }
-        if (t < best) {
-          best = t;
-          best_c = c;
+      for (int depth : {4, 3, 6}) {
+        const int occ = hh::dev::stream_blocks_per_sm(phase, h->ss[dir].fset, 1, depth);
+        for (int c = 1; c <= occ && rc == HH_OK; ++c) {
+          set_stream_grid(h, dir, phase, c, depth);
+          float t = 1e30f;
+          for (int rep = 0; rep < 6 && rc == HH_OK; ++rep) {
+            rc = timed_product(h, dir, x, y, 1, n, n, st, ms, 5, false);
+            if (rep >= 1) t = std::min(t, ms[phase]);
+          }
+          if (t < best) {
+            best = t;
+            best_c = c;
+            best_d = depth;
+          }
         }
       }
-      set_stream_grid(h, dir, phase, best_c);
+      set_stream_grid(h, dir, phase, best_c > 0 ? best_c : 1, best_d);
     }
   // many columns: the position split of the phase-1 items
   if (rc == HH_OK && nrhs_many > 0) {

@@ -53,9 +53,11 @@ cudaError_t launch_prep(const double* in, int64_t ld, int nr, const int32_t* per
                         int* counters = nullptr);
 // pdl (phase 2 only, and only directly after a phase-1 launch of the same
 // sequence): programmatic dependent launch, see stream.cu
+// nst: pipeline depth (stages per CTA) of one-column launches, 3, 4 or 6
+// (other values: 4); launches of 2 or 4 columns use 4
 cudaError_t launch_stream(int phase, unsigned fset, const StreamArgs& a, int grid, cudaStream_t st,
-                          bool pdl = false);
-int stream_blocks_per_sm(int phase, unsigned fset, int nr);
+                          bool pdl = false, int nst = 4);
+int stream_blocks_per_sm(int phase, unsigned fset, int nr, int nst = 4);
 int stream_rows_per_item(int fmt);   // phase-2 rows per item (1 KB of factor data per column)
 int stream_cols_per_item();          // phase-1 columns per item
 // kernel variants by the set of factor formats they contain (bit f = fmt f)

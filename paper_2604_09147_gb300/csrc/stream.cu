@@ -43,7 +43,7 @@ namespace {
 
 constexpr int kConsumers = 4;                       // consumer warps per CTA
 constexpr int kStreamThreads = 32 * (kConsumers + 1);
-constexpr int kStages = 4;
+constexpr int kStages = 4;                          // default pipeline depth (stages per CTA)
 constexpr int kStageBytes = 16384;
 constexpr int kP1Cols = 8;                          // columns per phase-1 item
 constexpr int kP1ColBytes = kStageBytes / kP1Cols;  // 2 KB per column and stage
@@ -70,14 +70,14 @@ struct XArea {
   static constexpr int bytes = (FSET & 28u) ? 8192 : 2048;
 };
 
-template <int PHASE, unsigned FSET>
+template <int PHASE, unsigned FSET, int NST>
 struct __align__(128) Smem {
   static constexpr int kX = XArea<FSET>::bytes;
-  uint8_t data[kStages][kStageBytes];
-  uint8_t x[PHASE == 1 ? kStages : 1][PHASE == 1 ? kX : 16];
-  Meta meta[kStages];
-  unsigned long long full[kStages];
-  unsigned long long empty[kStages];
+  uint8_t data[NST][kStageBytes];
+  uint8_t x[PHASE == 1 ? NST : 1][PHASE == 1 ? kX : 16];
+  Meta meta[NST];
+  unsigned long long full[NST];
+  unsigned long long empty[NST];
 };
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -225,8 +225,8 @@ __device__ __forceinline__ double f2d_scaled(float v, int e) {
 // Walks the item list (dynamic schedule) and fills stages.  Phase 1 stages
 // carry up to kP1Cols column segments of RC rows; phase 2 stages up to
 // kP2Cols column segments of the item's rows.
-template <int PHASE, unsigned FSET>
-__device__ void produce(Smem<PHASE, FSET>& sm, const StreamArgs& a) {
+template <int PHASE, unsigned FSET, int NST>
+__device__ void produce(Smem<PHASE, FSET, NST>& sm, const StreamArgs& a) {
   constexpr int kXBytes = XArea<FSET>::bytes;
   const int lane = threadIdx.x & 31;
   const uint64_t pol = evict_first_policy();
@@ -234,7 +234,7 @@ __device__ void produce(Smem<PHASE, FSET>& sm, const StreamArgs& a) {
   uint32_t par = 1;  // empty barriers: the first round passes immediately
   bool ok = true;
   int issued_mask = 0;  // stages whose copies may be in flight after a timeout
-  uint32_t issued_par[kStages] = {};  // full-barrier phase parity of the last issue per stage
+  uint32_t issued_par[NST] = {};  // full-barrier phase parity of the last issue per stage
   // the next item's number is taken from the counter while the current
   // item's stages are issued, so that the atomic's round trip overlaps them
   int next = 0;
@@ -333,7 +333,7 @@ __device__ void produce(Smem<PHASE, FSET>& sm, const StreamArgs& a) {
       }
       issued_mask |= 1 << stage;
       issued_par[stage] = par ^ 1u;
-      if (++stage == kStages) {
+      if (++stage == NST) {
         stage = 0;
         par ^= 1u;
       }
@@ -356,7 +356,7 @@ __device__ void produce(Smem<PHASE, FSET>& sm, const StreamArgs& a) {
     // consumers may be gone: let the copies issued into this CTA's shared
     // memory finish (bounded) before the CTA can exit
     const long long t0 = clock64();
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < NST; ++s) {
       if (!(issued_mask & (1 << s))) continue;
       while (!mbar_try(&sm.full[s], issued_par[s])) {
         if (clock64() - t0 > kWaitCycles) break;
@@ -613,8 +613,8 @@ __device__ __forceinline__ void p2_flush(const Meta& m, const StreamArgs& a, int
   }
 }
 
-template <int PHASE, int NR, unsigned FSET>
-__device__ void consume(Smem<PHASE, FSET>& sm, const StreamArgs& a) {
+template <int PHASE, int NR, unsigned FSET, int NST>
+__device__ void consume(Smem<PHASE, FSET, NST>& sm, const StreamArgs& a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wc = warp - 1;           // consumer warp index
   const int ct = threadIdx.x - 32;   // consumer thread index (0..127)
@@ -681,19 +681,19 @@ __device__ void consume(Smem<PHASE, FSET>& sm, const StreamArgs& a) {
       if constexpr (PHASE == 1) p1_flush<NR>(m, a, wc, lane, acc1, acd1);
       else p2_flush<NR>(m, a, ct, acc2, acd2);
     }
-    if (++stage == kStages) {
+    if (++stage == NST) {
       stage = 0;
       par ^= 1u;
     }
   }
 }
 
-template <int PHASE, int NR, unsigned FSET>
+template <int PHASE, int NR, unsigned FSET, int NST>
 __global__ void __launch_bounds__(kStreamThreads) stream_kernel(StreamArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
-  Smem<PHASE, FSET>& sm = *reinterpret_cast<Smem<PHASE, FSET>*>(smem_raw);
+  Smem<PHASE, FSET, NST>& sm = *reinterpret_cast<Smem<PHASE, FSET, NST>*>(smem_raw);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(&sm.full[s], 1);
       mbar_init(&sm.empty[s], kConsumers);
     }
@@ -701,8 +701,8 @@ __global__ void __launch_bounds__(kStreamThreads) stream_kernel(StreamArgs a) {
   }
   __syncthreads();
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  if (threadIdx.x < 32) produce<PHASE, FSET>(sm, a);
-  else consume<PHASE, NR, FSET>(sm, a);
+  if (threadIdx.x < 32) produce<PHASE, FSET, NST>(sm, a);
+  else consume<PHASE, NR, FSET, NST>(sm, a);
 }
 
 // launch with (pdl) or without programmatic stream serialization
@@ -721,63 +721,75 @@ cudaError_t launch_k(Kern k, int grid, size_t smem, cudaStream_t st, bool pdl, c
   return cudaLaunchKernelEx(&cfg, k, a);
 }
 
-template <int PHASE, unsigned FSET>
-cudaError_t launch_stream_t(const StreamArgs& a, int grid, cudaStream_t st, bool pdl) {
-  const size_t smem = sizeof(Smem<PHASE, FSET>);
-  cudaError_t e = cudaSuccess;
-  switch (a.nr) {
-    case 1:
-      e = cudaFuncSetAttribute(stream_kernel<PHASE, 1, FSET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) e = launch_k(stream_kernel<PHASE, 1, FSET>, grid, smem, st, pdl, a);
-      break;
-    case 2:
-      e = cudaFuncSetAttribute(stream_kernel<PHASE, 2, FSET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) e = launch_k(stream_kernel<PHASE, 2, FSET>, grid, smem, st, pdl, a);
-      break;
-    case 4:
-      e = cudaFuncSetAttribute(stream_kernel<PHASE, 4, FSET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) e = launch_k(stream_kernel<PHASE, 4, FSET>, grid, smem, st, pdl, a);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
+template <int PHASE, int NR, unsigned FSET, int NST>
+cudaError_t launch_one(const StreamArgs& a, int grid, cudaStream_t st, bool pdl) {
+  const size_t smem = sizeof(Smem<PHASE, FSET, NST>);
+  cudaError_t e = cudaFuncSetAttribute(stream_kernel<PHASE, NR, FSET, NST>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = launch_k(stream_kernel<PHASE, NR, FSET, NST>, grid, smem, st, pdl, a);
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
-template <int PHASE, unsigned FSET>
-int stream_occupancy(int nr) {
-  const size_t smem = sizeof(Smem<PHASE, FSET>);
+template <int PHASE, int NR, unsigned FSET, int NST>
+int occupancy_one() {
+  const size_t smem = sizeof(Smem<PHASE, FSET, NST>);
   int b = 0;
-  cudaError_t e = cudaErrorInvalidValue;
-  if (nr == 1) {
-    cudaFuncSetAttribute(stream_kernel<PHASE, 1, FSET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stream_kernel<PHASE, 1, FSET>, kStreamThreads, smem);
-  } else if (nr == 2) {
-    cudaFuncSetAttribute(stream_kernel<PHASE, 2, FSET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stream_kernel<PHASE, 2, FSET>, kStreamThreads, smem);
-  } else if (nr == 4) {
-    cudaFuncSetAttribute(stream_kernel<PHASE, 4, FSET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stream_kernel<PHASE, 4, FSET>, kStreamThreads, smem);
-  }
+  cudaFuncSetAttribute(stream_kernel<PHASE, NR, FSET, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stream_kernel<PHASE, NR, FSET, NST>, kStreamThreads, smem);
   return (e != cudaSuccess || b < 1) ? 1 : b;
+}
+
+// one right-hand side: pipeline depths 3, 4 and 6 (the autotuner's choice);
+// 2 and 4 right-hand sides: depth 4
+template <int PHASE, unsigned FSET>
+cudaError_t launch_stream_t(const StreamArgs& a, int grid, cudaStream_t st, bool pdl, int nst) {
+  switch (a.nr) {
+    case 1:
+      if (nst == 3) return launch_one<PHASE, 1, FSET, 3>(a, grid, st, pdl);
+      if (nst == 6) return launch_one<PHASE, 1, FSET, 6>(a, grid, st, pdl);
+      return launch_one<PHASE, 1, FSET, kStages>(a, grid, st, pdl);
+    case 2: return launch_one<PHASE, 2, FSET, kStages>(a, grid, st, pdl);
+    case 4: return launch_one<PHASE, 4, FSET, kStages>(a, grid, st, pdl);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int PHASE, unsigned FSET>
+int stream_occupancy(int nr, int nst) {
+  if (nr == 1) {
+    if (nst == 3) return occupancy_one<PHASE, 1, FSET, 3>();
+    if (nst == 6) return occupancy_one<PHASE, 1, FSET, 6>();
+    return occupancy_one<PHASE, 1, FSET, kStages>();
+  }
+  if (nr == 2) return occupancy_one<PHASE, 2, FSET, kStages>();
+  return occupancy_one<PHASE, 4, FSET, kStages>();
 }
 
 }  // namespace
 
-cudaError_t launch_stream(int phase, unsigned fset, const StreamArgs& a, int grid, cudaStream_t st, bool pdl) {
+bool stream_depth_ok(int nst) { return nst == 3 || nst == 4 || nst == 6; }
+
+cudaError_t launch_stream(int phase, unsigned fset, const StreamArgs& a, int grid, cudaStream_t st, bool pdl,
+                          int nst) {
   if (a.n_items == 0) return cudaSuccess;
   if (phase == 1) pdl = false;  // phase 1 needs the prep launch complete before it starts
+  if (!stream_depth_ok(nst)) nst = kStages;
   if (fset == kSetF64)
-    return phase == 1 ? launch_stream_t<1, kSetF64>(a, grid, st, false) : launch_stream_t<2, kSetF64>(a, grid, st, pdl);
+    return phase == 1 ? launch_stream_t<1, kSetF64>(a, grid, st, false, nst)
+                      : launch_stream_t<2, kSetF64>(a, grid, st, pdl, nst);
   if (fset == kSetF32)
-    return phase == 1 ? launch_stream_t<1, kSetF32>(a, grid, st, false) : launch_stream_t<2, kSetF32>(a, grid, st, pdl);
-  return phase == 1 ? launch_stream_t<1, kSetAll>(a, grid, st, false) : launch_stream_t<2, kSetAll>(a, grid, st, pdl);
+    return phase == 1 ? launch_stream_t<1, kSetF32>(a, grid, st, false, nst)
+                      : launch_stream_t<2, kSetF32>(a, grid, st, pdl, nst);
+  return phase == 1 ? launch_stream_t<1, kSetAll>(a, grid, st, false, nst)
+                    : launch_stream_t<2, kSetAll>(a, grid, st, pdl, nst);
 }
 
-int stream_blocks_per_sm(int phase, unsigned fset, int nr) {
-  if (fset == kSetF64) return phase == 1 ? stream_occupancy<1, kSetF64>(nr) : stream_occupancy<2, kSetF64>(nr);
-  if (fset == kSetF32) return phase == 1 ? stream_occupancy<1, kSetF32>(nr) : stream_occupancy<2, kSetF32>(nr);
-  return phase == 1 ? stream_occupancy<1, kSetAll>(nr) : stream_occupancy<2, kSetAll>(nr);
+int stream_blocks_per_sm(int phase, unsigned fset, int nr, int nst) {
+  if (!stream_depth_ok(nst)) nst = kStages;
+  if (fset == kSetF64) return phase == 1 ? stream_occupancy<1, kSetF64>(nr, nst) : stream_occupancy<2, kSetF64>(nr, nst);
+  if (fset == kSetF32) return phase == 1 ? stream_occupancy<1, kSetF32>(nr, nst) : stream_occupancy<2, kSetF32>(nr, nst);
+  return phase == 1 ? stream_occupancy<1, kSetAll>(nr, nst) : stream_occupancy<2, kSetAll>(nr, nst);
 }
 
 int stream_rows_per_item(int fmt) { return kP2RowBytes / (fmt == 0 ? 8 : (fmt == 1 ? 4 : (fmt == 4 ? 1 : 2))); }

@@ -240,6 +240,24 @@ def oracle_sample(path: str, x: np.ndarray, budget_s: float, fraction: float | N
     return (rate, desc, el, G) if keep else (rate, desc, el)
 
 
+def oracle_sample_1thread(path: str, x: np.ndarray, budget_s: float) -> dict:
+    """oracle_sample with NumPy's BLAS held to one thread: a child process
+    whose thread-count variables are set before NumPy loads."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = "1"
+    with tempfile.TemporaryDirectory() as d:
+        xp = os.path.join(d, "x.npy")
+        np.save(xp, x)
+        code = ("import sys, json, numpy as np; sys.path.insert(0, %r); import bench; "
+                "r, desc, el = bench.oracle_sample(%r, np.load(%r), %r); print(json.dumps([r, desc]))"
+                % (ROOT, path, xp, float(budget_s)))
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=max(120.0, 6 * budget_s))
+    rate, desc = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": rate, "cores": 1, "kind": "oracle", "sample": desc}
+
+
 def oracle_rows_check(G, x: np.ndarray, y: np.ndarray, leaves: int = 8, seed: int = 7) -> dict:
     """The product y (user order; one column or n x R) against the oracle's
     Algorithm 4 in float64 over the same stored factors, on the rows of a few
@@ -529,6 +547,52 @@ def run_construct(args):
     return 0
 
 
+def run_solve(args):
+    """Conjugate gradients (hh_solve_cg) for (A_h + I) x = b on the
+    16/8-bit Gaussian 65k matrix (a symmetric positive definite kernel), to
+    a relative residual of 1e-8: the solve's time, its iterations, and the
+    time per iteration against one product of the same matrix."""
+    import torch
+    import paper_2604_09147_gb300 as P
+    from paper_2604_09147_gb300 import build as B
+    B.build()
+    dev = torch.cuda.current_device()
+    c = W.CONFIGS["multirhs_262k"]
+    pts = W.config_points("multirhs_262k", args.low_bit_n)
+    H = P.HMatrix.build_cached(pts, CACHE, c["kernel"], c["kernel_param"], c["leaf"], c["eta"], c["ell"], c["tol"],
+                               c["fmts"], device=dev)
+    tuned = None if args.no_autotune else H.autotune(0)
+    n = len(pts)
+    b = torch.from_numpy(W.rhs(n, 1, "uniform", 4401)[:, 0].copy()).cuda()
+    H.solve_cg(b, shift=1.0, rtol=1e-8, max_iter=20)          # warm-up
+    torch.cuda.synchronize()
+    ts, its = [], 0
+    for _ in range(max(1, min(args.steps, 5))):
+        t0 = time.perf_counter()
+        x, its, res = H.solve_cg(b, shift=1.0, rtol=1e-8, max_iter=2000)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    y = torch.empty_like(b)
+    for _ in range(3):
+        H.matvec(b, out=y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        H.matvec(b, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    prod_ms = e0.elapsed_time(e1) / 20
+    t = statistics.median(ts)
+    out = {"metric": "conjugate-gradient solve seconds, (A_h + I) x = b to 1e-8", "value": t, "unit": "s",
+           "n_gpus": 1, "steps": len(ts), "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": WORKLOADS["lowbit_65k"] if args.low_bit_n == 65536 else f"n={n}", "n": n,
+                      "shift": 1.0, "rtol": 1e-8},
+           "iterations": its, "final_relres": res, "ms_per_iteration": 1e3 * t / max(1, its),
+           "product_ms": prod_ms, "overhead_per_iteration_ms": 1e3 * t / max(1, its) - prod_ms, "autotune": tuned}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -603,6 +667,12 @@ def run_ours(args):
         Ham.save(path)
         rate, desc, _, G = oracle_sample(path, xh0, args.cpu_seconds, keep=True)
         cpu = {"value": rate, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+        try:  # the same oracle on one thread
+            one = oracle_sample_1thread(path, xh0, args.cpu_seconds / 2)
+            one["unit"] = "matvec/s"
+            cpu["one_thread"] = one
+        except Exception as e:  # reported, not fatal to the measurement
+            cpu["one_thread"] = {"error": f"{type(e).__name__}: {e}"}
         # the product's error against the oracle, beside the paper's bound
         try:
             parity = oracle_rows_check(G, xh0, y_amp)
@@ -942,10 +1012,11 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="adaptive_65k")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU oracle baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["replicas", "sharded", "construct"], default="replicas",
+    ap.add_argument("--mode", choices=["replicas", "sharded", "construct", "solve"], default="replicas",
                     help="replicas: independent products per rank (weak scaling); sharded: the "
                          "adaptive workload's block rows split over the ranks (strong scaling); construct: "
-                         "construction time on the GPU against the host builder")
+                         "construction time on the GPU against the host builder; solve: conjugate "
+                         "gradients on the 16/8-bit Gaussian matrix")
     ap.add_argument("--construct-n", type=int, default=0,
                     help="construct mode: points of the exp(-r) family (0: the adaptive 65k workload)")
     ap.add_argument("--no-host-build", action="store_true", help="construct mode: skip the host builder")
@@ -970,6 +1041,8 @@ def main(argv=None):
         return run_sharded(args)
     if args.mode == "construct":
         return run_construct(args)
+    if args.mode == "solve":
+        return run_solve(args)
     if args.workload in MANY_N:
         return run_many(args)
     if args.workload in LOWBIT_N:

@@ -319,8 +319,11 @@ int hh_matvec_T(hh_handle h, const double* ybar, double* xbar, int nrhs, int64_t
  *   max_iter, iters, relres   iteration cap; iterations done and the final
  *           ||r|| / ||b|| (either pointer may be NULL).
  * Each iteration is one forward product (the streaming passes, on the
- * handle's workspace) and two dot products read back to the host (the call
- * synchronises `stream`); three n-vectors are allocated for the call.
+ * handle's workspace), two dot products and two vector updates; the scalars
+ * (alpha, beta, the convergence and breakdown tests) stay on the device and
+ * the host reads them every 8 iterations (iterations past the stop change
+ * nothing, so results and counts are those of testing every iteration).
+ * The call synchronises `stream`; three n-vectors are allocated for it. 
  * HH_EINVAL if b and x overlap or the iteration breaks down
  * (p^T (A_h + shift I) p <= 0: not positive definite). */
 int hh_solve_cg(hh_handle h, const double* b, double* x, double shift, double rtol, int max_iter,

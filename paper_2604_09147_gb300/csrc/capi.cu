@@ -1407,8 +1407,9 @@ int hh_solve_cg(hh_handle h, const double* b, double* x, double shift, double rt
   cudaGetDevice(&cur);
   if (cur != h->device) cudaSetDevice(h->device);
   cudaStream_t st = (cudaStream_t)stream;
-  double* scratch = nullptr;  // r, p, q, dot partials
-  if (cudaMalloc(&scratch, 3 * nb + sizeof(double) * hh::dev::kDotBlocks) != cudaSuccess) {
+  double* scratch = nullptr;  // r, p, q, dot partials, the solver's device scalars
+  const size_t state_doubles = (sizeof(hh::dev::CgState) + sizeof(double) - 1) / sizeof(double);
+  if (cudaMalloc(&scratch, 3 * nb + sizeof(double) * (hh::dev::kDotBlocks + state_doubles)) != cudaSuccess) {
     if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
     return fail(HH_ENOMEM, "cannot allocate the solver vectors");
   }
@@ -1416,16 +1417,17 @@ int hh_solve_cg(hh_handle h, const double* b, double* x, double shift, double rt
   double* p = r + n;
   double* q = p + n;
   double* part = q + n;
+  hh::dev::CgState* dstate = reinterpret_cast<hh::dev::CgState*>(part + hh::dev::kDotBlocks);
   std::vector<double> hpart(hh::dev::kDotBlocks);
   int rc = HH_OK;
   cudaError_t e = cudaSuccess;
-  auto dot = [&](const double* u, const double* v) {
+  auto dot = [&](const double* u, const double* v) {  // on the host: the start of the solve only
     double s = 0.0;
     if (e == cudaSuccess) e = hh::dev::launch_dot(u, v, n, part, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hpart.data(), part, sizeof(double) * hh::dev::kDotBlocks,
                                               cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    for (double v2 : hpart) s += v2;  // block order: deterministic
+    for (double v2 : hpart) s += v2;  // block order: deterministic, as the device sums them
     return s;
   };
   auto apply = [&](const double* in, double* out) {  // out = (A_h + shift I) in
@@ -1440,22 +1442,40 @@ int hh_solve_cg(hh_handle h, const double* b, double* x, double shift, double rt
   if (e == cudaSuccess && rc == HH_OK) e = cudaMemcpyAsync(p, r, nb, cudaMemcpyDeviceToDevice, st);
   const double bnorm = std::sqrt(dot(b, b));
   double rr = dot(r, r);
-  int it = 0;
-  while (rc == HH_OK && e == cudaSuccess && it < max_iter && std::sqrt(rr) > rtol * bnorm) {
-    apply(p, q);
-    const double pq = dot(p, q);
-    if (rc != HH_OK || e != cudaSuccess) break;
-    if (!(pq > 0.0)) {
-      rc = fail(HH_EINVAL, "conjugate gradients broke down: p^T (A + shift I) p <= 0");
-      break;
+  // iterations run on the device scalars (alpha, beta, the convergence and
+  // breakdown tests in one-thread kernels); the host reads them back every
+  // kCheck iterations, and iterations past the stop leave x untouched, so
+  // the result and the count are those of testing every iteration
+  constexpr int kCheck = 8;
+  hh::dev::CgState hs{};
+  hs.rr = rr;
+  hs.threshold = rtol * bnorm;
+  hs.done = (max_iter == 0 || !(std::sqrt(rr) > rtol * bnorm)) ? 1.0 : 0.0;
+  hs.max_iter = max_iter;
+  if (e == cudaSuccess && rc == HH_OK)
+    e = cudaMemcpyAsync(dstate, &hs, sizeof(hs), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  int launched = 0;
+  while (rc == HH_OK && e == cudaSuccess && hs.done == 0.0 && launched < max_iter) {
+    const int batch = std::min(kCheck, max_iter - launched);
+    for (int j = 0; j < batch && rc == HH_OK && e == cudaSuccess; ++j) {
+      apply(p, q);
+      if (rc != HH_OK || e != cudaSuccess) break;
+      e = hh::dev::launch_dot(p, q, n, part, st);
+      if (e == cudaSuccess) e = hh::dev::launch_cg_alpha(part, dstate, st);
+      if (e == cudaSuccess) e = hh::dev::launch_cg_step(x, r, p, q, dstate, n, st);
+      if (e == cudaSuccess) e = hh::dev::launch_dot(r, r, n, part, st);
+      if (e == cudaSuccess) e = hh::dev::launch_cg_beta(part, dstate, st);
+      if (e == cudaSuccess) e = hh::dev::launch_cg_dir(p, r, dstate, n, st);
     }
-    const double alpha = rr / pq;
-    e = hh::dev::launch_cg_step(x, r, p, q, alpha, n, st);
-    const double rr_new = dot(r, r);
-    if (e == cudaSuccess) e = hh::dev::launch_cg_dir(p, r, rr_new / rr, n, st);
-    rr = rr_new;
-    ++it;
+    launched += batch;
+    if (e == cudaSuccess && rc == HH_OK) e = cudaMemcpyAsync(&hs, dstate, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
+  const int it = static_cast<int>(hs.iters);
+  rr = hs.rr;
+  if (rc == HH_OK && e == cudaSuccess && hs.breakdown != 0.0)
+    rc = fail(HH_EINVAL, "conjugate gradients broke down: p^T (A + shift I) p <= 0");
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(scratch);
   if (rc == HH_OK && e != cudaSuccess) rc = fail(HH_ECUDA, std::string("solver launch failed: ") + cudaGetErrorString(e));

@@ -90,9 +90,16 @@ cudaError_t launch_batch_finish(const double* acc, const int64_t* xofs, const in
 constexpr int kDotBlocks = 256;  // a dot product writes kDotBlocks partial sums
 cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* partials, cudaStream_t st);
 cudaError_t launch_shift(double* q, const double* p, double shift, int64_t n, cudaStream_t st);  // q += shift p
-cudaError_t launch_cg_step(double* x, double* r, const double* p, const double* q, double alpha, int64_t n,
-                           cudaStream_t st);  // x += alpha p, r -= alpha q
-cudaError_t launch_cg_dir(double* p, const double* r, double beta, int64_t n, cudaStream_t st);  // p = r + beta p
+// scalars of one conjugate-gradient solve, kept on the device
+struct CgState {
+  double rr, alpha, beta, threshold;  // threshold: rtol ||b||
+  double done, breakdown, iters, max_iter, active;
+};
+cudaError_t launch_cg_step(double* x, double* r, const double* p, const double* q, const CgState* s, int64_t n,
+                           cudaStream_t st);  // x += alpha p, r -= alpha q (active iterations)
+cudaError_t launch_cg_dir(double* p, const double* r, const CgState* s, int64_t n, cudaStream_t st);  // p = r + beta p
+cudaError_t launch_cg_alpha(const double* partials, CgState* s, cudaStream_t st);  // alpha = rr / (p . q)
+cudaError_t launch_cg_beta(const double* partials, CgState* s, cudaStream_t st);   // rr, beta, convergence
 
 // ---- tensor-core path for many right-hand sides (tc.cu) ----
 // A piece: ranks [r0, r0 + k) of one low-rank block stored in fp32, fp16, bf16

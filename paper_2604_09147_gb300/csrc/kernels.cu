@@ -231,20 +231,56 @@ __global__ void shift_kernel(double* __restrict__ q, const double* __restrict__ 
 }
 
 // x += alpha p, r -= alpha q
+// The solver's scalars live on the device (CgState); each kernel reads them
+// there, so an iteration needs no host round trip.  `active` is decided at
+// the start of an iteration: a converged, broken-down or finished solve
+// leaves x, r and p untouched from then on.
 __global__ void cg_step_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                               const double* __restrict__ q, double alpha, int64_t n) {
+                               const double* __restrict__ q, const CgState* __restrict__ s, int64_t n) {
+  if (s->active == 0.0) return;
+  const double alpha = s->alpha;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     x[i] += alpha * p[i];
     r[i] -= alpha * q[i];
   }
 }
-
-// p = r + beta p
-__global__ void cg_dir_kernel(double* __restrict__ p, const double* __restrict__ r, double beta, int64_t n) {
+__global__ void cg_dir_kernel(double* __restrict__ p, const double* __restrict__ r, const CgState* __restrict__ s,
+                              int64_t n) {
+  if (s->active == 0.0) return;
+  const double beta = s->beta;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
     p[i] = r[i] + beta * p[i];
+}
+// sum of the dot kernel's partials in block order (one thread: deterministic)
+__device__ double sum_partials(const double* part) {
+  double v = 0.0;
+  for (int b = 0; b < kDotBlocks; ++b) v += part[b];
+  return v;
+}
+// start of an iteration: pq = p . q; alpha = rr / pq, or a breakdown
+__global__ void cg_alpha_kernel(const double* __restrict__ part, CgState* __restrict__ s) {
+  if (threadIdx.x != 0) return;
+  s->active = (s->done == 0.0 && s->iters < s->max_iter) ? 1.0 : 0.0;
+  if (s->active == 0.0) return;
+  const double pq = sum_partials(part);
+  if (!(pq > 0.0)) {
+    s->breakdown = 1.0;
+    s->done = 1.0;
+    s->active = 0.0;
+    return;
+  }
+  s->alpha = s->rr / pq;
+}
+// end of an iteration: rr_new = r . r, beta = rr_new / rr, convergence test
+__global__ void cg_beta_kernel(const double* __restrict__ part, CgState* __restrict__ s) {
+  if (threadIdx.x != 0 || s->active == 0.0) return;
+  const double rr_new = sum_partials(part);
+  s->beta = rr_new / s->rr;
+  s->rr = rr_new;
+  s->iters += 1.0;
+  if (!(sqrt(rr_new) > s->threshold)) s->done = 1.0;
 }
 
 int vec_blocks(int64_t n) {
@@ -265,14 +301,24 @@ cudaError_t launch_shift(double* q, const double* p, double shift, int64_t n, cu
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_step(double* x, double* r, const double* p, const double* q, double alpha, int64_t n,
+cudaError_t launch_cg_step(double* x, double* r, const double* p, const double* q, const CgState* s, int64_t n,
                            cudaStream_t st) {
-  cg_step_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>(x, r, p, q, alpha, n);
+  cg_step_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>(x, r, p, q, s, n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_dir(double* p, const double* r, double beta, int64_t n, cudaStream_t st) {
-  cg_dir_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>(p, r, beta, n);
+cudaError_t launch_cg_dir(double* p, const double* r, const CgState* s, int64_t n, cudaStream_t st) {
+  cg_dir_kernel<<<vec_blocks(n), kVecThreads, 0, st>>>(p, r, s, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_alpha(const double* partials, CgState* s, cudaStream_t st) {
+  cg_alpha_kernel<<<1, 32, 0, st>>>(partials, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_beta(const double* partials, CgState* s, cudaStream_t st) {
+  cg_beta_kernel<<<1, 32, 0, st>>>(partials, s);
   return cudaGetLastError();
 }
 

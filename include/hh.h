@@ -380,10 +380,14 @@ int hh_matvec_stages(hh_handle h, int transpose, const double* in, double* out, 
 int hh_matvec_batched(const hh_handle* hs, int count, const double* const* xs,
                       double* const* ys, void* stream);
 
-/* Batches of independent matrices (one right-hand side each) in one launch
- * sequence.  The product of every matrix is Algorithm 4 as above; the batch
- * only concatenates the work tables, so one product of the whole batch is
- * four kernel launches (prep, phase 1, phase 2, finish) whatever the count.
+/* Batches of independent matrices (one right-hand side each) in one launch.
+ * The product of every matrix is Algorithm 4 as above; the batch only
+ * concatenates the work tables, so one product of the whole batch is one
+ * persistent cooperative kernel (prep, phase 1, phase 2 and finish separated
+ * by grid-wide barriers, one co-resident CTA set) whatever the count.  Where
+ * the device has no cooperative launch, or HH_BATCH_LAUNCHES=4 is set when
+ * the batch is created, it is four launches (prep, phase 1, phase 2,
+ * finish).
  *
  * hh_batch_create -- a batch over `count` >= 1 handles on one device.  The
  *   handles must stay alive (not hh_free'd) while the batch exists.  Allocates

@@ -1751,6 +1751,8 @@ struct hh_batch_s {
   float* t32 = nullptr;
   float2* t64 = nullptr;
   int* counters = nullptr;
+  int persistent = 1;             // one cooperative kernel per product (0: prep, two passes, finish)
+  int pgrid[2] = {0, 0};          // its co-resident grid per direction
   cudaStream_t cap = nullptr;     // private stream for graph capture
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   const double* gx[2] = {nullptr, nullptr};
@@ -1780,7 +1782,37 @@ void free_batch(hh_batch_s* b) {
   if (cur >= 0 && cur != b->device) cudaSetDevice(cur);
 }
 
+// one batch product: the persistent kernel, or prep, phase 1, phase 2, finish
 cudaError_t batch_launches(hh_batch_s* b, int dir, const double* x, double* y, cudaStream_t st) {
+  if (b->persistent && b->pgrid[dir] > 0) {
+    hh::dev::BatchArgs ba;
+    std::memset(&ba, 0, sizeof(ba));
+    for (int phase = 1; phase <= 2; ++phase) {
+      const StreamSet& set = b->ss[dir];
+      hh::dev::StreamArgs& a = ba.pass[phase - 1];
+      a.desc = set.d_desc[phase - 1];
+      a.items = set.d_items[phase - 1];
+      a.n_items = set.n_items[phase - 1];
+      a.nr = 1;
+      a.npad = b->np;
+      a.xs = b->xs;
+      a.xs_lo = b->xs_lo;
+      a.t32 = b->t32;
+      a.t64 = b->t64;
+      a.acc = b->acc;
+      a.status = b->mats[0]->d_status;
+      a.counter = b->counters + (phase - 1);
+    }
+    ba.x = x;
+    ba.y = y;
+    ba.xofs = b->d_xofs;
+    ba.perm = b->d_perm;
+    ba.pofs = b->d_pofs;
+    ba.ns = b->d_ns;
+    ba.count = b->count;
+    ba.np = b->np;
+    return hh::dev::launch_batch_persistent(b->ss[dir].fset, ba, b->pgrid[dir], st);
+  }
   cudaError_t e = hh::dev::launch_batch_prep(x, b->d_xofs, b->d_perm, b->d_pofs, b->d_ns, b->count, b->np, b->xs,
                                              b->xs_lo, b->acc, b->counters, st);
   bool p1 = false;
@@ -1909,6 +1941,12 @@ int hh_batch_create(const hh_handle* hs, int count, hh_batch* out) {
     b->t64 = reinterpret_cast<float2*>(w + o_t64);
     b->counters = reinterpret_cast<int*>(w + o_cnt);
     ck(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    // the persistent kernel needs cooperative launch and one co-resident grid
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device);
+    const char* env = std::getenv("HH_BATCH_LAUNCHES");
+    b->persistent = (coop && !(env && std::atoi(env) == 4)) ? 1 : 0;
+    for (int d = 0; d < 2; ++d) b->pgrid[d] = hh::dev::batch_persistent_grid(b->ss[d].fset, b->sms);
   } catch (const CudaError& e) {
     free_batch(b);
     delete b;
@@ -1966,15 +2004,23 @@ int hh_batch_matvec_graph(hh_batch b, int transpose, const double* x, double* y,
       cudaGraphExecDestroy(b->gexec[dir]);
       b->gexec[dir] = nullptr;
     }
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
-    cudaError_t e2 = cudaSuccess;
-    if (e == cudaSuccess) {
-      e2 = batch_launches(b, dir, x, y, b->cap);
-      e = cudaStreamEndCapture(b->cap, &g);
+    cudaError_t e = cudaSuccess, e2 = cudaSuccess;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+      e2 = cudaSuccess;
+      if (e == cudaSuccess) {
+        e2 = batch_launches(b, dir, x, y, b->cap);
+        e = cudaStreamEndCapture(b->cap, &g);
+      }
+      if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&b->gexec[dir], g, 0);
+      if (g) cudaGraphDestroy(g);
+      if ((e == cudaSuccess && e2 == cudaSuccess) || !b->persistent) break;
+      // the cooperative kernel could not be captured: the four-launch sequence
+      cudaGetLastError();
+      b->gexec[dir] = nullptr;
+      b->persistent = 0;
     }
-    if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&b->gexec[dir], g, 0);
-    if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       b->gexec[dir] = nullptr;
       rc = fail(HH_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));

@@ -43,7 +43,7 @@ struct StreamArgs {
   float* t32;
   float2* t64;         // t of fp64 blocks as (leading, trailing) fp32 halves
   double* acc;
-  int* status;   // bit 0 bad descriptor, bit 2 a bounded wait expired
+  int* status;   // bit 0 bad descriptor, bit 2 a bounded wait expired, bit 4 batch kernel not cooperative
   int* counter;  // work counter of this pass (zeroed by the prep launch)
 };
 
@@ -85,6 +85,72 @@ cudaError_t launch_batch_prep(const double* x, const int64_t* xofs, const int32_
                               int* counters, cudaStream_t st);
 cudaError_t launch_batch_finish(const double* acc, const int64_t* xofs, const int32_t* perm, const int64_t* pofs,
                                 const int64_t* ns, int count, int64_t np, double* y, cudaStream_t st);
+
+// A whole batch product in one persistent cooperative kernel (stream.cu):
+// prep, phase 1, phase 2 and finish separated by grid-wide barriers.
+struct BatchArgs {
+  StreamArgs pass[2];  // phase 1, phase 2 (counters zeroed by the prep stage)
+  const double* x;
+  double* y;
+  const int64_t* xofs;
+  const int32_t* perm;
+  const int64_t* pofs;
+  const int64_t* ns;
+  int32_t count, pad;
+  int64_t np;
+};
+// CTAs of the persistent batch kernel that are co-resident on the device
+// (sms x its occupancy); the launch must not use more
+int batch_persistent_grid(unsigned fset, int sms);
+cudaError_t launch_batch_persistent(unsigned fset, const BatchArgs& a, int grid, cudaStream_t st);
+
+#ifdef __CUDACC__
+// matrix j of a batch holding concatenated position q: pofs[j] <= q < pofs[j + 1]
+__device__ __forceinline__ int batch_find(const int64_t* __restrict__ pofs, int count, int64_t q) {
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pofs[mid] <= q)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+// position p of a batch's input images: the four shifted copies of the fp32
+// leading / trailing halves, and the cleared accumulator
+__device__ __forceinline__ void batch_prep_position(int64_t p, const double* __restrict__ x,
+                                                    const int64_t* __restrict__ xofs, const int32_t* __restrict__ perm,
+                                                    const int64_t* __restrict__ pofs, const int64_t* __restrict__ ns,
+                                                    int count, int64_t np, float* __restrict__ xs,
+                                                    float* __restrict__ xs_lo, double* __restrict__ acc) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int64_t q = p + s;
+    double v = 0.0;
+    if (q < np) {
+      const int j = batch_find(pofs, count, q);
+      const int64_t l = q - pofs[j];
+      if (l < ns[j]) v = x[xofs[j] + perm[pofs[j] + l]];
+    }
+    const float hi = __double2float_rn(v);
+    xs[static_cast<int64_t>(s) * np + p] = hi;
+    xs_lo[static_cast<int64_t>(s) * np + p] = __double2float_rn(v - static_cast<double>(hi));
+  }
+  acc[p] = 0.0;
+}
+// position p of a batch's output: y in each matrix's caller order
+__device__ __forceinline__ void batch_finish_position(int64_t p, const double* __restrict__ acc,
+                                                      const int64_t* __restrict__ xofs,
+                                                      const int32_t* __restrict__ perm,
+                                                      const int64_t* __restrict__ pofs,
+                                                      const int64_t* __restrict__ ns, int count,
+                                                      double* __restrict__ y) {
+  const int j = batch_find(pofs, count, p);
+  const int64_t l = p - pofs[j];
+  if (l < ns[j]) y[xofs[j] + perm[pofs[j] + l]] = acc[p];
+}
+#endif
 
 // ---- vector kernels of the conjugate-gradient solver (kernels.cu) ----
 constexpr int kDotBlocks = 256;  // a dot product writes kDotBlocks partial sums

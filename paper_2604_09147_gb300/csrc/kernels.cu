@@ -126,17 +126,6 @@ namespace hh {
 namespace dev {
 namespace {
 
-__device__ __forceinline__ int batch_find(const int64_t* __restrict__ pofs, int count, int64_t q) {
-  int lo = 0, hi = count;  // pofs[lo] <= q < pofs[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (pofs[mid] <= q)
-      lo = mid;
-    else
-      hi = mid;
-  }
-  return lo;
-}
 
 __global__ void bprep_kernel(const double* __restrict__ x, const int64_t* __restrict__ xofs,
                              const int32_t* __restrict__ perm, const int64_t* __restrict__ pofs,
@@ -144,33 +133,16 @@ __global__ void bprep_kernel(const double* __restrict__ x, const int64_t* __rest
                              float* __restrict__ xs_lo, double* __restrict__ acc, int* __restrict__ counters) {
   if (counters && blockIdx.x == 0 && threadIdx.x < 2) counters[threadIdx.x] = 0;
   for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < np;
-       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int64_t q = p + s;
-      double v = 0.0;
-      if (q < np) {
-        const int j = batch_find(pofs, count, q);
-        const int64_t l = q - pofs[j];
-        if (l < ns[j]) v = x[xofs[j] + perm[pofs[j] + l]];
-      }
-      const float hi = __double2float_rn(v);
-      xs[static_cast<int64_t>(s) * np + p] = hi;
-      xs_lo[static_cast<int64_t>(s) * np + p] = __double2float_rn(v - static_cast<double>(hi));
-    }
-    acc[p] = 0.0;
-  }
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    batch_prep_position(p, x, xofs, perm, pofs, ns, count, np, xs, xs_lo, acc);
 }
 
 __global__ void bfinish_kernel(const double* __restrict__ acc, const int64_t* __restrict__ xofs,
                                const int32_t* __restrict__ perm, const int64_t* __restrict__ pofs,
                                const int64_t* __restrict__ ns, int count, int64_t np, double* __restrict__ y) {
   for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < np;
-       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int j = batch_find(pofs, count, p);
-    const int64_t l = p - pofs[j];
-    if (l < ns[j]) y[xofs[j] + perm[pofs[j] + l]] = acc[p];
-  }
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    batch_finish_position(p, acc, xofs, perm, pofs, ns, count, y);
 }
 
 }  // namespace

@@ -30,6 +30,7 @@
 // not write) while phase 1 drains, and its consumers wait for phase 1 to
 // complete (griddepcontrol.wait, a no-op for a normal launch) before they
 // read t.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -688,9 +689,10 @@ __device__ void consume(Smem<PHASE, FSET, NST>& sm, const StreamArgs& a) {
   }
 }
 
+// one pass by one CTA: barriers set up, then the producer warp and the
+// consumer warps; every thread returns (also after a bounded wait expired)
 template <int PHASE, int NR, unsigned FSET, int NST>
-__global__ void __launch_bounds__(kStreamThreads) stream_kernel(StreamArgs a) {
-  extern __shared__ __align__(128) uint8_t smem_raw[];
+__device__ __forceinline__ void stream_body(uint8_t* smem_raw, const StreamArgs& a) {
   Smem<PHASE, FSET, NST>& sm = *reinterpret_cast<Smem<PHASE, FSET, NST>*>(smem_raw);
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -703,6 +705,28 @@ __global__ void __launch_bounds__(kStreamThreads) stream_kernel(StreamArgs a) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (threadIdx.x < 32) produce<PHASE, FSET, NST>(sm, a);
   else consume<PHASE, NR, FSET, NST>(sm, a);
+}
+
+// after a pass in a kernel that reuses the shared memory: every thread is
+// done with the barriers (no copy is in flight once the consumers have
+// consumed every stage, or the producer has drained them after a timeout),
+// so they are invalidated before the memory serves another purpose
+template <int PHASE, unsigned FSET, int NST>
+__device__ __forceinline__ void stream_teardown(uint8_t* smem_raw) {
+  Smem<PHASE, FSET, NST>& sm = *reinterpret_cast<Smem<PHASE, FSET, NST>*>(smem_raw);
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int s = 0; s < NST; ++s) {
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(saddr(&sm.full[s])) : "memory");
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(saddr(&sm.empty[s])) : "memory");
+    }
+  __syncthreads();
+}
+
+template <int PHASE, int NR, unsigned FSET, int NST>
+__global__ void __launch_bounds__(kStreamThreads) stream_kernel(StreamArgs a) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  stream_body<PHASE, NR, FSET, NST>(smem_raw, a);
 }
 
 // launch with (pdl) or without programmatic stream serialization
@@ -766,6 +790,76 @@ int stream_occupancy(int nr, int nst) {
   return occupancy_one<PHASE, 4, FSET, kStages>();
 }
 
+// The whole batch product in one persistent kernel (a cooperative launch:
+// every CTA is resident, so the grid-wide barriers between the stages are
+// safe): prep over all positions, phase 1, phase 2 and the output
+// permutation.  Each stage's writes are visible to the next after the
+// barrier; the input copies and t, read with non-coherent loads in phase 2,
+// are written before that stage starts and not cached by it earlier.
+template <unsigned FSET>
+constexpr size_t batch_smem() {
+  return sizeof(Smem<1, FSET, kStages>) > sizeof(Smem<2, FSET, kStages>) ? sizeof(Smem<1, FSET, kStages>)
+                                                                         : sizeof(Smem<2, FSET, kStages>);
+}
+
+template <unsigned FSET>
+__global__ void __launch_bounds__(kStreamThreads) batch_kernel(BatchArgs a) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  const int64_t tid = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (!grid.is_valid()) {  // not a cooperative launch: no grid barrier may be used
+    if (tid == 0) atomicOr(a.pass[0].status, 16);
+    return;
+  }
+  const int64_t nth = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  if (tid < 2) *(tid == 0 ? a.pass[0].counter : a.pass[1].counter) = 0;
+  for (int64_t p = tid; p < a.np; p += nth)
+    batch_prep_position(p, a.x, a.xofs, a.perm, a.pofs, a.ns, a.count, a.np, const_cast<float*>(a.pass[0].xs),
+                        const_cast<float*>(a.pass[0].xs_lo), a.pass[0].acc);
+  grid.sync();
+  if (a.pass[0].n_items > 0) {
+    stream_body<1, 1, FSET, kStages>(smem_raw, a.pass[0]);
+    stream_teardown<1, FSET, kStages>(smem_raw);
+  }
+  grid.sync();
+  if (a.pass[1].n_items > 0) {
+    stream_body<2, 1, FSET, kStages>(smem_raw, a.pass[1]);
+    stream_teardown<2, FSET, kStages>(smem_raw);
+  }
+  grid.sync();
+  for (int64_t p = tid; p < a.np; p += nth)
+    batch_finish_position(p, a.pass[1].acc, a.xofs, a.perm, a.pofs, a.ns, a.count, a.y);
+}
+
+template <unsigned FSET>
+int batch_occupancy() {
+  const size_t smem = batch_smem<FSET>();
+  int b = 0;
+  cudaFuncSetAttribute(batch_kernel<FSET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_kernel<FSET>, kStreamThreads, smem);
+  return e == cudaSuccess ? b : 0;
+}
+
+template <unsigned FSET>
+cudaError_t launch_batch_t(const BatchArgs& a, int grid, cudaStream_t st) {
+  const size_t smem = batch_smem<FSET>();
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel<FSET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(kStreamThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, batch_kernel<FSET>, a);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
 }  // namespace
 
 bool stream_depth_ok(int nst) { return nst == 3 || nst == 4 || nst == 6; }
@@ -790,6 +884,19 @@ int stream_blocks_per_sm(int phase, unsigned fset, int nr, int nst) {
   if (fset == kSetF64) return phase == 1 ? stream_occupancy<1, kSetF64>(nr, nst) : stream_occupancy<2, kSetF64>(nr, nst);
   if (fset == kSetF32) return phase == 1 ? stream_occupancy<1, kSetF32>(nr, nst) : stream_occupancy<2, kSetF32>(nr, nst);
   return phase == 1 ? stream_occupancy<1, kSetAll>(nr, nst) : stream_occupancy<2, kSetAll>(nr, nst);
+}
+
+int batch_persistent_grid(unsigned fset, int sms) {
+  const int occ = fset == kSetF64 ? batch_occupancy<kSetF64>()
+                                  : (fset == kSetF32 ? batch_occupancy<kSetF32>() : batch_occupancy<kSetAll>());
+  return occ * sms;
+}
+
+cudaError_t launch_batch_persistent(unsigned fset, const BatchArgs& a, int grid, cudaStream_t st) {
+  if (grid < 1) return cudaErrorInvalidValue;
+  if (fset == kSetF64) return launch_batch_t<kSetF64>(a, grid, st);
+  if (fset == kSetF32) return launch_batch_t<kSetF32>(a, grid, st);
+  return launch_batch_t<kSetAll>(a, grid, st);
 }
 
 int stream_rows_per_item(int fmt) { return kP2RowBytes / (fmt == 0 ? 8 : (fmt == 1 ? 4 : (fmt == 4 ? 1 : 2))); }

@@ -289,8 +289,9 @@ def test_host_api_and_batched(P, tmp_path):
 
 def test_batch_one_launch_sequence_and_graph(P, tmp_path):
     """Uneven batch (2-D exp and 3-D 1/r, sizes that are not multiples of the
-    leaf size) through one launch sequence and through a captured CUDA graph,
-    forward and transposed, against the oracle per matrix."""
+    leaf size) through one persistent kernel and through a captured CUDA
+    graph, forward and transposed, against the oracle per matrix; and the
+    same batch through the four-launch sequence (HH_BATCH_LAUNCHES=4)."""
     specs = [(3000, 2, W.EXP, 64), (5184, 3, W.INV_R, 128), (2100, 2, W.EXP, 64), (7777, 3, W.INV_R, 128),
              (4096, 2, W.EXP, 64), (2500, 3, W.INV_R, 64)]
     mats, oracles, xs = [], [], []
@@ -318,6 +319,18 @@ def test_batch_one_launch_sequence_and_graph(P, tmp_path):
         # replays agree up to the order of the fp64 atomic additions
         assert rel(y3, y2) <= 1e-12
         assert rel(y2, y1) <= 1e-12
+    # the persistent cooperative kernel (default) against the four-launch sequence
+    os.environ["HH_BATCH_LAUNCHES"] = "4"
+    try:
+        B4 = P.HBatch(mats)
+    finally:
+        del os.environ["HH_BATCH_LAUNCHES"]
+    for tr in (False, True):
+        yp = B.matvec(x, transpose=tr, graph=True).cpu().numpy()
+        y4 = B4.matvec(x, transpose=tr, graph=True).cpu().numpy()
+        assert rel(y4, yp) <= 1e-12
+        assert rel(B4.matvec(x, transpose=tr).cpu().numpy(), yp) <= 1e-12
+    B4.close()
     B.close()
 
 

@@ -67,10 +67,8 @@ WORKLOADS["uneven_batch"] = ("64 independent matrices, N log-uniform in [nmin, n
                              "even index 2-D exp(-r) leaf 64, odd index 3-D 1/r leaf 128; eta 1, switch level "
                              "floor(L/2), tol 1e-6, adaptive {fp64,fp32,fp16,bf16}; one RHS U(-1,1) each")
 # fp32 FMA issue rate of the CUDA cores: 152 SMs x 128 lanes x 2 flops at the
-# 2,070 MHz maximum SM clock; a product of fp32 pairs (the dense blocks) costs
-# 9 fp32 instructions (3 FMA, 6 add) per multiply-add
+# 2,070 MHz maximum SM clock
 FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-DD_TFLOPS = FP32_TFLOPS * 2 / (2 * 9)
 
 
 def dist_env():
@@ -762,22 +760,28 @@ def run_many(args):
     # per-launch device times of the sequence (CUDA events around every launch)
     nst = max(3, min(args.steps, 20))
     st = np.mean([H.matvec_stages(x, y) for _ in range(nst)], axis=0)
-    names = ["images", "fp64_streaming", "mr_phase1", "tc_phase1", "mr_phase2", "mr_dense", "tc_phase2", "finish"]
+    names = ["images", "tc_dense", "fp64_streaming", "mr_phase1", "tc_phase1", "mr_phase2", "tc_phase2", "finish"]
     stages = {k: float(v) for k, v in zip(names, st)}
     hbm, peak_kind = peaks()
     bf16, bf16_kind = bf16_peak()
     fmt_b = {"fp32": 4, "fp16": 2, "bf16": 2, "e4m3": 1}
-    # Roofline per launch.  The CUDA-core products are bound by the fp32 (or
-    # fp32-pair) FMA rate.  The tensor-core phases are bound by HBM: at R
-    # columns a stored element carries 2R flop, at R = 128 64 flop/B for
-    # fp32 and 128 for bf16 factors, below the bf16 ridge (about 251 flop/B),
-    # so their roof is their stored factor bytes at the measured HBM
-    # bandwidth; the same algorithmic flops against the bf16 tensor peak are
-    # reported beside it.
+    # Roofline per launch.  The CUDA-core products are bound by the fp32 FMA
+    # rate.  The tensor-core phases are bound by HBM: at R columns a stored
+    # element carries 2R flop, at R = 128 64 flop/B for fp32 and 128 for
+    # bf16 factors, below the bf16 ridge (about 251 flop/B), so their roof
+    # is their stored factor bytes at the measured HBM bandwidth; the same
+    # algorithmic flops against the bf16 tensor peak are reported beside it.
+    # The dense blocks run on the tensor cores as 21 digit products per
+    # multiply-add (six 8-bit digits of H and of X, diagonals 0 to 5), in
+    # passes of at most 64 columns: their roof is the bf16 tensor peak for
+    # the MMA flops issued (128 rows x 16 positions per k-step of an entry,
+    # padding included); the fp64-equivalent 2R flop per entry is reported
+    # beside it.
+    rp_dense = sum((min(64, R - p0) + 15) // 16 * 16 for p0 in range(0, R, 64))
     per = {
         "mr_phase1": ("alu", 2.0 * R * inf["mr_v_elems"], FP32_TFLOPS, "derived fp32 FMA peak"),
         "mr_phase2": ("alu", 2.0 * R * inf["mr_u_elems"], FP32_TFLOPS, "derived fp32 FMA peak"),
-        "mr_dense": ("alu", 2.0 * R * inf["dense_elems"], DD_TFLOPS, "derived fp32-pair FMA peak"),
+        "tc_dense": ("tensor", 21 * 2.0 * rp_dense * inf["dense_tc_elems"], bf16, bf16_kind),
         "tc_phase1": ("hbm", 2.0 * R * inf["tc_v_elems"], bf16, bf16_kind),
         "tc_phase2": ("hbm", 2.0 * R * inf["tc_u_elems"], bf16, bf16_kind),
     }
@@ -787,7 +791,7 @@ def run_many(args):
     tcb = inf["tc_factor_bytes"]
     tcu = tcb * inf["tc_u_elems"] / max(1, inf["tc_u_elems"] + inf["tc_v_elems"])
     alg_bytes = {"mr_phase1": 4.0 * inf["mr_v_elems"], "mr_phase2": 4.0 * inf["mr_u_elems"],
-                 "mr_dense": 8.0 * inf["dense_elems"], "tc_phase1": tcb - tcu, "tc_phase2": tcu}
+                 "tc_dense": 8.0 * inf["dense_elems"], "tc_phase1": tcb - tcu, "tc_phase2": tcu}
     detail = {}
     for k, (bound, flops, peak, kind) in per.items():
         t = stages[k] * 1e-3
@@ -797,6 +801,9 @@ def run_many(args):
         if bound == "hbm":
             detail[k].update({"hbm_frac": detail[k]["operand_gbs"] / hbm if t > 0 else None,
                               "tensor_frac": tf / peak if t > 0 else None, "tensor_peak_kind": kind})
+        elif bound == "tensor":
+            detail[k].update({"peak_tflops": peak, "frac": tf / peak if t > 0 else None, "peak_kind": kind,
+                              "fp64_equiv_tflops": 2.0 * R * inf["dense_elems"] / t / 1e12 if t > 0 else None})
         else:
             detail[k].update({"peak_tflops": peak, "frac": tf / peak if t > 0 else None, "peak_kind": kind})
     dom = max(per, key=lambda k: stages[k])
@@ -857,7 +864,11 @@ def run_many(args):
                        "vs": "oracle Algorithm 4 (float64) over the same stored factors, sampled leaf-cluster rows, "
                              "all columns"})
         del G
-    launches = 2 + 6 + 1 + (3 * ((R + 3) // 4) if stages["fp64_streaming"] > 0.002 else 0)
+    # input images, tensor-core phase 1, dense input digits, dense blocks,
+    # tensor-core phase 2, output permutation; the CUDA-core phases where
+    # they have blocks; three streaming launches per 4 columns of fp64 blocks
+    launches = (6 + (inf["mr_v_elems"] > 0) + (inf["mr_u_elems"] > 0)
+                + (3 * ((R + 3) // 4) if stages["fp64_streaming"] > 0.002 else 0))
     out = {
         "metric": "H_h matvec right-hand sides/s (adaptive precision, many right-hand sides)",
         "value": value, "unit": "rhs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -865,8 +876,8 @@ def run_many(args):
         "dtype": "f32", "dtype_note": "tensor cores on exact bf16 slices with fp32 accumulation (fp32 factors "
                                       "and input: three slices, six products, accumulators drained every 64 terms; "
                                       "16/8-bit factors: two input slices, drained every 512 terms); CUDA-core fp32 "
-                                      "FMA for blocks on unaligned clusters; fp32 pairs for the fp64 dense diagonal; "
-                                      "fp64 output",
+                                      "FMA for blocks on unaligned clusters; fp64 dense diagonal on the tensor cores as "
+                                      "exact products of six 8-bit digits (about 2^-45 of sum |H||X|); fp64 output",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "n": n, "nrhs": R, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (%.2f GB of factors and dense blocks per step)"

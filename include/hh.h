@@ -113,7 +113,8 @@ typedef struct {
                                      {fwd phase 1, fwd phase 2, T phase 1, T phase 2};
                                      0 = the occupancy maximum                       */
   int64_t tc_panel_bytes[2];      /* device bytes held by the tensor-core operand
-                                     panels {forward, transpose}: 0 until the first
+                                     panels {forward, transpose} (factor slices and
+                                     dense-block digits): 0 until the first
                                      tensor-core product in that direction packs
                                      them                                           */
   int32_t tree_step;              /* binary levels per tree level: 1 for the KD tree,
@@ -126,6 +127,9 @@ typedef struct {
   int32_t stream_depth[4];        /* pipeline depth (stages per CTA) of one-column streaming
                                      launches per [direction][phase] (hh_autotune; default 4)  */
   int64_t item_bytes;             /* factor bytes of a streaming phase-1 item (hh_autotune)     */
+  int64_t dense_tc_elems;         /* operand elements of the dense blocks on the tensor cores
+                                     in the forward direction: 128 rows x 16 positions per
+                                     k-step of every tile entry (padding included)             */
 } hh_info_t;
 
 /*
@@ -293,8 +297,11 @@ int hh_perm(hh_handle h, int32_t* perm);
  * 2^-24 for fp32 blocks and below the unit roundoff of the 16- and 8-bit
  * formats; fp32 accumulation drained into round-to-nearest registers every
  * 64 terms for fp32 blocks, every 512 for the others), the other 32/16/8-bit
- * blocks on CUDA-core fp32 kernels, the dense blocks as fp32 pairs, the fp64
- * low-rank blocks on the streaming passes.  The first such call in each
+ * blocks on CUDA-core fp32 kernels, the dense blocks on the tensor cores as
+ * six exact 8-bit digits of their fp32-pair entries and of the input (one
+ * power of two per row and per right-hand side; digit products summed
+ * exactly, about 2^-45 of sum |H||x|), the fp64 low-rank blocks on the
+ * streaming passes.  The first such call in each
  * direction allocates the tensor-core workspace and the factor panels packed
  * for the tensor cores (hh_info tc_panel_bytes; an implicit device
  * synchronisation; HH_ENOMEM if they cannot be allocated).  Uses the
@@ -367,10 +374,11 @@ int hh_autotune(hh_handle h, int nrhs_many);
 
 /* hh_matvec_stages -- one product of 1 <= nrhs <= 128 right-hand sides
  * through the many-right-hand-side sequence (whatever nrhs), with CUDA events
- * around each launch; synchronises and writes ms[8] = {input images,
- * streaming passes over the fp64 low-rank blocks, CUDA-core phase 1,
- * tensor-core phase 1, CUDA-core phase 2, dense blocks, tensor-core phase 2,
- * output permutation}.  For measurement; uses the handle's workspaces. */
+ * around each launch; synchronises and writes ms[8] = {input images, dense
+ * blocks (input digits and the tensor-core kernel), streaming passes over the
+ * fp64 low-rank blocks, CUDA-core phase 1, tensor-core phase 1, CUDA-core
+ * phase 2, tensor-core phase 2, output permutation}.  For measurement; uses
+ * the handle's workspaces. */
 int hh_matvec_stages(hh_handle h, int transpose, const double* in, double* out, int nrhs,
                      int64_t ld_in, int64_t ld_out, void* stream, float* ms);
 

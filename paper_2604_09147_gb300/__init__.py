@@ -56,7 +56,7 @@ class _Info(ctypes.Structure):
         ("tc_panel_bytes", ctypes.c_int64 * 2), ("tree_step", ctypes.c_int32), ("pad_", ctypes.c_int32),
         ("build_device", ctypes.c_int32), ("pad2_", ctypes.c_int32), ("build_fallback", ctypes.c_int64),
         ("build_device_seconds", ctypes.c_double), ("stream_depth", ctypes.c_int32 * 4),
-        ("item_bytes", ctypes.c_int64),
+        ("item_bytes", ctypes.c_int64), ("dense_tc_elems", ctypes.c_int64),
     ]
 
 
@@ -327,8 +327,8 @@ class HMatrix:
     def matvec_stages(self, x: torch.Tensor, y: torch.Tensor, transpose: bool = False) -> list:
         """One product of up to 128 columns through the many-right-hand-side
         sequence with per-launch CUDA-event times in ms (synchronises):
-        [input images, fp64 streaming passes, CUDA-core phase 1, tensor-core
-        phase 1, CUDA-core phase 2, dense blocks, tensor-core phase 2, finish]."""
+        [input images, dense blocks, fp64 streaming passes, CUDA-core phase 1,
+        tensor-core phase 1, CUDA-core phase 2, tensor-core phase 2, finish]."""
         xv, nrhs, ldx, vec = _as_colmajor(x, self.n)
         ms = (ctypes.c_float * 8)()
         ldy = self.n if y.dim() == 1 else y.stride(1)

@@ -26,7 +26,7 @@ LIB = os.path.join(HERE, "libhh.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
 HOST_SRCS = ["builder.cpp", "linalg.cpp", "hhio.cpp", "shard.cpp"]
-CUDA_SRCS = ["kernels.cu", "stream.cu", "tc.cu", "mr.cu", "capi.cu", "construct.cu"]
+CUDA_SRCS = ["kernels.cu", "stream.cu", "tc.cu", "mr.cu", "dense_tc.cu", "capi.cu", "construct.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

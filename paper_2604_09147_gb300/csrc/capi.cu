@@ -81,10 +81,17 @@ struct MrSet {
   hh::dev::TcEntry* d_entries = nullptr;
   int n_pieces = 0, n_groups = 0, n_tiles = 0;
   int64_t t_floats = 0;
-  hh::dev::TcPiece* d_dpieces = nullptr;  // dense blocks
+  // dense blocks on the tensor cores (dense_tc.cu): 128-row tiles, their
+  // entries, and the digit panels and row exponents (allocated and packed
+  // on the first many-column product in this direction)
   hh::dev::TcTile* d_dtiles = nullptr;
-  hh::dev::TcEntry* d_dentries = nullptr;
-  int n_dtiles = 0;
+  hh::dev::TdEntry* d_dentries = nullptr;
+  int n_dtiles = 0, n_dentries = 0;
+  int64_t dimg_bytes = 0;
+  int64_t dx_bytes = 0;        // the input's digit panels of every entry (two passes)
+  int64_t dense_tc_elems = 0;  // 128 x 16 per k-step of every entry
+  uint8_t* d_dimg = nullptr;
+  int32_t* d_drexp = nullptr;
 };
 
 struct hh_matrix {
@@ -132,9 +139,10 @@ void free_many(hh_matrix* h, int d) {
   cudaFree(ms.d_groups);
   cudaFree(ms.d_tiles);
   cudaFree(ms.d_entries);
-  cudaFree(ms.d_dpieces);
   cudaFree(ms.d_dtiles);
   cudaFree(ms.d_dentries);
+  cudaFree(ms.d_dimg);
+  cudaFree(ms.d_drexp);
   ts = TcSet();
   ms = MrSet();
 }
@@ -615,7 +623,8 @@ void build_mr_set(hh_matrix* h, int dir, const std::vector<int64_t>& doff, const
   out.n_pieces = (int)pieces.size();
   out.n_groups = (int)gflat.size();
   out.n_tiles = (int)tiles.size();
-  // dense blocks
+  // dense blocks: 128-row tiles of the output, each block's share of a tile
+  // cut into entries of at most kTdMaxK contracted positions
   std::vector<TcPiece> dp;
   for (size_t q = 0; q < H.dense.size(); ++q) {
     const hh::DenseBlock& D = H.dense[q];
@@ -635,11 +644,45 @@ void build_mr_set(hh_matrix* h, int dir, const std::vector<int64_t>& doff, const
   }
   std::vector<TcTile> dt;
   std::vector<TcEntry> de;
-  build_tiles(H.n, kMrDenseRows, dp, [](const TcPiece& q) { return double(q.k) * 8; }, dt, de);
-  out.d_dpieces = upload(dp);
+  build_tiles(H.n, kTcRows, dp, [](const TcPiece& q) { return double(q.k) * 8; }, dt, de);
+  std::vector<TdEntry> te;
+  for (TcTile& t : dt) {
+    const int first = (int)te.size();
+    for (int i = 0; i < t.count; ++i) {
+      const TcEntry& e = de[size_t(t.first + i)];
+      const TcPiece& p = dp[size_t(e.piece)];
+      for (int k0 = 0; k0 < p.k; k0 += kTdMaxK) {
+        TdEntry x;
+        std::memset(&x, 0, sizeof(x));
+        x.d = reinterpret_cast<const float2*>(p.f2);
+        x.ld = p.ld2;
+        x.img = out.dimg_bytes;
+        x.src = e.src;
+        x.dst = e.dst;
+        x.nrows = e.nrows;
+        x.k0 = k0;
+        x.kc = std::min(kTdMaxK, p.k - k0);
+        x.in_off = p.in_off + k0;
+        x.e = p.e;
+        x.trans = p.pad;
+        // the first entry of the tile over these rows stores, later ones add
+        x.first = 1;
+        for (int q = first; q < (int)te.size(); ++q)
+          if (te[size_t(q)].dst < x.dst + x.nrows && x.dst < te[size_t(q)].dst + te[size_t(q)].nrows) x.first = 0;
+        x.xoff = out.dx_bytes;
+        out.dimg_bytes += int64_t((x.kc + 15) / 16) * kTdStepBytes;
+        out.dx_bytes += int64_t((x.kc + 15) / 16) * 2 * kTdXStepBytes;
+        out.dense_tc_elems += int64_t((x.kc + 15) / 16) * 128 * 16;
+        te.push_back(x);
+      }
+    }
+    t.first = first;
+    t.count = (int)te.size() - first;
+  }
   out.d_dtiles = upload(dt);
-  out.d_dentries = upload(de);
+  out.d_dentries = upload(te);
   out.n_dtiles = (int)dt.size();
+  out.n_dentries = (int)te.size();
 }
 
 // ---------------------------------------------------------------------------
@@ -807,9 +850,10 @@ size_t ws_layout(const hh_matrix* h, WsView* v, char* base, int R = hh::dev::kMa
 // for nr <= 4 right-hand sides; the products are added into acc [nr][npad]
 // (cleared by the prep launch).
 cudaError_t run_stream(hh_matrix* h, const StreamSet& set, const double* in, int64_t ld_in, int nr, double* acc,
-                       const WsView& w, cudaStream_t st, cudaEvent_t* ev) {
+                       const WsView& w, cudaStream_t st, cudaEvent_t* ev, bool clear_acc = true) {
   if (ev) cudaEventRecord(ev[0], st);
-  cudaError_t e = hh::dev::launch_prep(in, ld_in, nr, h->d_perm, h->H.n, h->npad, w.xs, w.xs_lo, acc, st, w.counters);
+  cudaError_t e = hh::dev::launch_prep(in, ld_in, nr, h->d_perm, h->H.n, h->npad, w.xs, w.xs_lo,
+                                       clear_acc ? acc : nullptr, st, w.counters);
   bool p1 = false;  // phase 1 launched: phase 2 may follow it as a programmatic dependent
   for (int phase = 1; phase <= 2 && e == cudaSuccess; ++phase) {
     if (ev) cudaEventRecord(ev[phase], st);
@@ -857,6 +901,8 @@ struct TcWs {
   float* xh;   // fp32 input images [npad][128] (mr.cu)
   float* xl;
   float* t32;  // T of the CUDA-core pieces
+  uint8_t* xdig;  // the input's digit panels of the dense blocks (dense_tc.cu)
+  int32_t* bexp;  // and their column exponents
 };
 
 size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
@@ -879,18 +925,23 @@ size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
   float* xl = (float*)take(sizeof(float) * 128 * h->npad);
   const int64_t tf = std::max(h->mr[0].t_floats, h->mr[1].t_floats);
   float* t32 = (float*)take(sizeof(float) * std::max<int64_t>(64, tf));
-  if (v) *v = {ximg, timg, part, cnt, acc, nblk, xh, xl, t32};
+  const int64_t dx = std::max(h->mr[0].dx_bytes, h->mr[1].dx_bytes);
+  const int64_t de = std::max(h->mr[0].n_dentries, h->mr[1].n_dentries);
+  uint8_t* xdig = (uint8_t*)take(std::max<size_t>(256, size_t(dx)));
+  int32_t* bexp = (int32_t*)take(sizeof(int32_t) * 128 * std::max<int64_t>(1, de));
+  if (v) *v = {ximg, timg, part, cnt, acc, nblk, xh, xl, t32, xdig, bexp};
   return off;
 }
 
 // Product for nrhs <= 128 right-hand sides in one pass over the blocks:
-// input images, the streaming passes over the fp64 low-rank blocks (chunks of
-// up to 4 right-hand sides), the CUDA-core and tensor-core phases 1, the
-// CUDA-core phase 2, the dense blocks, the tensor-core phase 2, and the output
-// permutation.  With ev (9 events) every launch is bracketed: [0] images,
-// [1] streaming passes, [2] CUDA-core phase 1, [3] tensor-core phase 1,
-// [4] CUDA-core phase 2, [5] dense blocks, [6] tensor-core phase 2,
-// [7] output permutation, [8] end.
+// input images, the dense blocks (first: they store into the cleared
+// accumulator), the streaming passes over the fp64 low-rank blocks (chunks
+// of up to 4 right-hand sides), the CUDA-core and tensor-core phases 1, the
+// CUDA-core and tensor-core phases 2, and the output permutation.  With ev
+// (9 events) every launch is bracketed: [0] images, [1] dense blocks,
+// [2] streaming passes, [3] CUDA-core phase 1, [4] tensor-core phase 1,
+// [5] CUDA-core phase 2, [6] tensor-core phase 2, [7] output permutation,
+// [8] end.
 cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr, int64_t ld_in, int64_t ld_out,
                    const WsView& w, const TcWs& t, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   auto mark = [&](int i) {
@@ -901,12 +952,34 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   const MrSet& ms = h->mr[dir];
   cudaError_t e = hh::dev::launch_tc_prep(in, ld_in, nr, h->d_perm, h->H.n, t.nblk, t.ximg, t.acc, h->npad, t.cnt,
                                           ts.n_cnt, t.xh, t.xl, h->npad, t.t32, ms.t_floats, st);
-  const StreamSet& rest = h->ss_rest[dir];
   mark(1);
+  {
+    hh::dev::TdArgs d;
+    std::memset(&d, 0, sizeof(d));
+    d.tiles = ms.d_dtiles;
+    d.entries = ms.d_dentries;
+    d.n_tiles = ms.n_dtiles;
+    d.nr = nr;
+    d.img = ms.d_dimg;
+    d.rexp = ms.d_drexp;
+    d.xh = t.xh;
+    d.xl = t.xl;
+    d.xdig = t.xdig;
+    d.bexp = t.bexp;
+    d.acc = t.acc;
+    d.npad = h->npad;
+    d.status = h->d_status;
+    if (e == cudaSuccess) e = hh::dev::launch_td_prep(d, ms.n_dentries, st);
+    if (e == cudaSuccess) e = hh::dev::launch_td(d, h->sms, st);
+  }
+  const StreamSet& rest = h->ss_rest[dir];
+  mark(2);
   if (rest.n_items[0] + rest.n_items[1] > 0)
     for (int rb = 0; rb < nr && e == cudaSuccess;) {
       const int rem = nr - rb, c = rem >= 4 ? 4 : (rem >= 2 ? 2 : 1);
-      e = run_stream(h, rest, in + int64_t(rb) * ld_in, ld_in, c, t.acc + int64_t(rb) * h->npad, w, st, nullptr);
+      // the accumulator already holds the dense blocks' results
+      e = run_stream(h, rest, in + int64_t(rb) * ld_in, ld_in, c, t.acc + int64_t(rb) * h->npad, w, st, nullptr,
+                     false);
       rb += c;
     }
   hh::dev::TcArgs a;
@@ -945,20 +1018,12 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   m.acc = t.acc;
   m.npad = h->npad;
   m.status = h->d_status;
-  hh::dev::MrArgs md = m;
-  md.pieces = ms.d_dpieces;
-  md.tiles = ms.d_dtiles;
-  md.entries = ms.d_dentries;
-  md.n_groups = 0;
-  md.n_tiles = ms.n_dtiles;
-  mark(2);
-  if (e == cudaSuccess) e = hh::dev::launch_mr(1, m, st);
   mark(3);
-  if (e == cudaSuccess) e = hh::dev::launch_tc(1, a, h->sms, st);
+  if (e == cudaSuccess) e = hh::dev::launch_mr(1, m, st);
   mark(4);
-  if (e == cudaSuccess) e = hh::dev::launch_mr(2, m, st);
+  if (e == cudaSuccess) e = hh::dev::launch_tc(1, a, h->sms, st);
   mark(5);
-  if (e == cudaSuccess) e = hh::dev::launch_mr(3, md, st);
+  if (e == cudaSuccess) e = hh::dev::launch_mr(2, m, st);
   mark(6);
   if (e == cudaSuccess) e = hh::dev::launch_tc(2, a, h->sms, st);
   mark(7);
@@ -1010,6 +1075,23 @@ int run_product(hh_matrix* h, int dir, const double* in, double* out, int nrhs, 
       h->tc_ws_bytes = tneed;
     }
     tc_ws_layout(h, &t, (char*)h->d_tc_ws);
+    MrSet& ms = h->mr[dir];
+    if (!ms.d_dimg && ms.dimg_bytes > 0) {
+      cudaStreamSynchronize(st);
+      if (cudaMalloc(&ms.d_dimg, size_t(ms.dimg_bytes)) != cudaSuccess ||
+          cudaMalloc(&ms.d_drexp, sizeof(int32_t) * 128 * size_t(ms.n_dentries)) != cudaSuccess) {
+        cudaFree(ms.d_dimg);
+        ms.d_dimg = nullptr;
+        ms.d_drexp = nullptr;
+        if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+        return fail(HH_ENOMEM, "cannot allocate the dense-block digit panels");
+      }
+      const cudaError_t pe = hh::dev::launch_td_pack(ms.d_dentries, ms.n_dentries, ms.d_dimg, ms.d_drexp, st);
+      if (pe != cudaSuccess) {
+        if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+        return fail(HH_ECUDA, std::string("dense panel packing failed: ") + cudaGetErrorString(pe));
+      }
+    }
     TcSet& ts = h->tc[dir];
     if (!ts.d_img && ts.img_bytes > 0) {
       cudaStreamSynchronize(st);
@@ -1360,11 +1442,13 @@ int hh_info(hh_handle h, hh_info_t* o) {
   o->split_positions = h->split_len;
   for (int d = 0; d < 2; ++d)
     for (int p = 1; p <= 2; ++p) o->blocks_per_sm[2 * d + p - 1] = h->blocks_per_sm[d][p];
-  for (int d = 0; d < 2; ++d) o->tc_panel_bytes[d] = h->tc[d].d_img ? h->tc[d].img_bytes : 0;
+  for (int d = 0; d < 2; ++d)
+    o->tc_panel_bytes[d] = (h->tc[d].d_img ? h->tc[d].img_bytes : 0) + (h->mr[d].d_dimg ? h->mr[d].dimg_bytes : 0);
   o->tree_step = H.step;
   o->build_device = H.build_device;
   o->build_fallback = H.build_fallback;
   o->build_device_seconds = H.build_device_seconds;
+  o->dense_tc_elems = h->mr[0].dense_tc_elems;
   for (int d = 0; d < 2; ++d)
     for (int p = 1; p <= 2; ++p) o->stream_depth[2 * d + p - 1] = h->ss[d].depth[p];
   o->item_bytes = h->item_bytes;

@@ -47,7 +47,8 @@ struct StreamArgs {
   int* counter;  // work counter of this pass (zeroed by the prep launch)
 };
 
-// host-callable launchers (kernels.cu, stream.cu)
+// host-callable launchers (kernels.cu, stream.cu); launch_prep clears acc
+// (nr columns) unless it is null
 cudaError_t launch_prep(const double* in, int64_t ld, int nr, const int32_t* perm, int64_t n,
                         int64_t npad, float* xs, float* xs_lo, double* acc, cudaStream_t st,
                         int* counters = nullptr);
@@ -138,6 +139,61 @@ __device__ __forceinline__ void batch_prep_position(int64_t p, const double* __r
     xs_lo[static_cast<int64_t>(s) * np + p] = __double2float_rn(v - static_cast<double>(hi));
   }
   acc[p] = 0.0;
+}
+// v 2^e as an fp64 value built from v's bits with integer operations (exact),
+// so that adding an fp32 result into an fp64 accumulator costs no instruction
+// on the low-rate fp64 units.  Subnormal, non-finite or out-of-range results
+// (rare) take fp64 arithmetic in a function that is not inlined, so that the
+// compiler cannot predicate its fp64 instructions into the common path.
+static __device__ __noinline__ double f32_to_f64_rare(float v, int e) { return ldexp(static_cast<double>(v), e); }
+__device__ __forceinline__ double f32_to_f64(float v, int e) {
+  const uint32_t b = __float_as_uint(v);
+  if ((b & 0x7fffffffu) == 0u) return 0.0;
+  const int ex = static_cast<int>((b >> 23) & 0xffu);
+  const int de = ex - 127 + 1023 + e;
+  if (ex == 0 || ex == 255 || de < 1 || de > 2046) return f32_to_f64_rare(v, e);
+  const unsigned long long bits = (static_cast<unsigned long long>(b & 0x80000000u) << 32) |
+                                  (static_cast<unsigned long long>(de) << 52) |
+                                  (static_cast<unsigned long long>(b & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+// (S + C) 2^e as an fp64 value from the bits of the fp32 values S and C with
+// 64-bit integer operations only: both significands aligned in units of
+// 2^-32 of the larger one's exponent, added, normalised to 53 bits
+// (truncating below 2^-52 of the sum) and packed.  Returns false, leaving
+// out untouched, for zero, subnormal or non-finite inputs and out-of-range
+// results; the caller handles those (rare) with pair_to_f64_rare outside its
+// hot loop, so that no fp64 instruction is predicated into it.
+__device__ __forceinline__ bool pair_to_f64_fast(float S, float C, int e, double& out) {
+  if (fabsf(C) > fabsf(S)) {
+    const float t = S;
+    S = C;
+    C = t;
+  }
+  const uint32_t bs = __float_as_uint(S), bc = __float_as_uint(C);
+  if ((bs & 0x7fffffffu) == 0u) {  // both zero
+    out = 0.0;
+    return true;
+  }
+  const int es = static_cast<int>((bs >> 23) & 0xffu), ec = static_cast<int>((bc >> 23) & 0xffu);
+  long long ms = static_cast<long long>((bs & 0x7fffffu) | 0x800000u);
+  long long mc = static_cast<long long>((bc & 0x7fffffu) | 0x800000u);
+  if (bs >> 31) ms = -ms;
+  if (bc >> 31) mc = -mc;
+  if (ec == 0) mc = 0;  // C zero (or subnormal: below 2^-126, dropped only if S is normal)
+  const int d = es - ec;
+  const long long sum = ms * (1LL << 32) + (d <= 32 ? mc * (1LL << (32 - d)) : (d < 56 ? (mc >> (d - 32)) : 0LL));
+  const unsigned long long sign = sum < 0 ? 1ull : 0ull;
+  const unsigned long long mag = static_cast<unsigned long long>(sum < 0 ? -sum : sum);
+  const int sh = 11 - __clzll(static_cast<long long>(mag));
+  const unsigned long long mant = sh >= 0 ? (mag >> sh) : (mag << -sh);
+  const int de = es - 130 + sh + 1023 + e;
+  out = __longlong_as_double(
+      static_cast<long long>((sign << 63) | (static_cast<unsigned long long>(de) << 52) | (mant & 0xfffffffffffffull)));
+  return es != 0 && es != 255 && ec != 255 && mag != 0 && de >= 1 && de <= 2046;
+}
+static __device__ __noinline__ double pair_to_f64_rare(float S, float C, int e) {
+  return ldexp(static_cast<double>(S) + static_cast<double>(C), e);
 }
 // position p of a batch's output: y in each matrix's caller order
 __device__ __forceinline__ void batch_finish_position(int64_t p, const double* __restrict__ acc,
@@ -262,13 +318,53 @@ cudaError_t launch_tc_pack(const TcPiece* pieces, const TcGroup* groups, int n_g
 // phase 1 or 2 over every group / tile; grid: persistent CTAs (<= SMs)
 cudaError_t launch_tc(int phase, const TcArgs& a, int grid, cudaStream_t st);
 
+// ---- dense blocks for many right-hand sides on the tensor cores (dense_tc.cu) ----
+// One dense block's share of a 128-row output tile, over at most
+// kTdMaxK contracted positions.  Forward: A[m][k] = H[src + m - dst][k0 + k];
+// transposed: A[m][k] = H[k0 + k][src + m - dst]; H is column-major with
+// leading dimension ld, held as fp32 pairs (hi, lo) of its value times 2^-e.
+struct TdEntry {
+  const float2* d;
+  int64_t ld;
+  int64_t img;          // byte offset of the packed digit panel [k-step][6 digits][128 rows x 32 B]
+  int64_t xoff;         // byte offset of the input's digit panel [pass][k-step][6 digits][64 rows x 32 B]
+  int32_t src, dst, nrows;
+  int32_t in_off;       // tree position of contracted position k0
+  int32_t k0, kc;       // contracted positions k0 .. k0 + kc - 1 (kc <= kTdMaxK)
+  int32_t e, trans;
+  int32_t first;        // 1: no earlier entry of the tile covers these rows (store, not add)
+  int32_t pad;
+};
+struct TdArgs {
+  const TcTile* tiles;      // row0, rows, first, count (entries [first, first + count))
+  const TdEntry* entries;
+  int32_t n_tiles, nr;      // tiles; right-hand sides of this launch (<= 128)
+  const uint8_t* img;       // packed digit panels of H
+  const int32_t* rexp;      // [entry][128]: power of two of tile row m's digits
+  const float* xh;          // input, tree order, fp32 leading halves [npos][128] (td_prep)
+  const float* xl;          // trailing halves
+  uint8_t* xdig;            // the input's digit panels (written by td_prep, read by td_kernel)
+  int32_t* bexp;            // [entry][128]: b_r - 7 of right-hand side r's digits
+  double* acc;              // output accumulator [nr][npad], tree order, all zero before
+                            // the launch (the first entry over a row stores into it)
+  int64_t npad;
+  int* status;              // bit 3: a bounded wait expired
+};
+constexpr int kTdMaxK = 128;       // contracted positions of one entry
+constexpr int kTdDigits = 6;       // digits per value (8 bits each)
+constexpr int64_t kTdStepBytes = int64_t(kTdDigits) * 4096;  // one k-step of an H digit panel
+constexpr int64_t kTdXStepBytes = int64_t(kTdDigits) * 2048; // one k-step of an input digit panel (64 columns)
+// digit panels of the entries [0, n) (one CTA per entry) and their row exponents
+cudaError_t launch_td_pack(const TdEntry* entries, int n, uint8_t* img, int32_t* rexp, cudaStream_t st);
+// the input's digit panels and column exponents of every entry (n_entries CTAs)
+cudaError_t launch_td_prep(const TdArgs& a, int n_entries, cudaStream_t st);
+// Y += H X over every tile; grid: persistent CTAs (<= SMs)
+cudaError_t launch_td(const TdArgs& a, int grid, cudaStream_t st);
+
 // ---- CUDA-core products for many right-hand sides (mr.cu) ----
 // Work lists in the tensor-core structures: phase-1 groups of at most
 // kMrRanks ranks (pieces with kp = ranks rounded up to 4, T at toff floats,
-// [rank][128]); phase-2 tiles of kMrRows rows; dense tiles of 64 rows whose
-// pieces are dense blocks (f2 = the fp64 block, ld2, k = the contracted
-// dimension, in_off its cluster offset, e = the power of two that undoes the
-// stored scale, pad = 1 for the transposed block).
+// [rank][128]); phase-2 tiles of kMrRows rows.
 struct MrArgs {
   const TcPiece* pieces;
   const TcGroup* groups;
@@ -285,8 +381,7 @@ struct MrArgs {
 };
 constexpr int kMrRanks = 64;
 constexpr int kMrRows = 128;
-constexpr int kMrDenseRows = 64;
-// kind 1: phase 1, 2: phase 2, 3: dense blocks
+// kind 1: phase 1, 2: phase 2
 cudaError_t launch_mr(int kind, const MrArgs& a, cudaStream_t st);
 
 }  // namespace dev

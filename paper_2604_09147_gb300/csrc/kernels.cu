@@ -4,8 +4,8 @@
 //            its fp32 leading half hi = fl32(x) and trailing half
 //            lo = fl32(x - hi), each in four copies shifted by 0..3 positions
 //            so that every 16-byte vector of a factor column meets an aligned
-//            vector of the input; clears the fp64 output accumulator and the
-//            work counters of the two passes.
+//            vector of the input; clears the fp64 output accumulator (unless
+//            it is passed as null) and the work counters of the two passes.
 //   finish : output accumulator (tree order) -> the caller's order, through
 //            the inverse permutation (caller position -> tree position).
 //   presplit: fp64 factors and dense blocks -> pairs of fp32 values, once
@@ -39,7 +39,7 @@ __global__ void prep_kernel(const double* __restrict__ in, int64_t ld, int nr,
           xs_lo[(static_cast<int64_t>(s) * nr + r) * npad + p] = lo;
         }
       }
-      if (q < npad) acc[static_cast<int64_t>(r) * npad + q] = 0.0;
+      if (acc && q < npad) acc[static_cast<int64_t>(r) * npad + q] = 0.0;
     }
   }
 }

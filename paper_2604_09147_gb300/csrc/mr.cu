@@ -13,12 +13,7 @@
 //   mr_phase2  Y_I += U_b T_b for the same blocks: one CTA per 128-row output
 //              tile over every such block covering it; a thread holds 8 rows
 //              x RPT right-hand sides.
-//   mr_dense   Y_I += H_IJ X_J (or H_JI^T) for the fp64 dense blocks: one CTA
-//              per 64-row output tile; every product is formed from fp32
-//              leading and trailing halves of the fp64 entry and input and
-//              accumulated as an unevaluated fp32 pair (about 2^-44 relative),
-//              so the dense blocks keep the fp64 path's accuracy.
-// The tiles of phase 2 and of the dense kernel add into the fp64 output
+// The tiles of phase 2 add into the fp64 output
 // accumulator with plain read-modify-writes: within one launch every output
 // row belongs to one CTA, and launches are ordered on the stream.  Operands
 // are staged through shared memory with register double buffering (the loads
@@ -38,7 +33,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kK1 = 32;       // positions per phase-1 stage
 constexpr int kK2 = 16;       // ranks (dense: K columns) per phase-2 stage
-constexpr int kDenseRows = 64;
 
 constexpr int kF32 = 1, kBF16 = 3, kE4M3 = 4;
 
@@ -321,148 +315,6 @@ __global__ void __launch_bounds__(kThreads, 2) mr_phase2(MrArgs a) {
   add_tile<RPT, kMrRows, 8>(a, tl, sm2, acc, tr, tc);
 }
 
-// ------------------------------------------------------------------ dense blocks
-// a dense entry held as an fp32 pair (hi, lo) of its value times 2^-e, times
-// 2^e: exact scaling in fp32 when 2^e is a normal fp32 number (the builder's
-// scales are), else through fp64
-__device__ __forceinline__ void pair_scaled(float2 v, int e, float& hi, float& lo) {
-  if (e >= -126 && e <= 127) {
-    const float sc = __int_as_float((127 + e) << 23);
-    hi = v.x * sc;
-    lo = v.y * sc;
-  } else {
-    const double d = ldexp(static_cast<double>(v.x) + static_cast<double>(v.y), e);
-    hi = __double2float_rn(d);
-    lo = __double2float_rn(d - static_cast<double>(hi));
-  }
-}
-
-// S + C += (ah + al)(bh + bl): the leading product exactly (fma error term),
-// the cross terms in fp32, the sum kept as an unevaluated pair (two-sum)
-__device__ __forceinline__ void dd_fma(float& S, float& C, float ah, float al, float bh, float bl) {
-  const float p = ah * bh;
-  const float pe = fmaf(ah, bh, -p);
-  const float cr = fmaf(ah, bl, fmaf(al, bh, pe));
-  const float t = S + p;
-  const float bp = t - S;
-  const float err = (S - (t - bp)) + (p - bp);
-  S = t;
-  C += err + cr;
-}
-
-template <int RPT>
-__global__ void __launch_bounds__(kThreads, 2) mr_dense(MrArgs a) {
-  constexpr int RP = 16 * RPT;
-  extern __shared__ __align__(16) float sm3[];
-  float* sDh = sm3;                              // [2][kK2][64]
-  float* sDl = sDh + 2 * kK2 * kDenseRows;
-  float* sXh = sDl + 2 * kK2 * kDenseRows;       // [2][kK2][RP]
-  float* sXl = sXh + 2 * kK2 * RP;
-  const TcTile tl = a.tiles[blockIdx.x];
-  const int tid = threadIdx.x;
-  int nst = 0;
-  for (int e = 0; e < tl.count; ++e) nst += (a.pieces[a.entries[tl.first + e].piece].k + kK2 - 1) / kK2;
-  // loader roles: D entries (k = tid >> 4, rows 4 (tid & 15) .. +3); X units
-  const int dk = tid >> 4, dm = tid & 15;
-  constexpr int XU = kK2 * RP / 4 / kThreads > 0 ? kK2 * RP / 4 / kThreads : 1;
-  float dh[4], dl[4];
-  float4 xh[XU], xl[XU];
-  Cur lc{0, 0};
-  auto load = [&]() {
-    const TcEntry en = a.entries[tl.first + lc.e];
-    const TcPiece& q = a.pieces[en.piece];
-    const float2* D = reinterpret_cast<const float2*>(q.f2);  // fp64 entries as fp32 pairs
-    const int k = kK2 * lc.chunk + dk;
-    const bool trans = q.pad != 0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int m = 4 * dm + t;
-      float2 d = make_float2(0.f, 0.f);
-      if (k < q.k && m >= en.dst && m < en.dst + en.nrows) {
-        const int64_t row = en.src + (m - en.dst);
-        d = __ldg(D + (trans ? row * q.ld2 + k : static_cast<int64_t>(k) * q.ld2 + row));
-      }
-      pair_scaled(d, q.e, dh[t], dl[t]);
-    }
-#pragma unroll
-    for (int h = 0; h < XU; ++h) {
-      const int u = tid + h * kThreads;
-      float4 vh = make_float4(0.f, 0.f, 0.f, 0.f), vl = vh;
-      if (u < kK2 * RP / 4) {
-        const int r = u / (RP / 4), c4 = u - r * (RP / 4), kk = kK2 * lc.chunk + r;
-        if (kk < q.k) {
-          const int64_t off = (static_cast<int64_t>(q.in_off) + kk) * 128 + 4 * c4;
-          vh = *reinterpret_cast<const float4*>(a.xh + off);
-          vl = *reinterpret_cast<const float4*>(a.xl + off);
-        }
-      }
-      xh[h] = vh;
-      xl[h] = vl;
-    }
-    if (++lc.chunk == (q.k + kK2 - 1) / kK2) {
-      lc.chunk = 0;
-      ++lc.e;
-    }
-  };
-  auto store = [&](int buf) {
-    *reinterpret_cast<float4*>(sDh + (buf * kK2 + dk) * kDenseRows + 4 * dm) = make_float4(dh[0], dh[1], dh[2], dh[3]);
-    *reinterpret_cast<float4*>(sDl + (buf * kK2 + dk) * kDenseRows + 4 * dm) = make_float4(dl[0], dl[1], dl[2], dl[3]);
-#pragma unroll
-    for (int h = 0; h < XU; ++h) {
-      const int u = tid + h * kThreads;
-      if (u < kK2 * RP / 4) {
-        const int r = u / (RP / 4), c4 = u - r * (RP / 4);
-        *reinterpret_cast<float4*>(sXh + (buf * kK2 + r) * RP + 4 * c4) = xh[h];
-        *reinterpret_cast<float4*>(sXl + (buf * kK2 + r) * RP + 4 * c4) = xl[h];
-      }
-    }
-  };
-  const int tr = tid >> 4, tc = tid & 15;
-  float S[4][RPT], C[4][RPT];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int e = 0; e < RPT; ++e) S[i][e] = C[i][e] = 0.f;
-  if (nst > 0) {
-    load();
-    store(0);
-  }
-  __syncthreads();
-  for (int i = 0; i < nst; ++i) {
-    const int buf = i & 1;
-    if (i + 1 < nst) load();
-#pragma unroll 2
-    for (int k = 0; k < kK2; ++k) {
-      const float4 h4 = *reinterpret_cast<const float4*>(sDh + (buf * kK2 + k) * kDenseRows + 4 * tr);
-      const float4 l4 = *reinterpret_cast<const float4*>(sDl + (buf * kK2 + k) * kDenseRows + 4 * tr);
-      float bh[RPT], bl[RPT];
-      load_x<RPT>(sXh + (buf * kK2 + k) * RP, tc, bh);
-      load_x<RPT>(sXl + (buf * kK2 + k) * RP, tc, bl);
-      const float ah[4] = {h4.x, h4.y, h4.z, h4.w}, al[4] = {l4.x, l4.y, l4.z, l4.w};
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int e = 0; e < RPT; ++e) dd_fma(S[r][e], C[r][e], ah[r], al[r], bh[e], bl[e]);
-    }
-    if (i + 1 < nst) store(buf ^ 1);
-    __syncthreads();
-  }
-  float acc[4][RPT];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int e = 0; e < RPT; ++e) acc[r][e] = S[r][e] + C[r][e];
-  // the sum of the pair is rounded to fp32 here only for the transpose through
-  // shared memory: add the trailing part separately to keep it
-  add_tile<RPT, kDenseRows, 4>(a, tl, sm3, acc, tr, tc);
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int e = 0; e < RPT; ++e) acc[r][e] = C[r][e] - (acc[r][e] - S[r][e]);
-  add_tile<RPT, kDenseRows, 4>(a, tl, sm3, acc, tr, tc);
-}
-
-
 template <int RPT>
 cudaError_t launch_rpt(int kind, const MrArgs& a, cudaStream_t st) {
   constexpr int RP = 16 * RPT;
@@ -470,14 +322,10 @@ cudaError_t launch_rpt(int kind, const MrArgs& a, cudaStream_t st) {
     const size_t smem = sizeof(float) * (2 * kK1 * kVRow + 2 * kK1 * RP);
     cudaError_t e = cudaFuncSetAttribute(mr_phase1<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) mr_phase1<RPT><<<a.n_groups, kP1Threads, smem, st>>>(a);
-  } else if (kind == 2) {
+  } else {
     const size_t smem = sizeof(float) * std::max(2 * kK2 * (kMrRows + RP), kMrRows * (std::min(RP, 64) + 1));
     cudaError_t e = cudaFuncSetAttribute(mr_phase2<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) mr_phase2<RPT><<<a.n_tiles, kThreads, smem, st>>>(a);
-  } else {
-    const size_t smem = sizeof(float) * std::max(4 * kK2 * (kDenseRows + RP), kDenseRows * (std::min(RP, 64) + 1));
-    cudaError_t e = cudaFuncSetAttribute(mr_dense<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) mr_dense<RPT><<<a.n_tiles, kThreads, smem, st>>>(a);
   }
   return cudaGetLastError();
 }

@@ -14,7 +14,8 @@
 //            (an atomic counter, nothing waits) adds them in split order.
 //   phase 2  items are 128-row output tiles: D[row][r] = sum over the blocks
 //            covering the tile and their ranks of U[row][j] T[j][r], N = R,
-//            added once into the fp64 output accumulator.
+//            added once into the fp64 output accumulator (fire-and-forget
+//            fp64 reductions in L2: the drain warps wait on no load).
 //
 // Operands.  The factors are packed once per matrix and direction into bf16
 // slices laid out exactly as the MMAs read them (tc_pack below): a phase-1
@@ -662,7 +663,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
       if (!ok || nst == 0 || row >= tl.rows) continue;
 #pragma unroll
       for (int j = 0; j < 128; ++j)
-        if (j < a.nr) a.acc[static_cast<int64_t>(j) * a.npad + tl.row0 + row] += static_cast<double>(acc[j]);
+        if (j < a.nr) atomicAdd(a.acc + static_cast<int64_t>(j) * a.npad + tl.row0 + row, f32_to_f64(acc[j], 0));
     }
   }
   ws_teardown(c, produced, mmas, a.status);

@@ -253,3 +253,34 @@ def test_many_rhs_tiny_matrices(P, tmp_path, n, leaf):
         ref = M.matvec_T(O, x) if tr else M.matvec(O, x)
         ab = abs_product(O, x, tr)
         assert np.linalg.norm(y - ref) <= TOL * np.linalg.norm(ref) + np.linalg.norm(ab)
+
+
+@pytest.mark.parametrize("leaf,ell", [(64, 5), (256, 1)])
+def test_many_rhs_dense_entries_fp64(P, tmp_path, leaf, ell):
+    """The dense blocks on the tensor cores where several entries meet the same
+    output rows: with the switch level at the leaves (2,048 points, leaf 64,
+    L = 5) the leaf neighbours stay dense, so a row has several dense blocks;
+    with leaf 256 every block is split over two entries of 128 contracted
+    positions.  The later entries load and add, the first one stores.  The
+    input's magnitude varies by 2^40 over positions and columns, so the
+    exponents of the digits (one per row, one per right-hand side and entry)
+    are exercised; the fp64 path's 1e-12 holds for every column."""
+    from oracle import build as OB
+    n = 2048
+    pts = W.points(n, 2, 9100 + leaf)
+    O = OB.build(pts, W.EXP, 1.0, leaf, 1.0, ell, 1e-10, W.F64)
+    assert any(d.row_off != d.col_off for d in O.dense) or max(d.m for d in O.dense) > 128
+    path = str(tmp_path / "d.hhm")
+    hhfile.write(O, path)
+    H = P.HMatrix.load(path, 0)
+    nrhs = 40
+    p = np.arange(n)[:, None]
+    j = np.arange(nrhs)[None, :]
+    x = W.rhs(n, nrhs, "uniform", 9200 + leaf) * 2.0 ** (((p * 37 + j * 11) % 41) - 20)
+    xg = torch.from_numpy(np.ascontiguousarray(x.T)).cuda().t()
+    for tr in (False, True):
+        y = H.matvec(xg, transpose=tr).cpu().numpy()
+        H.sync_status()
+        ref = M.matvec_T(O, x) if tr else M.matvec(O, x)
+        cols = np.linalg.norm(y - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        assert cols.max() <= 1e-12, cols.max()

@@ -71,7 +71,9 @@ namespace {
 constexpr long long kWaitCycles = 4000000000LL;
 constexpr int kThreads = 192;
 constexpr int kKS = kTcKSteps;           // K steps per stage
-constexpr int kDepth = 4;
+constexpr int kDepth = 2;         // stages per CTA
+constexpr int kCtasPerSm = 2;     // two CTAs per SM: two bulk-copy queues, two MMA issuers
+constexpr int kBanks = 1;         // accumulator banks per CTA (256 tensor-memory columns each)
 // a stage: kKS K steps of the A operand (phase 1: X slices [3][128 x 32 B]
 // per step; phase 2: U slices [sf][128 x 32 B] per step), then kKS K steps of
 // the B operand (phase 1: V slices [sf][nk x 32 B]; phase 2: T slices
@@ -79,7 +81,7 @@ constexpr int kDepth = 4;
 constexpr int kOpA = kKS * 3 * 4096;
 constexpr int kOpB = kKS * 3 * 4096;
 constexpr int kStage = kOpA + kOpB;
-constexpr uint32_t kTmemCols = 512;      // bank b: main at 256 b, corrections at 256 b + 128
+constexpr uint32_t kTmemCols = 256 * kBanks;  // bank b: main at 256 b, corrections at 256 b + 128
 // Stages whose K steps add into one bank before it is drained
 // (kTcChunkF32 / kTcChunk16).  Each MMA's addition into an fp32 accumulator
 // truncates (at most one unit in the last place of the running sum), so over
@@ -246,7 +248,7 @@ __device__ __forceinline__ int item_of(int k, int n_items) {
 
 struct Ctl {
   uint64_t full[kDepth], empty[kDepth];
-  uint64_t bfull[2], bempty[2];
+  uint64_t bfull[kBanks], bempty[kBanks];
   uint32_t tmem;
   int abort;
 };
@@ -281,7 +283,7 @@ __device__ __forceinline__ void ws_setup(Ctl* c) {
       mbar_init(&c->full[s], 1);
       mbar_init(&c->empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kBanks; ++b) {
       mbar_init(&c->bfull[b], 1);
       mbar_init(&c->bempty[b], 4);
     }
@@ -318,25 +320,20 @@ __device__ __forceinline__ void ws_teardown(Ctl* c, int produced, int mmas, int*
 }
 
 // drain warps: add bank b (this warp's lane quarter, columns 0 .. ncols) into
-// acc, 32 columns (main and corrections) per tcgen05.wait::ld
+// acc, 16 columns (main and corrections) per tcgen05.wait::ld
 __device__ __forceinline__ void drain(const Ctl* c, int bank, int ncols, float* acc) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int w = threadIdx.x >> 5;
   const uint32_t t = c->tmem + (static_cast<uint32_t>(32 * (w & 3)) << 16) + 256 * bank;
 #pragma unroll
-  for (int cb = 0; cb < 4; ++cb) {
-    if (32 * cb < ncols) {
-      uint32_t h0[16], h1[16], l0[16], l1[16];
-      tmem_ld16_nowait(t + 32 * cb, h0);
-      tmem_ld16_nowait(t + 32 * cb + 16, h1);
-      tmem_ld16_nowait(t + 128 + 32 * cb, l0);
-      tmem_ld16_nowait(t + 128 + 32 * cb + 16, l1);
+  for (int cb = 0; cb < 8; ++cb) {
+    if (16 * cb < ncols) {
+      uint32_t h0[16], l0[16];
+      tmem_ld16_nowait(t + 16 * cb, h0);
+      tmem_ld16_nowait(t + 128 + 16 * cb, l0);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        acc[32 * cb + j] += __uint_as_float(h0[j]) + __uint_as_float(l0[j]);
-        acc[32 * cb + 16 + j] += __uint_as_float(h1[j]) + __uint_as_float(l1[j]);
-      }
+      for (int j = 0; j < 16; ++j) acc[16 * cb + j] += __uint_as_float(h0[j]) + __uint_as_float(l0[j]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -363,7 +360,7 @@ __device__ __forceinline__ const TcPiece& piece_at(const TcArgs& a, const TcGrou
 }
 
 // ------------------------------------------------------------------ phase 1
-__global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) tc_phase1(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align128(smem_raw);
   Ctl* c = reinterpret_cast<Ctl*>(base + kDepth * kStage);
@@ -384,7 +381,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
         const TcGroup g = gn;
         itn = item_of(k + 1, a.n_groups);
         if (itn >= 0) gn = a.groups[itn];
-        const uint32_t xbytes = tc_input_slices(g.fmt) * 4096u;
         const uint32_t vbytes = tc_factor_slices(g.fmt) * static_cast<uint32_t>(g.nk) * 32u;
         const int nblk = (g.p1 - g.p0 + 15) >> 4, nst = (nblk + kKS - 1) / kKS;
         for (int i = 0; i < nst; ++i, ++gs) {
@@ -397,8 +393,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
           // 16-position blocks b0 .. b0 + nb - 1 of the cluster
           const int b0 = (g.p0 >> 4) + kKS * i, nb = min(kKS, nblk - kKS * i);
           const int64_t blk = (static_cast<int64_t>(g.in_off) >> 4) + b0;
-          mbar_expect_tx(&c->full[s], nb * (xbytes + vbytes));
-          for (int t = 0; t < nb; ++t) bulk_copy(st + t * (3 * 4096), a.ximg + (blk + t) * (3 * 4096), xbytes, &c->full[s]);
+          // the stage's input blocks with all three slices in one copy (the
+          // 16- and 8-bit groups read two of them): a CTA's bulk copies run
+          // one after another, so fewer and larger copies fill faster
+          mbar_expect_tx(&c->full[s], nb * (3u * 4096u + vbytes));
+          bulk_copy(st, a.ximg + blk * (3 * 4096), nb * (3u * 4096u), &c->full[s]);
           bulk_copy_once(st + kOpA, a.img + g.img + static_cast<int64_t>(b0) * vbytes, nb * vbytes, &c->full[s], pol);
           produced = gs + 1;
         }
@@ -425,13 +424,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
           // chunks of L stages alternate between the banks: a chunk's first
           // K step starts fresh accumulators, the others add to them, then
           // the bank is handed to the drain warps
-          const int b = gp & 1;
+          const int b = gp % kBanks;
           if (!ws_wait(&c->full[s], par, abort)) {
             ok = false;
             break;
           }
           if (j == 0) {
-            if (gp >= 2 && !ws_wait(&c->bempty[b], ((gp >> 1) - 1) & 1, abort)) {
+            if (gp >= kBanks && !ws_wait(&c->bempty[b], ((gp / kBanks) - 1) & 1, abort)) {
               ok = false;
               break;
             }
@@ -473,8 +472,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
 #pragma unroll
       for (int j = 0; j < 128; ++j) acc[j] = 0.f;
       for (int q = 0; q < nchunks; ++q, ++gp) {
-        const int b = gp & 1;
-        if (!ws_wait(&c->bfull[b], (gp >> 1) & 1, abort)) {
+        const int b = gp % kBanks;
+        if (!ws_wait(&c->bfull[b], (gp / kBanks) & 1, abort)) {
           ok = false;
           break;
         }
@@ -539,7 +538,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase1(TcArgs a) {
 }
 
 // ------------------------------------------------------------------ phase 2
-__global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) tc_phase2(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align128(smem_raw);
   Ctl* c = reinterpret_cast<Ctl*>(base + kDepth * kStage);
@@ -603,13 +602,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
           const int np = n_products(fmt);
           const uint32_t ustep = tc_factor_slices(fmt) * 256u, tstep = tc_input_slices(fmt) * 256u;
           for (int ks = 0; ks < nks; ks += kKS, ++i, ++gs) {
-            const int b = gp & 1;
+            const int b = gp % kBanks;
             if (!ws_wait(&c->full[s], par, abort)) {
               ok = false;
               break;
             }
             if (j == 0) {
-              if (gp >= 2 && !ws_wait(&c->bempty[b], ((gp >> 1) - 1) & 1, abort)) {
+              if (gp >= kBanks && !ws_wait(&c->bempty[b], ((gp / kBanks) - 1) & 1, abort)) {
                 ok = false;
                 break;
               }
@@ -651,8 +650,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_phase2(TcArgs a) {
 #pragma unroll
       for (int j = 0; j < 128; ++j) acc[j] = 0.f;
       for (int q = 0; q < (nst + L - 1) / L; ++q, ++gp) {
-        const int b = gp & 1;
-        if (!ws_wait(&c->bfull[b], (gp >> 1) & 1, abort)) {
+        const int b = gp % kBanks;
+        if (!ws_wait(&c->bfull[b], (gp / kBanks) & 1, abort)) {
           ok = false;
           break;
         }
@@ -788,6 +787,7 @@ cudaError_t launch_tc(int phase, const TcArgs& a, int grid, cudaStream_t st) {
   if (a.rp < 16 || a.rp > 128 || (a.rp & 15)) return cudaErrorInvalidValue;
   const int n = phase == 1 ? a.n_groups : a.n_tiles;
   if (n <= 0) return cudaSuccess;
+  grid *= kCtasPerSm;  // grid: SMs
   if (grid > n) grid = n;
   if (grid < 1) grid = 1;
   const size_t smem = kDepth * kStage + 128 + sizeof(Ctl);

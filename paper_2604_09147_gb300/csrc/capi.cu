@@ -1700,7 +1700,7 @@ int hh_autotune(hh_handle h, int nrhs_many) {
   if (rc == HH_OK && nrhs_many > 0) {
     int best_s = h->split_len;
     float best = 1e30f;
-    for (int split : {256, 512, 1024, 2048, 4096}) {
+    for (int split : {512, 1024, 2048, 4096, 8192, 16384}) {
       h->split_len = split;
       try {
         rebuild_many(h);

@@ -273,6 +273,14 @@ def test_many_rhs_dense_entries_fp64(P, tmp_path, leaf, ell):
     path = str(tmp_path / "d.hhm")
     hhfile.write(O, path)
     H = P.HMatrix.load(path, 0)
+    # hh_info's count of the tensor-core dense work: per 128-row tile, each
+    # dense block meeting it, in entries of at most 128 contracted positions,
+    # 128 x 16 operand elements per k-step of 16 positions
+    ksteps = 0
+    for d in O.dense:
+        tiles = range(d.row_off // 128, (d.row_off + d.m - 1) // 128 + 1)
+        ksteps += len(tiles) * sum((min(128, d.n - k0) + 15) // 16 for k0 in range(0, d.n, 128))
+    assert H.info()["dense_tc_elems"] == ksteps * 128 * 16
     nrhs = 40
     p = np.arange(n)[:, None]
     j = np.arange(nrhs)[None, :]

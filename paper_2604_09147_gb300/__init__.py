@@ -305,11 +305,19 @@ class HMatrix:
                                  self.n, base, nb, _stream_ptr(x.device)))
         return out[:, 0] if vec else out
 
-    def matvec_host(self, x: np.ndarray, transpose: bool = False) -> np.ndarray:
-        """End-to-end product from host memory (copies inside the call)."""
+    def matvec_host(self, x: np.ndarray, transpose: bool = False, out: np.ndarray | None = None) -> np.ndarray:
+        """End-to-end product from host memory (copies inside the call).  out:
+        an optional column-major float64 array of x's shape to write into
+        (page-locked memory, e.g. a pinned torch tensor's numpy view, lets the
+        device-to-host copy run at full speed)."""
         xa = np.asfortranarray(x, dtype=np.float64)
         nrhs = 1 if xa.ndim == 1 else xa.shape[1]
-        y = np.empty_like(xa, order="F")
+        if out is None:
+            y = np.empty_like(xa, order="F")
+        else:
+            if out.shape != xa.shape or out.dtype != np.float64 or not out.flags.f_contiguous:
+                raise ValueError("out must be a column-major float64 array of x's shape")
+            y = out
         st = _stream_ptr(self.device) if self.device >= 0 else 0
         _check(_L().hh_matvec_host(self._h, 1 if transpose else 0, xa.ctypes.data, y.ctypes.data, nrhs, st))
         return y

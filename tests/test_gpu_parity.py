@@ -283,8 +283,12 @@ def test_host_api_and_batched(P, tmp_path):
     for H, O, x, y in zip(mats, oracles, xs, ys):
         assert rel(y.cpu().numpy(), M.matvec(O, x)) <= TOL32
         assert rel(H.matvec_host(x), M.matvec(O, x)) <= TOL32
+        out = torch.empty(len(x), dtype=torch.float64, pin_memory=True).numpy()
+        assert H.matvec_host(x, out=out) is out and rel(out, M.matvec(O, x)) <= TOL32
         assert rel(H.matvec_ws(gpu(x)).cpu().numpy(), M.matvec(O, x)) <= TOL32
         H.sync_status()
+    with pytest.raises(ValueError):
+        mats[0].matvec_host(xs[0], out=np.empty(len(xs[0]) + 1))
 
 
 def test_batch_one_launch_sequence_and_graph(P, tmp_path):

@@ -919,7 +919,7 @@ size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
   uint8_t* ximg = (uint8_t*)take(size_t(3) * nblk * 4096);  // [block][three bf16 slices][4 KB]
   uint8_t* timg = (uint8_t*)take(std::max<size_t>(256, size_t(tb)));
   float* part = (float*)take(sizeof(float) * std::max<int64_t>(64, pf));
-  int* cnt = (int*)take(sizeof(int) * std::max(64, nc));
+  int* cnt = (int*)take(sizeof(int) * std::max(64, nc + 2));  // split-group counters, then 2 work counters
   double* acc = (double*)take(sizeof(double) * hh::dev::kTcMaxRhs * h->npad);
   float* xh = (float*)take(sizeof(float) * 128 * h->npad);
   float* xl = (float*)take(sizeof(float) * 128 * h->npad);
@@ -950,8 +950,9 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   mark(0);
   const TcSet& ts = h->tc[dir];
   const MrSet& ms = h->mr[dir];
+  // clears the split-group counters and, after them, the two work counters
   cudaError_t e = hh::dev::launch_tc_prep(in, ld_in, nr, h->d_perm, h->H.n, t.nblk, t.ximg, t.acc, h->npad, t.cnt,
-                                          ts.n_cnt, t.xh, t.xl, h->npad, t.t32, ms.t_floats, st);
+                                          ts.n_cnt + 2, t.xh, t.xl, h->npad, t.t32, ms.t_floats, st);
   mark(1);
   {
     hh::dev::TdArgs d;
@@ -999,6 +1000,7 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   a.part = t.part;
   a.cnt = t.cnt;
   a.n_cnt = ts.n_cnt;
+  a.work = t.cnt + ts.n_cnt;
   a.acc = t.acc;
   a.npad = h->npad;
   a.status = h->d_status;

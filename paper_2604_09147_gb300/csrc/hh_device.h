@@ -289,6 +289,7 @@ struct TcArgs {
   float* part;           // partial sums of split groups
   int* cnt;              // arrival counters of split groups (cleared by the prep launch)
   int32_t n_cnt, pad;
+  int* work;             // work counters of phase 1 and phase 2 (cleared by the prep launch)
   double* acc;           // output accumulator [nr][npad], tree order
   int64_t npad;
   int* status;           // bit 3: a bounded wait expired

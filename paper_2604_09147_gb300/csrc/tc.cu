@@ -49,8 +49,9 @@
 //              are advanced by additions);
 //   warps 2-5  drain the banks (tensor-memory lane quarter w mod 4) into fp32
 //              registers and write each item's result.
-// Items are cost-sorted on the host and dealt to the CTAs in snake order;
-// every role walks the same sequence.  Shared-memory operands use the K-major
+// Items are cost-sorted on the host and taken dynamically from a work
+// counter by each CTA's producer, which passes their indices to the other
+// roles through a small shared-memory queue.  Shared-memory operands use the K-major
 // layout without swizzling: 8-row by 16-byte core matrices, the two core
 // matrices of one K step 128 bytes apart (leading byte offset), successive
 // 8-row groups 256 bytes apart (stride byte offset).  Every mbarrier wait has
@@ -238,17 +239,13 @@ __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
   return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 127) & ~static_cast<uintptr_t>(127));
 }
 
-// k-th item of this CTA: rounds of gridDim.x items, dealt forwards in even
-// rounds and backwards in odd ones; -1 when the list is exhausted
-__device__ __forceinline__ int item_of(int k, int n_items) {
-  const int g = gridDim.x, c = (k & 1) ? g - 1 - static_cast<int>(blockIdx.x) : static_cast<int>(blockIdx.x);
-  const long long i = static_cast<long long>(k) * g + c;
-  return i < n_items ? static_cast<int>(i) : -1;
-}
+constexpr int kQ = 4;  // item queue slots between the producer and the other roles
 
 struct Ctl {
   uint64_t full[kDepth], empty[kDepth];
   uint64_t bfull[kBanks], bempty[kBanks];
+  uint64_t qfull[kQ], qempty[kQ];  // item index published / read by the MMA thread and the 4 drain warps
+  int qid[kQ];
   uint32_t tmem;
   int abort;
 };
@@ -287,6 +284,10 @@ __device__ __forceinline__ void ws_setup(Ctl* c) {
       mbar_init(&c->bfull[b], 1);
       mbar_init(&c->bempty[b], 4);
     }
+    for (int q = 0; q < kQ; ++q) {
+      mbar_init(&c->qfull[q], 1);
+      mbar_init(&c->qempty[q], 5);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     c->abort = 0;
   }
@@ -298,6 +299,35 @@ __device__ __forceinline__ void ws_setup(Ctl* c) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Items are taken dynamically, in the host's cost order, from a work counter
+// in global memory (cleared by the input-image launch): the producer takes
+// the index of its k-th item and publishes it in queue slot k mod kQ; the MMA
+// thread and the drain warps read it there.  Returns the item, -1 when the
+// list is exhausted, -2 when a bounded wait gave up.
+__device__ __forceinline__ int q_publish(Ctl* c, int k, int* counter, int n, volatile int* abort) {
+  const int slot = k % kQ;
+  if (k >= kQ && !ws_wait(&c->qempty[slot], ((k / kQ) - 1) & 1, abort)) return -2;
+  int it = atomicAdd(counter, 1);
+  if (it >= n) it = -1;
+  c->qid[slot] = it;
+  mbar_arrive(&c->qfull[slot]);
+  return it;
+}
+// whole_warp: a drain warp (all lanes read, lane 0 releases the slot);
+// otherwise the single MMA-issuing thread
+__device__ __forceinline__ int q_take(Ctl* c, int k, volatile int* abort, bool whole_warp) {
+  const int slot = k % kQ;
+  if (!ws_wait(&c->qfull[slot], (k / kQ) & 1, abort)) return -2;
+  const int it = *reinterpret_cast<volatile int*>(&c->qid[slot]);
+  if (whole_warp) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&c->qempty[slot]);
+  } else {
+    mbar_arrive(&c->qempty[slot]);
+  }
+  return it;
 }
 
 // after the role loops: on an abort the producer waits (bounded) for the
@@ -374,12 +404,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) tc_phase1(TcArgs a) {
       const uint64_t pol = evict_first();
       int gs = 0;
       bool ok = true;
-      int itn = item_of(0, a.n_groups);
+      int itn = q_publish(c, 0, a.work, a.n_groups, abort);
       TcGroup gn{};
       if (itn >= 0) gn = a.groups[itn];  // the next item, loaded one ahead
       for (int k = 0; ok && itn >= 0; ++k) {
         const TcGroup g = gn;
-        itn = item_of(k + 1, a.n_groups);
+        itn = q_publish(c, k + 1, a.work, a.n_groups, abort);
+        if (itn == -2) break;
         if (itn >= 0) gn = a.groups[itn];
         const uint32_t vbytes = tc_factor_slices(g.fmt) * static_cast<uint32_t>(g.nk) * 32u;
         const int nblk = (g.p1 - g.p0 + 15) >> 4, nst = (nblk + kKS - 1) / kKS;
@@ -408,12 +439,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) tc_phase1(TcArgs a) {
       const uint64_t d0 = op_desc(base);
       int gs = 0, gp = 0;
       bool ok = true;
-      int itn = item_of(0, a.n_groups);
+      int itn = q_take(c, 0, abort, false);
       TcGroup gn{};
       if (itn >= 0) gn = a.groups[itn];  // the next item, loaded one ahead
       for (int k = 0; ok && itn >= 0; ++k) {
         const TcGroup g = gn;
-        itn = item_of(k + 1, a.n_groups);
+        itn = q_take(c, k + 1, abort, false);
+        if (itn == -2) break;
         if (itn >= 0) gn = a.groups[itn];
         const int np = n_products(g.fmt), nblk = (g.p1 - g.p0 + 15) >> 4, nst = (nblk + kKS - 1) / kKS;
         const int L = chunk_of(g.fmt);
@@ -460,12 +492,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) tc_phase1(TcArgs a) {
     float acc[128];
     int gp = 0;
     bool ok = true;
-    int itn = item_of(0, a.n_groups);
+    int itn = q_take(c, 0, abort, true);
     TcGroup gn{};
     if (itn >= 0) gn = a.groups[itn];
     for (int k = 0; ok && itn >= 0; ++k) {
       const TcGroup g = gn;
-      itn = item_of(k + 1, a.n_groups);
+      itn = q_take(c, k + 1, abort, true);
+      if (itn == -2) break;
       if (itn >= 0) gn = a.groups[itn];
       const int L = chunk_of(g.fmt), nk = g.nk, nst = (((g.p1 - g.p0 + 15) >> 4) + kKS - 1) / kKS;
       const int nchunks = (nst + L - 1) / L;
@@ -552,12 +585,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) tc_phase2(TcArgs a) {
       const uint64_t pol = evict_first();
       int gs = 0;
       bool ok = true;
-      int itn = item_of(0, a.n_tiles);
+      int itn = q_publish(c, 0, a.work + 1, a.n_tiles, abort);
       TcTile tn{};
       if (itn >= 0) tn = a.tiles[itn];  // the next item, loaded one ahead
       for (int k = 0; ok && itn >= 0; ++k) {
         const TcTile tl = tn;
-        itn = item_of(k + 1, a.n_tiles);
+        itn = q_publish(c, k + 1, a.work + 1, a.n_tiles, abort);
+        if (itn == -2) break;
         if (itn >= 0) tn = a.tiles[itn];
         TcEntry nx = a.entries[tl.first];  // the next entry, loaded one ahead
         for (int e = 0; e < tl.count && ok; ++e) {
@@ -586,12 +620,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) tc_phase2(TcArgs a) {
       const uint64_t d0 = op_desc(base);
       int gs = 0, gp = 0;
       bool ok = true;
-      int itn = item_of(0, a.n_tiles);
+      int itn = q_take(c, 0, abort, false);
       TcTile tn{};
       if (itn >= 0) tn = a.tiles[itn];  // the next item, loaded one ahead
       for (int k = 0; ok && itn >= 0; ++k) {
         const TcTile tl = tn;
-        itn = item_of(k + 1, a.n_tiles);
+        itn = q_take(c, k + 1, abort, false);
+        if (itn == -2) break;
         if (itn >= 0) tn = a.tiles[itn];
         const int nst = tl.nst, L = tl.chunk;
         int i = 0, j = 0, s = gs % kDepth, par = (gs / kDepth) & 1;
@@ -639,12 +674,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) tc_phase2(TcArgs a) {
     float acc[128];
     int gp = 0;
     bool ok = true;
-    int itn = item_of(0, a.n_tiles);
+    int itn = q_take(c, 0, abort, true);
     TcTile tn{};
     if (itn >= 0) tn = a.tiles[itn];
     for (int k = 0; ok && itn >= 0; ++k) {
       const TcTile tl = tn;
-      itn = item_of(k + 1, a.n_tiles);
+      itn = q_take(c, k + 1, abort, true);
+      if (itn == -2) break;
       if (itn >= 0) tn = a.tiles[itn];
       const int nst = tl.nst, L = tl.chunk;
 #pragma unroll

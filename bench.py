@@ -885,6 +885,7 @@ def run_many(args):
                    "l2": "inputs larger than L2 (%.2f GB of factors and dense blocks per step)"
                          % (inf["bytes_per_matvec"] / 1e9)},
         "streaming_4col": {"ms_per_step": ms_stream, "speedup": ms_stream / ms},
+        "other_stages_ms": {k: stages[k] for k in ("images", "fp64_streaming", "finish")},
         "blocks_per_fmt": inf["blocks_per_fmt"], "factor_bytes_per_fmt": inf["factor_bytes_per_fmt"],
         "tc_factor_bytes": inf["tc_factor_bytes"], "bound_thm44": inf["bound_thm44"], "build_seconds": build_s,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "parity": parity,

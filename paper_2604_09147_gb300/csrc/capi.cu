@@ -903,6 +903,7 @@ struct TcWs {
   float* t32;  // T of the CUDA-core pieces
   uint8_t* xdig;  // the input's digit panels of the dense blocks (dense_tc.cu)
   int32_t* bexp;  // and their column exponents
+  double* xt;     // the input in tree order [128][npad]
 };
 
 size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
@@ -929,7 +930,8 @@ size_t tc_ws_layout(const hh_matrix* h, TcWs* v, char* base) {
   const int64_t de = std::max(h->mr[0].n_dentries, h->mr[1].n_dentries);
   uint8_t* xdig = (uint8_t*)take(std::max<size_t>(256, size_t(dx)));
   int32_t* bexp = (int32_t*)take(sizeof(int32_t) * 128 * std::max<int64_t>(1, de));
-  if (v) *v = {ximg, timg, part, cnt, acc, nblk, xh, xl, t32, xdig, bexp};
+  double* xt = (double*)take(sizeof(double) * hh::dev::kTcMaxRhs * h->npad);
+  if (v) *v = {ximg, timg, part, cnt, acc, nblk, xh, xl, t32, xdig, bexp, xt};
   return off;
 }
 
@@ -952,7 +954,7 @@ cudaError_t run_tc(hh_matrix* h, int dir, const double* in, double* out, int nr,
   const MrSet& ms = h->mr[dir];
   // clears the split-group counters and, after them, the two work counters
   cudaError_t e = hh::dev::launch_tc_prep(in, ld_in, nr, h->d_perm, h->H.n, t.nblk, t.ximg, t.acc, h->npad, t.cnt,
-                                          ts.n_cnt + 2, t.xh, t.xl, h->npad, t.t32, ms.t_floats, st);
+                                          ts.n_cnt + 2, t.xh, t.xl, h->npad, t.t32, ms.t_floats, t.xt, st);
   mark(1);
   {
     hh::dev::TdArgs d;

@@ -118,6 +118,42 @@ __device__ __forceinline__ int batch_find(const int64_t* __restrict__ pofs, int 
   }
   return lo;
 }
+// d as an unevaluated fp32 pair hi + lo (hi = fl32(d) rounded to nearest
+// even, lo = fl32(d - hi)) from d's bits with integer operations: the
+// device's fp64 conversions and subtraction run on its low-rate fp64 units.
+// Zero, subnormal, non-finite or out-of-range values (|d| below 2^-74 or
+// above the fp32 range) take the fp64 conversions in a function that is not
+// inlined (rare).
+static __device__ __noinline__ void split_f64_rare(double d, float& hi, float& lo) {
+  hi = __double2float_rn(d);
+  lo = __double2float_rn(d - static_cast<double>(hi));
+}
+__device__ __forceinline__ void split_f64(double d, float& hi, float& lo) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const int E = static_cast<int>((b >> 52) & 0x7ffu);
+  const int e = E - 1023 + 127;  // fp32 biased exponent of hi (before rounding up)
+  if (E == 0 || e < 53 || e > 253) {
+    if ((b << 1) == 0) {
+      hi = lo = 0.f;
+      return;
+    }
+    split_f64_rare(d, hi, lo);
+    return;
+  }
+  const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);  // 53-bit significand
+  unsigned long long top = m >> 29;                                      // 24 bits
+  const unsigned long long rem = m & ((1ull << 29) - 1);
+  if (rem > (1ull << 28) || (rem == (1ull << 28) && (top & 1ull))) top += 1;
+  const int r = static_cast<int>(static_cast<long long>(m) - static_cast<long long>(top << 29));  // |r| <= 2^28
+  const uint32_t sign = static_cast<uint32_t>(b >> 32) & 0x80000000u;
+  const uint32_t hb = top == (1ull << 24) ? (static_cast<uint32_t>(e + 1) << 23)
+                                          : ((static_cast<uint32_t>(e) << 23) | static_cast<uint32_t>(top & 0x7fffffu));
+  hi = __uint_as_float(hb | sign);
+  // lo = r 2^(E - 1075): the integer rounded once to fp32, then an exact
+  // scaling by a normal power of two (e - 52 >= 1)
+  const float lf = static_cast<float>(r) * __uint_as_float(static_cast<uint32_t>(e - 52) << 23);
+  lo = sign ? -lf : lf;
+}
 // position p of a batch's input images: the four shifted copies of the fp32
 // leading / trailing halves, and the cleared accumulator
 __device__ __forceinline__ void batch_prep_position(int64_t p, const double* __restrict__ x,
@@ -134,9 +170,10 @@ __device__ __forceinline__ void batch_prep_position(int64_t p, const double* __r
       const int64_t l = q - pofs[j];
       if (l < ns[j]) v = x[xofs[j] + perm[pofs[j] + l]];
     }
-    const float hi = __double2float_rn(v);
+    float hi, lo;
+    split_f64(v, hi, lo);
     xs[static_cast<int64_t>(s) * np + p] = hi;
-    xs_lo[static_cast<int64_t>(s) * np + p] = __double2float_rn(v - static_cast<double>(hi));
+    xs_lo[static_cast<int64_t>(s) * np + p] = lo;
   }
   acc[p] = 0.0;
 }
@@ -309,10 +346,10 @@ inline __host__ __device__ int tc_factor_slices(int fmt) { return fmt == 1 ? 3 :
 inline __host__ __device__ int tc_input_slices(int fmt) { return fmt == 1 ? 3 : 2; }
 // input images of the many-column sequence (both the tensor-core image and
 // the fp32 halves [npos][128] of mr.cu, npos <= 16 nblk) and the clearing of
-// acc, cnt and t32
+// acc, cnt and t32; xt: scratch [nr][npad] fp64 for the tree-ordered input
 cudaError_t launch_tc_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t nblk,
                            uint8_t* ximg, double* acc, int64_t npad, int* cnt, int n_cnt, float* xh, float* xl,
-                           int64_t npos, float* t32, int64_t t_floats, cudaStream_t st);
+                           int64_t npos, float* t32, int64_t t_floats, double* xt, cudaStream_t st);
 // packs the factor panels of a set's groups (phase 1) and entries (phase 2) into img
 cudaError_t launch_tc_pack(const TcPiece* pieces, const TcGroup* groups, int n_groups, const TcEntry* entries,
                            int n_entries, uint8_t* img, cudaStream_t st);

@@ -29,8 +29,8 @@ __global__ void prep_kernel(const double* __restrict__ in, int64_t ld, int nr,
     const int64_t u = q < n ? static_cast<int64_t>(perm[q]) : -1;
     for (int r = 0; r < nr; ++r) {
       const double v = u >= 0 ? in[u + r * ld] : 0.0;
-      const float hi = __double2float_rn(v);
-      const float lo = __double2float_rn(v - static_cast<double>(hi));
+      float hi, lo;
+      split_f64(v, hi, lo);
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         const int64_t p = q - s;
@@ -53,24 +53,40 @@ __global__ void presplit_kernel(uint8_t* __restrict__ base, const int64_t* __res
     float2* q = reinterpret_cast<float2*>(p);
     const int64_t n = spans[2 * s + 1];
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const double v = p[i];
-      const float hi = __double2float_rn(v);
-      q[i] = make_float2(hi, __double2float_rn(v - static_cast<double>(hi)));
+      float hi, lo;
+      split_f64(p[i], hi, lo);
+      q[i] = make_float2(hi, lo);
     }
   }
 }
 
-// out[u + r ld] = acc[r npad + iperm[u]]: a thread owns caller position u
-// and walks the columns, so the writes of a warp are coalesced and the
-// gathered reads of the threads in flight stay in a few accumulator columns
+// out[u + r ld] = acc[r npad + iperm[u]], column by column: consecutive
+// threads take consecutive caller positions u of the same column, so the
+// writes of a warp are coalesced and the gathered reads of the threads in
+// flight stay in a few accumulator columns (L2); each thread handles four
+// pairs with independent loads
 __global__ void finish_kernel(const double* __restrict__ acc, int nr, const int32_t* __restrict__ iperm,
                               int64_t n, int64_t npad, double* __restrict__ out, int64_t ld) {
   // launched as a programmatic dependent of the last pass: wait for it
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u < n;
-       u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t p = iperm[u];
-    for (int r = 0; r < nr; ++r) out[u + r * ld] = acc[static_cast<int64_t>(r) * npad + p];
+  const int64_t total = static_cast<int64_t>(nr) * n;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t q0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q0 < total; q0 += 4 * stride) {
+    double v[4];
+    int64_t o[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t q = q0 + j * stride;
+      o[j] = -1;
+      if (q < total) {
+        const int64_t r = q / n, u = q - r * n;
+        v[j] = acc[r * npad + iperm[u]];
+        o[j] = u + r * ld;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (o[j] >= 0) out[o[j]] = v[j];
   }
 }
 

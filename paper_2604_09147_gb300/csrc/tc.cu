@@ -758,7 +758,22 @@ __global__ void tc_pack2_kernel(const TcPiece* __restrict__ pieces, const TcEntr
   }
 }
 
-// X (caller's order, column-major, ld) -> tree order, once per product:
+// X (caller's order, column-major, ld) -> xt (tree order, [nr][npad] fp64),
+// column by column: consecutive threads take consecutive tree positions of
+// the same column, so the gathered reads of the threads in flight stay in a
+// few columns of X (L2) and the writes are coalesced
+__global__ void tc_gather_kernel(const double* __restrict__ x, int64_t ld, int nr, const int32_t* __restrict__ perm,
+                                 int64_t n, int64_t npad, double* __restrict__ xt) {
+  const int64_t total = static_cast<int64_t>(nr) * npad;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total; q += stride) {
+    const int64_t r = q / npad, p = q - r * npad;
+    xt[q] = p < n ? x[static_cast<int64_t>(perm[p]) + r * ld] : 0.0;
+  }
+}
+
+// the input in tree order (xt, or X read through the permutation when xt is
+// null) -> the images, once per product:
 //   * fp32 of each value as three bf16 slices in the phase-1 operand image
 //     [16-position block][slice][128 rows x 32 B] (rows r >= nr and positions
 //     >= n are zero);
@@ -766,11 +781,12 @@ __global__ void tc_pack2_kernel(const TcPiece* __restrict__ pieces, const TcEntr
 //     kernels (mr.cu);
 // and clears the output accumulator, the arrival counters of the split
 // groups and the T arena of the CUDA-core pieces.  One gather of X feeds
-// both images.
-__global__ void tc_prep_kernel(const double* __restrict__ x, int64_t ld, int nr, const int32_t* __restrict__ perm,
-                               int64_t n, int64_t nblk, uint8_t* __restrict__ ximg, double* __restrict__ acc,
-                               int64_t npad, int* __restrict__ cnt, int n_cnt, float* __restrict__ xh,
-                               float* __restrict__ xl, int64_t npos, float* __restrict__ t32, int64_t t_floats) {
+// both images; each value is split into fp32 halves with integer operations.
+__global__ void tc_prep_kernel(const double* __restrict__ x, int64_t ld, const int32_t* __restrict__ perm,
+                               const double* __restrict__ xt, int nr, int64_t n, int64_t nblk,
+                               uint8_t* __restrict__ ximg, double* __restrict__ acc, int64_t npad,
+                               int* __restrict__ cnt, int n_cnt, float* __restrict__ xh, float* __restrict__ xl,
+                               int64_t npos, float* __restrict__ t32, int64_t t_floats) {
   const int64_t total = nblk * 256;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -781,11 +797,13 @@ __global__ void tc_prep_kernel(const double* __restrict__ x, int64_t ld, int nr,
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int64_t p = 16 * blk + 8 * c + t;
-      const double d = (r < nr && p < n) ? x[static_cast<int64_t>(perm[p]) + r * ld] : 0.0;
-      v[t] = __double2float_rn(d);
+      double d = 0.0;
+      if (r < nr && p < n) d = xt ? xt[static_cast<int64_t>(r) * npad + p] : x[static_cast<int64_t>(perm[p]) + r * ld];
+      float lo;
+      split_f64(d, v[t], lo);
       if (p < npos) {
         xh[p * 128 + r] = v[t];
-        xl[p * 128 + r] = __double2float_rn(d - static_cast<double>(v[t]));
+        xl[p * 128 + r] = lo;
       }
     }
     store_slices(v, 3, ximg + blk * (3 * 4096) + core_off(r, c), 4096);
@@ -800,13 +818,22 @@ __global__ void tc_prep_kernel(const double* __restrict__ x, int64_t ld, int nr,
 
 cudaError_t launch_tc_prep(const double* x, int64_t ld, int nr, const int32_t* perm, int64_t n, int64_t nblk,
                            uint8_t* ximg, double* acc, int64_t npad, int* cnt, int n_cnt, float* xh, float* xl,
-                           int64_t npos, float* t32, int64_t t_floats, cudaStream_t st) {
+                           int64_t npos, float* t32, int64_t t_floats, double* xt, cudaStream_t st) {
   if (16 * nblk < npos) return cudaErrorInvalidValue;  // the fp32 images must be covered
+  // the input's columns read through the permutation stay in L2 up to about
+  // 100 MB; beyond that they are first gathered column by column into xt
+  const bool gather = static_cast<int64_t>(nr) * n * 8 > (int64_t(100) << 20);
+  if (gather) {
+    int64_t gb = (static_cast<int64_t>(nr) * npad + 255) / 256;
+    if (gb > 8192) gb = 8192;
+    if (gb < 1) gb = 1;
+    tc_gather_kernel<<<static_cast<int>(gb), 256, 0, st>>>(x, ld, nr, perm, n, npad, xt);
+  }
   int64_t blocks = (nblk * 256 + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   if (blocks < 1) blocks = 1;
-  tc_prep_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(x, ld, nr, perm, n, nblk, ximg, acc, npad, cnt, n_cnt, xh,
-                                                          xl, npos, t32, t_floats);
+  tc_prep_kernel<<<static_cast<int>(blocks), 256, 0, st>>>(x, ld, perm, gather ? xt : nullptr, nr, n, nblk, ximg, acc,
+                                                          npad, cnt, n_cnt, xh, xl, npos, t32, t_floats);
   return cudaGetLastError();
 }
 

@@ -366,7 +366,7 @@ int hh_matvec_timed(hh_handle h, int transpose, const double* in, double* out, i
  * (CUDA events, a private stream, temporary buffers of 2 n max(4, nrhs_many)
  * doubles): the CTAs per SM of each streaming pass (1 .. occupancy maximum,
  * per direction and phase) and, when nrhs_many > 0, the positions per
- * many-column phase-1 item ({512, ..., 16384}) for products of nrhs_many
+ * many-column phase-1 item ({1024, ..., 65536}) for products of nrhs_many
  * columns.  The choices stay in the handle (hh_info reports them); results
  * of products do not depend on them beyond rounding.  Synchronous; not
  * concurrent with products on the same handle. */

@@ -1704,7 +1704,7 @@ int hh_autotune(hh_handle h, int nrhs_many) {
   if (rc == HH_OK && nrhs_many > 0) {
     int best_s = h->split_len;
     float best = 1e30f;
-    for (int split : {512, 1024, 2048, 4096, 8192, 16384}) {
+    for (int split : {1024, 2048, 4096, 8192, 16384, 32768, 65536}) {
       h->split_len = split;
       try {
         rebuild_many(h);

@@ -334,7 +334,7 @@ struct TcArgs {
 constexpr int kTcMaxRhs = 128;          // right-hand sides per tensor-core launch sequence
 constexpr int kTcRows = 128;            // phase-2 tile rows
 constexpr int kTcGroupRanks = 128;      // ranks of one phase-1 group
-constexpr int kTcSplitPositions = 4096; // positions of one phase-1 item (default)
+constexpr int kTcSplitPositions = 8192; // positions of one phase-1 item (default)
 constexpr int kTcKSteps = 2;            // K steps (16 positions or ranks) per pipeline stage
 // stages whose K steps add into one tensor-memory bank before it is drained
 // (fp32 pieces; the 16- and 8-bit pieces)

@@ -167,7 +167,7 @@ def test_oracle_written_file_roundtrips_through_library(P, tmp_path):
     assert inf["tc_blocks"] == len(tc)
     assert inf["tc_v_elems"] == sum(b.n * b.k for b in tc) and inf["tc_u_elems"] == sum(b.m * b.k for b in tc)
     assert inf["dense_elems"] == sum(d.m * d.n for d in O.dense)
-    assert inf["tuned"] == 0 and inf["split_positions"] == 4096 and inf["tc_panel_bytes"] == [0, 0]
+    assert inf["tuned"] == 0 and inf["split_positions"] == 8192 and inf["tc_panel_bytes"] == [0, 0]
     assert inf["dense_tc_elems"] == 0        # tables of the device path: none without device data
 
 

@@ -366,10 +366,10 @@ def test_autotune_keeps_results(P):
     xm = gpu(np.ascontiguousarray(W.rhs(6000, 40, "normal", 9502).T)).t()
     before = [H.matvec(x1).cpu().numpy(), H.matvec(x1, transpose=True).cpu().numpy(), H.matvec(xm).cpu().numpy()]
     info0 = H.info()
-    assert info0["tuned"] == 0 and info0["split_positions"] == 4096
+    assert info0["tuned"] == 0 and info0["split_positions"] == 8192
     choice = H.autotune(40)
     info = H.info()
-    assert info["tuned"] == 1 and choice["split_positions"] in (512, 1024, 2048, 4096, 8192, 16384)
+    assert info["tuned"] == 1 and choice["split_positions"] in (1024, 2048, 4096, 8192, 16384, 32768, 65536)
     assert all(1 <= c <= 16 for c in choice["blocks_per_sm"])
     after = [H.matvec(x1).cpu().numpy(), H.matvec(x1, transpose=True).cpu().numpy(), H.matvec(xm).cpu().numpy()]
     H.sync_status()

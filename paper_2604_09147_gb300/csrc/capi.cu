@@ -394,7 +394,12 @@ void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
   for (size_t i = 0; i < raw.size();) {
     size_t j = i;
     while (j < raw.size() && !(raw[i].first < raw[j].first) && !(raw[j].first < raw[i].first)) ++j;
-    // pieces [i, j) share the input cluster and the format: pack into groups
+    // pieces [i, j) share the input cluster and the format: pack into groups;
+    // their items are listed split-major (every group's first position
+    // range, then every group's second, ...), so that items taken at the
+    // same time read the same input blocks, which then stay in L2 (the cost
+    // sort below keeps this order among items of equal cost)
+    std::vector<TcGroup> gl;
     for (size_t t = i; t < j;) {
       TcGroup g;
       std::memset(&g, 0, sizeof(g));
@@ -418,22 +423,27 @@ void build_tc_set(hh_matrix* h, int dir, TcSet& out) {
       if (nsplit > 1) {
         g.gid = out.n_cnt / 4;
         out.n_cnt += 4;
+        g.poff = out.part_floats;  // nsplit consecutive [128][nk] partial sums
+        out.part_floats += int64_t(nsplit) * 128 * g.nk;
       }
       g.img = out.img_bytes;
       out.img_bytes += align128(int64_t((g.rows + 15) / 16) * hh::dev::tc_factor_slices(g.fmt) * g.nk * 32);
-      for (int sp = 0; sp < nsplit; ++sp) {
+      gl.push_back(g);
+    }
+    const int nsplit = gl.empty() ? 0 : gl.front().nsplit;  // the groups of a key share the cluster
+    for (int sp = 0; sp < nsplit; ++sp)
+      for (const TcGroup& g : gl) {
         TcGroup gs = g;
         gs.split = sp;
         gs.p0 = sp * split_len;
         gs.p1 = std::min(g.rows, (sp + 1) * split_len);
         if (nsplit > 1) {
-          gs.poff = out.part_floats;
-          out.part_floats += int64_t(128) * g.nk;
+          // a group's split items are consecutive in the partial-sum arena
+          gs.poff = g.poff + int64_t(sp) * 128 * g.nk;
         }
         groups.push_back({gs, double((gs.p1 - gs.p0 + 15) / 16) *
                                    double(hh::dev::tc_factor_slices(g.fmt) * g.nk * 32 + hh::dev::tc_input_slices(g.fmt) * 4096)});
       }
-    }
     i = j;
   }
   std::stable_sort(groups.begin(), groups.end(), [](const CGroup& x, const CGroup& y) { return x.cost > y.cost; });

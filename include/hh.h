@@ -28,8 +28,10 @@
  *    calls on one handle must be ordered on a single stream; use
  *    hh_matvec_ws with caller-owned workspaces for concurrent streams.
  *  - Device-side anomalies (an invalid descriptor) are recorded in a device
- *    status word and reported by hh_sync_status(); the kernels never trap and
- *    contain no waits on other blocks.
+ *    status word and reported by hh_sync_status(); the kernels never trap,
+ *    every wait inside a block has a clock limit, and no kernel waits on
+ *    other blocks except the batch product's cooperative kernel, whose grid
+ *    barriers span one co-resident launch (hh_batch_matvec).
  */
 #ifndef HH_H_
 #define HH_H_

@@ -140,6 +140,19 @@ def test_tc_backward_error_within_theorem_4_4(P, tmp_path_factory):
     assert be.max() <= H.info()["bound_thm44"] + 1e-6
 
 
+@pytest.mark.parametrize("name", ["gauss_all", "gauss_narrow"])
+@pytest.mark.parametrize("nrhs", [5, 8, 16, 17])
+def test_tc_few_columns(P, tmp_path_factory, name, nrhs):
+    """5 to 31 columns take the many-column sequence too (hh_matvec switches
+    at 5): fewer right-hand sides than one 16-row MMA block, and 8 columns as
+    in the many-right-hand-side workload, against the oracle per column and
+    per leaf cluster, forward and transposed."""
+    H, O = case(P, tmp_path_factory, name)
+    check(H, O, nrhs, False, 7400 + nrhs)
+    check(H, O, nrhs, True, 7500 + nrhs)
+    assert min(H.info()["tc_panel_bytes"]) > 0            # both directions went through the tensor cores
+
+
 @pytest.mark.parametrize("nrhs", [33, 47, 200])
 def test_tc_ragged_rhs_counts(P, tmp_path_factory, nrhs):
     """nrhs not a multiple of 16 (padded right-hand sides must stay zero) and
@@ -212,7 +225,7 @@ def test_tc_autograd_multi_rhs(P, tmp_path_factory):
     assert np.linalg.norm(xt.grad.cpu().numpy() - ref_g) <= TOL * np.linalg.norm(ref_g) + np.linalg.norm(ab_g)
 
 
-@pytest.mark.parametrize("nrhs", [32, 40, 128])
+@pytest.mark.parametrize("nrhs", [5, 8, 32, 40, 128])
 def test_many_rhs_fp64_matrix(P, tmp_path, nrhs):
     """Uniform fp64 storage with many right-hand sides: the fp64 low-rank blocks
     take the streaming passes in chunks of 4 columns and the dense blocks the

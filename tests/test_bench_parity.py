@@ -41,3 +41,4 @@ def test_rows_check_many_columns(tmp_path):
     Yp[:, 3] *= 1 + 1e-6
     r = bench.oracle_rows_check(G, X, Yp, leaves=1 << G.tree.L)
     assert r["rows"] == 2000 and 0 < r["rel_err"] < 1e-6
+
